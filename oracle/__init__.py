@@ -1,0 +1,171 @@
+"""CPU oracle for the hierarchy-cut-code hot path -- TEST INFRASTRUCTURE.
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+and reference legs may import this package.  The product library
+(``paper_2305_16652_gb300``) never imports, links or calls it; the two share
+no code.  Functions take and return numpy arrays and run single-threaded in
+``hcc_oracle.cpp`` (built with g++, no FMA contraction).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hcc_oracle.cpp")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libhcc_oracle.so")
+_lib = None
+
+HIT_DTYPE = np.dtype([("prim", np.int32), ("t", np.float32), ("u", np.float32), ("v", np.float32)])
+
+
+def build(force: bool = False) -> str:
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    P = ctypes.c_void_p
+    u32, u64, i32, f64, f32 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_float
+    lib.oracle_surface_area.argtypes = [P, P]
+    lib.oracle_surface_area.restype = f64
+    lib.oracle_had.argtypes = [u32, P, P, P, P, P, f64, P]
+    lib.oracle_had.restype = None
+    lib.oracle_select_cut.argtypes = [u32, P, P, P, P, P, u32, f64, P]
+    lib.oracle_select_cut.restype = u32
+    lib.oracle_encode_hcc.argtypes = [u64, P, P, u32, P, P, u32, P]
+    lib.oracle_encode_hcc.restype = None
+    lib.oracle_key_margin.argtypes = [u64, P, P, u32, P, P, u32, P]
+    lib.oracle_key_margin.restype = None
+    lib.oracle_encode_twopoint.argtypes = [u64, P, P, P, P, u32, P]
+    lib.oracle_encode_twopoint.restype = None
+    lib.oracle_stable_sort.argtypes = [u64, P, P]
+    lib.oracle_stable_sort.restype = None
+    lib.oracle_gather.argtypes = [u64, P, P, P, P, P]
+    lib.oracle_gather.restype = None
+    lib.oracle_intersect.argtypes = [P, P, f32, f32, P, P, P, P]
+    lib.oracle_intersect.restype = i32
+    lib.oracle_trace_brute.argtypes = [u32, P, u64, P, P, i32, P]
+    lib.oracle_trace_brute.restype = None
+    lib.oracle_trace_bvh.argtypes = [u32, P, P, P, P, P, P, P, P, u64, P, P, i32, P]
+    lib.oracle_trace_bvh.restype = None
+    _lib = lib
+    return lib
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def surface_area(lo, hi) -> float:
+    lo, hi = _c(lo, np.float32), _c(hi, np.float32)
+    return float(_load().oracle_surface_area(_p(lo), _p(hi)))
+
+
+def _tree(bvh):
+    return (_c(bvh.lo, np.float32), _c(bvh.hi, np.float32), _c(bvh.left, np.int32), _c(bvh.right, np.int32),
+            _c(bvh.count, np.uint32))
+
+
+def had(bvh, lam: float = 0.125) -> np.ndarray:
+    lo, hi, left, right, count = _tree(bvh)
+    out = np.zeros(lo.shape[0], np.float64)
+    _load().oracle_had(lo.shape[0], _p(lo), _p(hi), _p(left), _p(right), _p(count), lam, _p(out))
+    return out
+
+
+def select_cut(bvh, cut_size: int, lam: float = 0.125) -> np.ndarray:
+    """Cut node ids in key order (HAD descending)."""
+    lo, hi, left, right, count = _tree(bvh)
+    out = np.zeros(max(cut_size, 1), np.int32)
+    m = _load().oracle_select_cut(lo.shape[0], _p(lo), _p(hi), _p(left), _p(right), _p(count), cut_size, lam,
+                                  _p(out))
+    return out[:m].copy()
+
+
+def encode_hcc(org, dir, cut_lo, cut_hi, key_bits: int) -> np.ndarray:
+    org, dir = _c(org, np.float32), _c(dir, np.float32)
+    cut_lo, cut_hi = _c(cut_lo, np.float32), _c(cut_hi, np.float32)
+    n = org.shape[0]
+    keys = np.zeros(n, np.uint64)
+    _load().oracle_encode_hcc(n, _p(org), _p(dir), cut_lo.shape[0], _p(cut_lo), _p(cut_hi), key_bits, _p(keys))
+    return keys
+
+
+def key_margin(org, dir, cut_lo, cut_hi, key_bits: int) -> np.ndarray:
+    org, dir = _c(org, np.float32), _c(dir, np.float32)
+    cut_lo, cut_hi = _c(cut_lo, np.float32), _c(cut_hi, np.float32)
+    n = org.shape[0]
+    out = np.zeros(n, np.float64)
+    _load().oracle_key_margin(n, _p(org), _p(dir), cut_lo.shape[0], _p(cut_lo), _p(cut_hi), key_bits, _p(out))
+    return out
+
+
+def encode_twopoint(org, dir, scene_lo, scene_hi, key_bits: int) -> np.ndarray:
+    org, dir = _c(org, np.float32), _c(dir, np.float32)
+    lo, hi = _c(scene_lo, np.float32), _c(scene_hi, np.float32)
+    n = org.shape[0]
+    keys = np.zeros(n, np.uint64)
+    _load().oracle_encode_twopoint(n, _p(org), _p(dir), _p(lo), _p(hi), key_bits, _p(keys))
+    return keys
+
+
+def stable_sort(keys) -> np.ndarray:
+    keys = _c(keys, np.uint64)
+    n = keys.shape[0]
+    perm = np.zeros(n, np.uint32)
+    _load().oracle_stable_sort(n, _p(keys), _p(perm))
+    return perm
+
+
+def gather(org, dir, perm):
+    org, dir, perm = _c(org, np.float32), _c(dir, np.float32), _c(perm, np.uint32)
+    n = perm.shape[0]
+    oo = np.zeros((n, 4), np.float32)
+    od = np.zeros((n, 4), np.float32)
+    _load().oracle_gather(n, _p(org), _p(dir), _p(perm), _p(oo), _p(od))
+    return oo, od
+
+
+def intersect(o, d, tmin, tmax, tri):
+    o, d, tri = _c(o, np.float32), _c(d, np.float32), _c(tri, np.float32)
+    t, u, v = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+    hit = _load().oracle_intersect(_p(o), _p(d), tmin, tmax, _p(tri), ctypes.byref(t), ctypes.byref(u),
+                                   ctypes.byref(v))
+    return (bool(hit), t.value, u.value, v.value)
+
+
+def trace_brute(tris, org, dir, any_hit: bool = False) -> np.ndarray:
+    tris, org, dir = _c(tris, np.float32), _c(org, np.float32), _c(dir, np.float32)
+    n = org.shape[0]
+    hits = np.zeros(n, HIT_DTYPE)
+    _load().oracle_trace_brute(tris.shape[0], _p(tris), n, _p(org), _p(dir), int(any_hit), _p(hits))
+    return hits
+
+
+def trace_bvh(bvh, org, dir, any_hit: bool = False) -> np.ndarray:
+    lo, hi, left, right, count = _tree(bvh)
+    first, order = _c(bvh.first, np.uint32), _c(bvh.order, np.uint32)
+    tris, org, dir = _c(bvh.tris, np.float32), _c(org, np.float32), _c(dir, np.float32)
+    n = org.shape[0]
+    hits = np.zeros(n, HIT_DTYPE)
+    _load().oracle_trace_bvh(lo.shape[0], _p(lo), _p(hi), _p(left), _p(right), _p(first), _p(count), _p(order),
+                             _p(tris), n, _p(org), _p(dir), int(any_hit), _p(hits))
+    return hits
