@@ -1,0 +1,442 @@
+"""Benchmark: secondary-ray throughput of the hierarchy-cut-code pipeline.
+
+One step = one pass of the whole hot path over one wavefront of secondary
+rays of the 1920x1080, 8 spp furnished-room workload (16,588,800 rays,
+~1M triangles): HCC encode (cut of 32 nodes, 32-bit keys) -> radix sort ->
+gather -> closest-hit trace with the hits scattered back to input order.
+The same wavefront is also run through the TwoPoint and NoSort orders.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (single-threaded) on a bounded sample
+of the same workload and prints the same JSON line with "impl": "reference".
+Under torchrun (N > 1) every rank traces its own wavefront (weak scaling);
+rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "secondary Mrays/s incl. encode+sort, HCC vs NoSort/TwoPoint; p50/p99 latency"
+UNIT = "Mrays/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "trace_traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+SMS, LANES_PER_SM = 152, 128
+
+# FP32/INT lane operations the trace kernel issues per unit of work, counted
+# from trace.cu: one internal-node visit decodes 12 quantised bounds (byte
+# select, convert, outward fma: 3 ops each), runs two slab tests (6 sub, 6 mul,
+# 12 min/max, 1 mul, 1 min each) and orders/pushes (~10); one triangle test
+# is the Moller-Trumbore sequence (~45 ops incl. the reciprocal).
+OPS_PER_NODE = 36 + 2 * 26 + 10 + 6
+OPS_PER_TRI = 45
+# HBM bytes each stage must move per ray (32-bit keys; see the design notes)
+BYTES_ENCODE = 32 + 4
+BYTES_GATHER = 4 + 32 + 32
+
+
+def sort_bytes_per_key(passes: int, key_bytes: int = 4) -> int:
+    """Histogram read + first pass (ids synthesised) + middle passes + last pass (perm only)."""
+    if passes <= 0:
+        return key_bytes + 4
+    if passes == 1:
+        return key_bytes + key_bytes + 4
+    return key_bytes + (key_bytes + key_bytes + 4) + (passes - 2) * 2 * (key_bytes + 4) + (key_bytes + 4 + 4)
+
+
+def active_digit_passes(keys_t, key_bits: int) -> int:
+    """8-bit digit passes whose digit is not the same for every key (the sort skips the others)."""
+    k = keys_t.cpu().numpy().view(np.uint32 if key_bits <= 32 else np.uint64).astype(np.uint64)
+    passes = 0
+    for p in range((key_bits + 7) // 8):
+        d = (k >> np.uint64(8 * p)) & np.uint64(255)
+        passes += int(not np.all(d == d[0]))
+    return passes
+
+
+# ----------------------------------------------------------- distributed
+
+def dist_env():
+    """(rank, world, local_rank) from the torchrun environment (1 process by default)."""
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def shard_seed(base_seed: int, rank: int) -> int:
+    """Each rank traces its own wavefront: same scene, its own ray samples."""
+    return base_seed + 1000 * rank
+
+
+def reduce_max(value: float, world: int) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.dev = device_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -------------------------------------------------------------- workload
+
+def make_workload(seed: int, quick: bool):
+    from paper_2305_16652_gb300 import gen
+    if quick:
+        return gen.room_workload(seed, target_tris=200_000, W=480, H=270, spp=8, shadow=False)
+    return gen.room_workload(seed, target_tris=1_000_000, W=1920, H=1080, spp=8, shadow=False)
+
+
+def peaks():
+    try:
+        p = json.load(open(PEAKS_FILE))
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, 2070.0, "fallback"
+
+
+def recorded_traffic():
+    """DRAM bytes per trace launch from a committed ncu summary, if the kernel is unchanged."""
+    try:
+        rec = json.load(open(TRAFFIC_FILE))
+        src = open(os.path.join(ROOT, "paper_2305_16652_gb300", "csrc", "trace.cu"), "rb").read()
+        if rec.get("trace_cu_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return rec.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------- our path
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2305_16652_gb300 import hcc
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = make_workload(shard_seed(1, rank), args.quick)
+    n = w.rays.n
+    K, C = args.key_bits, args.cut_size
+    ctx = hcc.hcc_create(local_rank)
+    bvh = hcc.hcc_bvh_upload(ctx, w.bvh)
+    cut = hcc.hcc_select_cut(ctx, bvh, C, 0.125)
+    hcc.hcc_reserve(ctx, n, K)
+    org = torch.from_numpy(w.rays.org).to(dev)
+    dir_ = torch.from_numpy(w.rays.dir).to(dev)
+    keys = torch.empty(n, dtype=torch.int32, device=dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    sorg, sdir = torch.empty_like(org), torch.empty_like(dir_)
+    hits = torch.empty((n, 4), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(method, ev=None):
+        """One wavefront through the C ABI; ev = 5 events around the 4 stages."""
+        if ev:
+            ev[0].record(stream)
+        if method == "nosort":
+            hcc.hcc_trace(ctx, bvh, org, dir_, hits)
+            if ev:
+                for e in ev[1:]:
+                    e.record(stream)
+            return
+        hcc.hcc_encode(ctx, method, bvh, cut if method == "hcc" else None, org, dir_, K, keys)
+        if ev:
+            ev[1].record(stream)
+        hcc.hcc_sort(ctx, keys, K, n, perm)
+        if ev:
+            ev[2].record(stream)
+        hcc.hcc_gather(ctx, org, dir_, perm, sorg, sdir)
+        if ev:
+            ev[3].record(stream)
+        hcc.hcc_trace(ctx, bvh, sorg, sdir, hits, scatter=perm)
+        if ev:
+            ev[4].record(stream)
+
+    def timed(method, steps, warmup):
+        for _ in range(warmup):
+            step(method)
+        hcc.hcc_sync(ctx)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(steps):
+            step(method, evs[i])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        hcc.hcc_sync(ctx)
+        barrier(world)
+        per = [evs[i][0].elapsed_time(evs[i][4]) for i in range(steps)]
+        stages = [[evs[i][s].elapsed_time(evs[i][s + 1]) for i in range(steps)] for s in range(4)]
+        gap = [evs[i][4].elapsed_time(evs[i + 1][0]) for i in range(steps - 1)]
+        total_ms = evs[0][0].elapsed_time(evs[-1][4])
+        return dict(per=per, stages=stages, total_ms=total_ms, wall_s=wall, gaps=gap)
+
+    # NoSort and TwoPoint first (context for the headline), then the HCC headline
+    others = {}
+    for method in ("nosort", "twopoint"):
+        r = timed(method, max(3, args.steps // 2), args.warmup)
+        t_max = reduce_max(r["total_ms"], world)
+        others[method] = dict(mrays_s=round(n * world * (len(r["per"])) / (t_max * 1e3), 2),
+                              ms_per_step=round(t_max / len(r["per"]), 3),
+                              stages_ms=[round(statistics.mean(s), 4) for s in r["stages"]])
+    with ClockSampler(local_rank) as clk:
+        r = timed("hcc", args.steps, args.warmup)
+    clocks = clk.summary()
+    t_max = reduce_max(r["total_ms"], world)
+    ms_step = t_max / args.steps
+    value = n * world * args.steps / (t_max * 1e3)  # Mrays/s over all ranks
+    per = sorted(r["per"])
+    p50 = statistics.median(per)
+    p99 = per[min(len(per) - 1, int(round(0.99 * (len(per) - 1))))]
+    st = [statistics.mean(s) for s in r["stages"]]
+
+    # e2e through the public host-buffer call: H2D rays, pipeline, D2H hits
+    h_org = torch.empty((n, 4), dtype=torch.float32, pin_memory=True)
+    h_dir = torch.empty((n, 4), dtype=torch.float32, pin_memory=True)
+    h_org.copy_(torch.from_numpy(w.rays.org))
+    h_dir.copy_(torch.from_numpy(w.rays.dir))
+    h_hits = torch.empty((n, 4), dtype=torch.int32, pin_memory=True)
+    a_org, a_dir, a_hits = h_org.numpy(), h_dir.numpy(), h_hits.numpy()
+    for _ in range(2):
+        hcc.hcc_run_host(ctx, "hcc", bvh, cut, a_org, a_dir, K, a_hits)
+    e2e_steps = max(3, min(args.steps, 10))
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        hcc.hcc_run_host(ctx, "hcc", bvh, cut, a_org, a_dir, K, a_hits)
+    e2e_s = reduce_max(time.perf_counter() - t0, world)
+    e2e_value = n * world * e2e_steps / (e2e_s * 1e6)
+
+    # parity of the timed path on a sample (sorted vs unsorted bit-identical)
+    step("hcc")
+    hcc.hcc_sync(ctx)
+    h_hcc = hits.clone()
+    step("nosort")
+    hcc.hcc_sync(ctx)
+    identical = bool(torch.equal(h_hcc, hits))
+
+    # work counts of the trace (order-independent per ray) for the ALU roofline
+    counts = hcc.hcc_trace_counts(ctx, bvh, org, dir_)
+    hbm, sm_max, peak_kind = peaks()
+    clk_mhz = clocks.get("sm_max_mhz") or sm_max
+    alu_peak = SMS * LANES_PER_SM * clk_mhz * 1e6 / 1e12  # Tops/s
+    trace_ms = st[3]
+    work = counts["node_visits"] * OPS_PER_NODE + counts["tri_tests"] * OPS_PER_TRI
+    achieved = work / (trace_ms * 1e-3) / 1e12
+    sort_passes = active_digit_passes(keys, K)
+    sb = sort_bytes_per_key(sort_passes)
+    stages = {
+        "encode": dict(ms=round(st[0], 4), bound="hbm", achieved_gbs=round(BYTES_ENCODE * n / (st[0] * 1e6), 1),
+                       frac=round(BYTES_ENCODE * n / (st[0] * 1e6) / hbm, 3)),
+        "sort": dict(ms=round(st[1], 4), bound="hbm", active_passes=sort_passes, bytes_per_key=sb,
+                     achieved_gbs=round(sb * n / (st[1] * 1e6), 1), frac=round(sb * n / (st[1] * 1e6) / hbm, 3)),
+        "gather": dict(ms=round(st[2], 4), bound="hbm", achieved_gbs=round(BYTES_GATHER * n / (st[2] * 1e6), 1),
+                       frac=round(BYTES_GATHER * n / (st[2] * 1e6) / hbm, 3)),
+        "trace": dict(ms=round(st[3], 4), bound="alu", achieved_tops=round(achieved, 3),
+                      frac=round(achieved / alu_peak, 3),
+                      node_visits_per_ray=round(counts["node_visits"] / n, 2),
+                      tri_tests_per_ray=round(counts["tri_tests"] / n, 2)),
+    }
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name + f" ({n} secondary rays), HCC cut {C}, {K}-bit keys",
+                   "rays": n, "triangles": int(w.tris.shape[0]), "cut_size": C, "key_bits": K, "lambda": 0.125,
+                   "l2": f"inputs larger than L2 ({n * 32 / 1e6:.0f} MB of rays per step)",
+                   "parallelism": f"replica per GPU x{world}"},
+        "p50_ms": round(p50, 4), "p99_ms": round(p99, 4),
+        "stages_ms": {"encode": round(st[0], 4), "sort": round(st[1], 4), "gather": round(st[2], 4),
+                      "trace": round(st[3], 4)},
+        "methods": {"hcc": {"mrays_s": round(value, 2), "ms_per_step": round(ms_step, 3)}, **others},
+        "speedup_vs_nosort": round(value / others["nosort"]["mrays_s"], 3),
+        "speedup_vs_twopoint": round(value / others["twopoint"]["mrays_s"], 3),
+        "hits_identical_hcc_vs_nosort": identical,
+        "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(n * 32),
+                "d2h_bytes_per_step": int(n * 16), "call": "hcc_run_host"},
+        "gpu_launches": 10 * args.steps,
+        "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 2), "unit": "Tops/s",
+                     "frac": round(achieved / alu_peak, 3), "traffic": recorded_traffic(),
+                     "kernel": "k_trace (closest hit, HCC order)",
+                     "peak_source": f"{SMS} SMs x {LANES_PER_SM} lanes x {clk_mhz:.0f} MHz"},
+        "stages": stages,
+        "hbm_peak_gbs": hbm, "hbm_peak_source": peak_kind,
+        "clocks": clocks,
+    }
+    hcc.hcc_cut_destroy(cut)
+    hcc.hcc_bvh_destroy(bvh)
+    hcc.hcc_destroy(ctx)
+    return out, w
+
+
+# ------------------------------------------------------- oracle (CPU) leg
+
+def oracle_sample(w, sample_n: int, seed: int = 7):
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(w.rays.n, size=min(sample_n, w.rays.n), replace=False))
+    return w.rays.org[idx].copy(), w.rays.dir[idx].copy()
+
+
+def oracle_step(w, cut_ids, org, dir_, key_bits):
+    import oracle
+    keys = oracle.encode_hcc(org, dir_, w.bvh.lo[cut_ids], w.bvh.hi[cut_ids], key_bits)
+    perm = oracle.stable_sort(keys)
+    so, sd = oracle.gather(org, dir_, perm)
+    oracle.trace_bvh(w.bvh, so, sd)
+
+
+def cpu_baseline(w, key_bits, cut_size, sample_n):
+    import oracle
+    cut_ids = oracle.select_cut(w.bvh, cut_size)
+    org, dir_ = oracle_sample(w, sample_n)
+    t0 = time.perf_counter()
+    oracle_step(w, cut_ids, org, dir_, key_bits)
+    dt = time.perf_counter() - t0
+    return {"value": round(org.shape[0] / dt / 1e6, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{org.shape[0]} seeded random rays of the same wavefront, encode+sort+gather+trace, "
+                      f"single-threaded C++ oracle, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    w = make_workload(1, args.quick)
+    import oracle
+    cut_ids = oracle.select_cut(w.bvh, args.cut_size)
+    org, dir_ = oracle_sample(w, args.ref_sample)
+    for _ in range(args.warmup):
+        oracle_step(w, cut_ids, org[:1000], dir_[:1000], args.key_bits)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(w, cut_ids, org, dir_, args.key_bits)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = org.shape[0] * len(times) / tot / 1e6
+    return {"metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * tot / len(times), 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
+            "config": {"workload": w.name + f" ({w.rays.n} secondary rays), HCC cut {args.cut_size}, "
+                                            f"{args.key_bits}-bit keys", "rays": w.rays.n},
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{org.shape[0]} seeded random rays per step, encode+sort+gather+trace"},
+            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cut-size", type=int, default=32)
+    ap.add_argument("--key-bits", type=int, default=32)
+    ap.add_argument("--quick", action="store_true", help="480x270 image, 200k triangles (development only)")
+    ap.add_argument("--cpu-sample", type=int, default=1_500_000)
+    ap.add_argument("--ref-sample", type=int, default=300_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    args.warmup = max(args.warmup, 3)
+    rank, world, local_rank = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if args.impl != "reference":
+            import torch
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            out = run_reference(args, rank, world)
+        else:
+            from paper_2305_16652_gb300 import build
+            build()
+            out, w = run_ours(args, rank, world, local_rank)
+            if rank == 0 and not args.no_cpu_baseline:
+                out["cpu_baseline"] = cpu_baseline(w, args.key_bits, args.cut_size, args.cpu_sample)
+        if rank == 0 and out is not None:
+            print(json.dumps(out), flush=True)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

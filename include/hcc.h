@@ -1,0 +1,290 @@
+/*
+ * hcc.h -- C ABI of the GB300 hierarchy-cut-code ray-reordering library.
+ *
+ * The library implements the reordering hot path of Xiang et al., "Faster
+ * Ray Tracing through Hierarchy Cut Code" (arXiv 2305.16652), Sec. 4.2 and
+ * Sec. 5: a cut of the BVH is chosen once per scene (Algorithm 2, Eq. 1),
+ * every ray gets a key from its intersections with the cut nodes
+ * (Algorithm 1), ray indices are sorted by key, the rays are fetched in
+ * sorted order and traced.  The paper's NoSort and TwoPoint baselines run
+ * behind the same calls.  Every step runs in hand-written CUDA kernels for
+ * sm_103a except cut selection, which the paper also performs once per scene
+ * on the host.
+ *
+ * Conventions shared by every call
+ *   - Status: every call returns an hcc_status; HCC_OK is 0.  Argument
+ *     errors are reported before anything is launched or written.  No call
+ *     aborts the process or throws across the ABI.
+ *   - Memory: ray, key, permutation and hit buffers are allocated by the
+ *     caller on the context's device and passed as plain device pointers;
+ *     the library never frees them.  Opaque handles (context, BVH, cut) are
+ *     owned by the library and released by their *_destroy call.  The
+ *     context owns its scratch memory (sort buffers, error word).
+ *   - Execution: calls that take device buffers are asynchronous on the
+ *     context's CUDA stream.  Errors found by kernels (traversal-stack
+ *     overflow, a bounded wait that gave up) are recorded in a device error
+ *     word and returned by the next hcc_sync.
+ *   - Threads: a context must not be used by two host threads at once; use
+ *     one context per host thread or stream.  BVH and cut handles are
+ *     read-only after creation and may be shared by contexts on the same
+ *     device.
+ *   - Sizes: n = 0 is a valid no-op everywhere.
+ */
+#ifndef HCC_H
+#define HCC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hcc_status {
+    HCC_OK = 0,
+    HCC_ERR_INVALID_ARG = 1,    /* null pointer, bad size, misaligned buffer, bad enum */
+    HCC_ERR_OOM = 2,            /* device or host allocation failed */
+    HCC_ERR_CUDA = 3,           /* a CUDA runtime call failed; see hcc_last_error */
+    HCC_ERR_UNSUPPORTED = 4,    /* valid request this build does not implement */
+    HCC_ERR_STACK_OVERFLOW = 5, /* a ray needed more traversal-stack entries than exist */
+    HCC_ERR_TIMEOUT = 6         /* a bounded device-side wait gave up */
+} hcc_status;
+
+/* Ray-ordering methods (Sec. 5 and Table 1 of the paper). */
+typedef enum hcc_method {
+    HCC_METHOD_NOSORT = 0,   /* trace in generation order (Table 1, NoSort) */
+    HCC_METHOD_HCC = 1,      /* hierarchy cut code (Sec. 4.2) */
+    HCC_METHOD_TWOPOINT = 2  /* origin + estimated termination Morton code (Sec. 3.2, Sec. 5) */
+} hcc_method;
+
+typedef struct hcc_ctx hcc_ctx; /* device, stream, scratch, device error word */
+typedef struct hcc_bvh hcc_bvh; /* device copy of a BVH2: quantised nodes, triangles */
+typedef struct hcc_cut hcc_cut; /* cut nodes in key order and their exact boxes */
+
+/*
+ * A BVH2 on the host (Sec. 3.1), read only during hcc_bvh_upload.
+ * Nodes are numbered so that node 0 is the root.  left[i] < 0 (and
+ * right[i] < 0) marks a leaf that owns order[first[i] .. first[i]+count[i]),
+ * 1 <= count <= 4; otherwise left/right are child node ids.  lo/hi: the
+ * node's axis-aligned box, 3 floats each, which must contain the node's
+ * triangles.  tris: num_tris triangles as 9 floats (v0, v1, v2); order holds
+ * triangle ids (indices into tris); hits report these ids.
+ */
+typedef struct hcc_bvh_desc {
+    uint32_t num_nodes;
+    const float *lo;       /* [num_nodes * 3] */
+    const float *hi;       /* [num_nodes * 3] */
+    const int32_t *left;   /* [num_nodes] */
+    const int32_t *right;  /* [num_nodes] */
+    const uint32_t *first; /* [num_nodes] */
+    const uint32_t *count; /* [num_nodes] */
+    uint32_t num_tris;
+    const float *tris;     /* [num_tris * 9] */
+    const uint32_t *order; /* [num_tris] */
+} hcc_bvh_desc;
+
+/*
+ * n rays on the device as two float4 streams (structure of arrays), each
+ * 16-byte aligned: org_tmin[i] = (ox, oy, oz, tmin), dir_tmax[i] =
+ * (dx, dy, dz, tmax).  A ray covers the parameter interval [tmin, tmax];
+ * tmax = +inf for an unbounded ray.  Directions need not be normalised.
+ */
+typedef struct hcc_rays {
+    float *org_tmin;
+    float *dir_tmax;
+    uint64_t n;
+} hcc_rays;
+
+/* One hit record (16 bytes): prim = triangle id or -1 for a miss (then t =
+ * +inf); u, v are the barycentric coordinates of the hit on (v0, v1, v2). */
+typedef struct hcc_hit {
+    int32_t prim;
+    float t, u, v;
+} hcc_hit;
+
+/* Largest ray count a single sort accepts (the look-back counters are 30-bit). */
+#define HCC_MAX_SORT_N ((uint64_t)((1u << 30) - 1u))
+/* Traversal-stack entries per ray in hcc_trace. */
+#define HCC_TRACE_STACK 64
+
+/* ------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` issuing work on `stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * handle.  Errors: INVALID_ARG (out NULL, bad device), CUDA, OOM. */
+hcc_status hcc_create(hcc_ctx **out, int device, void *stream);
+
+/* Release the context and its scratch after waiting for its stream. */
+hcc_status hcc_destroy(hcc_ctx *ctx);
+
+/* Replace the stream used by later calls. */
+hcc_status hcc_set_stream(hcc_ctx *ctx, void *stream);
+
+/* Pre-allocate sort and pipeline scratch for up to max_n rays and keys of
+ * up to max_key_bits bits, so that later calls allocate nothing.  Calls that
+ * need more scratch than reserved grow it themselves (a synchronising
+ * cudaMalloc).  Errors: INVALID_ARG, OOM. */
+hcc_status hcc_reserve(hcc_ctx *ctx, uint64_t max_n, uint32_t max_key_bits);
+
+/* Wait for all work queued on the context's stream, then read and clear the
+ * device error word: STACK_OVERFLOW or TIMEOUT if a kernel reported one
+ * since the last hcc_sync, INVALID_ARG if a gather or scatter met an index
+ * out of range, CUDA if the stream failed, else OK. */
+hcc_status hcc_sync(hcc_ctx *ctx);
+
+/* Text of the last error recorded on this context ("" if none).  The
+ * string is owned by the context and valid until its next call. */
+const char *hcc_last_error(const hcc_ctx *ctx);
+
+/* Static name of a status code. */
+const char *hcc_status_string(hcc_status s);
+
+/* ----------------------------------------------------------------- BVH */
+
+/* Copy a host BVH2 to the device in the traversal layout: every internal
+ * node becomes one 32-byte record holding both children's boxes quantised
+ * to 8 bits per bound and rounded outward (a superset of each exact box),
+ * triangles become (v0, v1 - v0, v2 - v0) records.  The exact boxes are kept
+ * on the host for cut selection.  Synchronous.  Errors: INVALID_ARG
+ * (malformed tree, leaf count outside 1..4, ids out of range), OOM, CUDA. */
+hcc_status hcc_bvh_upload(hcc_ctx *ctx, const hcc_bvh_desc *desc, hcc_bvh **out);
+
+/* Node and triangle counts, tree depth (root = 0) and the root box. Any
+ * output pointer may be NULL. */
+hcc_status hcc_bvh_info(const hcc_bvh *bvh, uint32_t *num_nodes, uint32_t *num_tris, uint32_t *depth,
+                        float *scene_lo3, float *scene_hi3);
+
+hcc_status hcc_bvh_destroy(hcc_bvh *bvh);
+
+/* -------------------------------------------------------- cut selection */
+
+/*
+ * Choose the cut (Sec. 4.2.2): compute the hierarchically accumulated
+ * density of every node (Eq. 1: TC * SA for a leaf, HAD_left + HAD_right +
+ * lambda * SA otherwise, in double), run the priority-queue search of
+ * Algorithm 2 with MaxQueueSize = cut_size (a popped leaf joins the cut and
+ * lowers MaxQueueSize by one), and order the cut by HAD, descending, ties by
+ * lower node id.  Cut node r drives key bit (key_bits - 1 - r) in hcc_encode.
+ * If the tree has fewer leaves than cut_size the cut is every leaf.  Runs on
+ * the host (once per scene, as in the paper) and copies the cut's exact
+ * boxes to the device.  The paper uses lambda = 0.125.
+ * Errors: INVALID_ARG (cut_size 0, lambda negative or not finite), OOM, CUDA.
+ */
+hcc_status hcc_select_cut(hcc_ctx *ctx, const hcc_bvh *bvh, uint32_t cut_size, double lambda, hcc_cut **out);
+
+/* Actual cut size and, if node_ids is not NULL, the cut's node ids in key
+ * order (node_ids must hold *size entries; call once with NULL to size it). */
+hcc_status hcc_cut_info(const hcc_cut *cut, uint32_t *size, int32_t *node_ids);
+
+hcc_status hcc_cut_destroy(hcc_cut *cut);
+
+/* ---------------------------------------------------------------- encode */
+
+/*
+ * One sort key per ray.  keys: n uint32_t if key_bits <= 32, else n
+ * uint64_t (device, aligned to its type); the key occupies the low key_bits
+ * bits, higher bits are 0.  key_bits in 1..64.
+ *   HCC (Algorithm 1): bit (key_bits - 1 - r) = [the ray meets cut node r's
+ *     box on [tmin, tmax]] for r < min(cut size, key_bits); other bits 0.
+ *     Slab test per axis t = (bound - o) * (1 / d) in IEEE float, inclusive
+ *     (tnear <= tfar).  Requires cut; bvh may be NULL.
+ *   TWOPOINT (Sec. 3.2, Sec. 5): origin and estimated termination point
+ *     o + L d, L = 0.25 * largest extent of the root box, each normalised to
+ *     the root box and quantised to floor(key_bits / 6) bits, interleaved
+ *     most significant level first in the order o.x o.y o.z t.x t.y t.z and
+ *     left-justified in key_bits.  Requires bvh; cut may be NULL.
+ *   NOSORT: INVALID_ARG (nothing to encode).
+ * Errors: INVALID_ARG, CUDA.
+ */
+hcc_status hcc_encode(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const hcc_cut *cut,
+                      const hcc_rays *rays, uint32_t key_bits, void *keys);
+
+/* ------------------------------------------------------------------ sort */
+
+/*
+ * Stable ascending sort of ray ids 0..n-1 by the low key_bits bits of keys
+ * (Sec. 4.2.3 "Sorting": keys sorted as natural numbers; Sec. 5: the sort
+ * orders ray indices).  perm[j] = id of the j-th ray in sorted order.
+ * keys: n uint32_t (key_bits <= 32) or uint64_t (key_bits > 32), device,
+ * not modified.  perm: n uint32_t, device, must not overlap keys.
+ * LSD radix sort, 8-bit digits; digits that are equal for every key are
+ * skipped, which leaves the result unchanged.  Scratch comes from the
+ * context (see hcc_reserve).  n <= HCC_MAX_SORT_N.
+ * Errors: INVALID_ARG, OOM, CUDA; TIMEOUT at hcc_sync if a bounded
+ * inter-block wait gave up (perm is then unspecified).
+ */
+hcc_status hcc_sort(hcc_ctx *ctx, const void *keys, uint32_t key_bits, uint64_t n, uint32_t *perm);
+
+/* ---------------------------------------------------------------- gather */
+
+/*
+ * out ray j = in ray perm[j] for j < n, both float4 streams, bit for bit
+ * (Sec. 5: the trace fetches rays through the sorted indices).  in->n is the
+ * number of valid source rays (every perm[j] must be below it); out->n is
+ * the count gathered.  in and out must not overlap.  An entry perm[j] >=
+ * in->n is never read through: out ray j is then zero and hcc_sync reports
+ * INVALID_ARG.
+ * Errors: INVALID_ARG, CUDA.
+ */
+hcc_status hcc_gather(hcc_ctx *ctx, const hcc_rays *in, const uint32_t *perm, const hcc_rays *out);
+
+/* ----------------------------------------------------------------- trace */
+
+/*
+ * Closest hit (any_hit = 0) or any hit (any_hit != 0) of every ray against
+ * the BVH's triangles by stack-based traversal of the quantised BVH2 and
+ * the Moller-Trumbore test (two-sided, no epsilon, hit when tmin < t <
+ * tmax).  Closest hit = smallest t, ties to the lower triangle id; it does
+ * not depend on traversal order.  Any hit reports some hit of the ray.
+ * Result of ray j goes to hits[j], or to hits[scatter[j]] when scatter is
+ * not NULL (scatter must then be a permutation of 0..n-1; an entry >= n is
+ * skipped and reported as INVALID_ARG by hcc_sync).  hits: n records,
+ * device, 16-byte aligned.
+ * Errors: INVALID_ARG, CUDA; STACK_OVERFLOW at hcc_sync if some ray needed
+ * more than HCC_TRACE_STACK entries (its record is then a miss).
+ */
+hcc_status hcc_trace(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *rays, int any_hit,
+                     const uint32_t *scatter, hcc_hit *hits);
+
+/*
+ * Diagnostic (never on the timed path): trace like hcc_trace without
+ * scatter and also count, over all rays, the internal BVH nodes visited and
+ * the triangle tests run.  A ray's counts depend only on the ray, not on
+ * its position in the batch, so they are the same for every ray order.
+ * Allocates a temporary hit buffer and waits for the stream; the counts are
+ * valid on return.  Errors: INVALID_ARG, OOM, CUDA.
+ */
+hcc_status hcc_trace_counts(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *rays, int any_hit,
+                            uint64_t *node_visits, uint64_t *tri_tests);
+
+/* ------------------------------------------------------- whole pipeline */
+
+/*
+ * The per-bounce reordering pipeline of Sec. 5 in one call:
+ *   NOSORT:   trace(rays) -> hits
+ *   HCC:      encode(cut) -> sort -> gather -> trace with scatter -> hits
+ *   TWOPOINT: encode(root box) -> sort -> gather -> trace with scatter -> hits
+ * hits[i] is always the result of input ray i, so every method produces
+ * the same array.  Keys, permutation and sorted rays live in the context's
+ * scratch.  Device pointers; asynchronous on the context's stream.
+ * Errors: as the individual calls.
+ */
+hcc_status hcc_run(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const hcc_cut *cut,
+                   const hcc_rays *rays, uint32_t key_bits, int any_hit, hcc_hit *hits);
+
+/*
+ * hcc_run on host memory: org_tmin and dir_tmax are n float4 each and hits
+ * n records, all in host memory (page-locked memory gives asynchronous,
+ * full-speed copies).  Copies the rays to device scratch, runs the
+ * pipeline, copies the hits back and waits for the stream, so the hits are
+ * valid on return.  Errors: as hcc_run, plus those of hcc_sync.
+ */
+hcc_status hcc_run_host(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const hcc_cut *cut,
+                        const float *org_tmin, const float *dir_tmax, uint64_t n, uint32_t key_bits, int any_hit,
+                        hcc_hit *hits);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HCC_H */

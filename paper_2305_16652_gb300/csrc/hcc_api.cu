@@ -1,0 +1,743 @@
+// C ABI of the hcc library: argument checking, device memory, the BVH
+// upload (quantised node layout), host-side cut selection (Sec. 4.2.2) and
+// the per-bounce pipeline (Sec. 5).  Kernels live in encode.cu, sort.cu,
+// gather.cu and trace.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hcc_internal.cuh"
+
+using namespace hcc;
+
+// ---------------------------------------------------------------- handles
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct hcc_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    uint32_t *d_err = nullptr;
+    std::string last_error;
+    DevBuf sort_scratch;
+    DevBuf keys, perm, sorted_org, sorted_dir;  // hcc_run
+    DevBuf in_org, in_dir, hits;                // hcc_run_host
+};
+
+struct hcc_bvh {
+    int device = 0;
+    uint4 *d_nodes = nullptr;
+    float4 *d_tris = nullptr;
+    uint32_t num_nodes = 0, num_internal = 0, num_tris = 0, depth = 0;
+    uint32_t root_ref = 0;
+    // exact tree kept on the host for cut selection
+    std::vector<float> lo, hi;
+    std::vector<int32_t> left, right;
+    std::vector<uint32_t> count;
+};
+
+struct hcc_cut {
+    int device = 0;
+    std::vector<int32_t> ids;
+    float4 *d_boxes = nullptr;  // (lo, hi) pairs in key order, at most 64 nodes
+    uint32_t on_device = 0;
+};
+
+namespace {
+
+constexpr uint32_t MAX_KEY_NODES = 64;
+
+hcc_status fail(hcc_ctx *ctx, hcc_status st, const char *fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->last_error = buf;
+    }
+    return st;
+}
+
+hcc_status cuda_fail(hcc_ctx *ctx, cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) return fail(ctx, HCC_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(ctx, HCC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Make ctx current on its device for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+hcc_status ensure(hcc_ctx *ctx, DevBuf &b, size_t bytes, const char *what) {
+    if (b.bytes >= bytes) return HCC_OK;
+    if (b.p) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "stream sync before growing scratch");
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes ? bytes : 256);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, HCC_ERR_OOM, "cudaMalloc of %zu bytes for %s failed", bytes, what);
+    }
+    b.p = p;
+    b.bytes = bytes;
+    return HCC_OK;
+}
+
+void release(DevBuf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+hcc_status check_rays(hcc_ctx *ctx, const hcc_rays *r, const char *name) {
+    if (!r) return fail(ctx, HCC_ERR_INVALID_ARG, "%s is NULL", name);
+    if (r->n == 0) return HCC_OK;
+    if (!r->org_tmin || !r->dir_tmax) return fail(ctx, HCC_ERR_INVALID_ARG, "%s has a NULL stream", name);
+    if (!aligned(r->org_tmin, 16) || !aligned(r->dir_tmax, 16))
+        return fail(ctx, HCC_ERR_INVALID_ARG, "%s streams must be 16-byte aligned", name);
+    if (r->n > (uint64_t)0xFFFFFFFFu) return fail(ctx, HCC_ERR_INVALID_ARG, "%s: n above 2^32-1", name);
+    return HCC_OK;
+}
+
+// ------------------------------------------------------ node quantisation
+
+// Round a float toward -inf to a value whose low 8 mantissa bits are zero.
+float round_down_24(float x) {
+    uint32_t b;
+    std::memcpy(&b, &x, 4);
+    if ((b & 0xFFu) == 0) return x;
+    if (!(x < 0.0f))
+        b &= ~0xFFu;
+    else
+        b = (b & ~0xFFu) + 0x100u;
+    float y;
+    std::memcpy(&y, &b, 4);
+    return y;
+}
+
+uint32_t float_bits(float x) {
+    uint32_t b;
+    std::memcpy(&b, &x, 4);
+    return b;
+}
+
+// Quantise the boxes of an internal node's two children (exact boxes lo/hi,
+// 3 floats each) into the 32-byte record described in hcc_internal.cuh.
+// Every decoded bound origin + q * 2^E is outside (or on) the exact bound.
+void quantise_node(const float *lo0, const float *hi0, const float *lo1, const float *hi1, uint32_t ref0,
+                   uint32_t ref1, uint32_t w[8]) {
+    uint8_t q[2][6];
+    for (int a = 0; a < 3; ++a) {
+        const float o = round_down_24(std::min(lo0[a], lo1[a]));
+        const double od = o;
+        const double top = std::max((double)hi0[a], (double)hi1[a]);
+        const double ext = top - od;
+        int E = -126;
+        if (ext > 0) {
+            int e2;
+            std::frexp(ext / 255.0, &e2);  // ext/255 in [2^(e2-1), 2^e2)
+            E = std::max(e2, -126);
+            while (E > -126 && std::ldexp(255.0, E - 1) >= ext) --E;
+            while (std::ldexp(255.0, E) < ext) ++E;
+        }
+        const double s = std::ldexp(1.0, E);
+        const float *los[2] = {lo0, lo1}, *his[2] = {hi0, hi1};
+        for (int c = 0; c < 2; ++c) {
+            double ql = std::floor(((double)los[c][a] - od) / s);
+            double qh = std::ceil(((double)his[c][a] - od) / s);
+            ql = std::min(std::max(ql, 0.0), 255.0);
+            qh = std::min(std::max(qh, 0.0), 255.0);
+            while (ql > 0 && od + ql * s > (double)los[c][a]) ql -= 1;
+            while (qh < 255 && od + qh * s < (double)his[c][a]) qh += 1;
+            q[c][a] = (uint8_t)ql;
+            q[c][3 + a] = (uint8_t)qh;
+        }
+        w[a] = (float_bits(o) & 0xFFFFFF00u) | (uint32_t)(E + 127);
+    }
+    // byte stream: child0 lo.xyz hi.xyz, child1 lo.xyz hi.xyz
+    uint8_t bytes[12];
+    for (int k = 0; k < 6; ++k) {
+        bytes[k] = q[0][k];
+        bytes[6 + k] = q[1][k];
+    }
+    for (int j = 0; j < 3; ++j)
+        w[3 + j] = (uint32_t)bytes[4 * j] | ((uint32_t)bytes[4 * j + 1] << 8) | ((uint32_t)bytes[4 * j + 2] << 16) |
+                   ((uint32_t)bytes[4 * j + 3] << 24);
+    w[6] = ref0;
+    w[7] = ref1;
+}
+
+// ---------------------------------------------------------- cut selection
+
+// Eq. 1 in double, children before parents (reverse of a pre-order walk).
+std::vector<double> compute_had(const hcc_bvh *b, double lambda) {
+    const uint32_t n = b->num_nodes;
+    std::vector<double> had(n, 0.0);
+    std::vector<int32_t> order;
+    order.reserve(n);
+    std::vector<int32_t> todo{0};
+    while (!todo.empty()) {
+        int32_t k = todo.back();
+        todo.pop_back();
+        order.push_back(k);
+        if (b->left[k] >= 0) {
+            todo.push_back(b->right[k]);
+            todo.push_back(b->left[k]);
+        }
+    }
+    for (auto it = order.rbegin(); it != order.rend(); ++it) {
+        const int32_t k = *it;
+        const double ex = (double)b->hi[3 * k] - (double)b->lo[3 * k];
+        const double ey = (double)b->hi[3 * k + 1] - (double)b->lo[3 * k + 1];
+        const double ez = (double)b->hi[3 * k + 2] - (double)b->lo[3 * k + 2];
+        const double sa = 2.0 * (ex * ey + ey * ez + ez * ex);
+        if (b->left[k] < 0)
+            had[k] = (double)b->count[k] * sa;
+        else
+            had[k] = (had[b->left[k]] + had[b->right[k]]) + lambda * sa;
+    }
+    return had;
+}
+
+// Max-heap of node ids by (HAD descending, id ascending).
+struct HadHeap {
+    const std::vector<double> &had;
+    std::vector<int32_t> a;
+    explicit HadHeap(const std::vector<double> &h) : had(h) {}
+    bool above(int32_t x, int32_t y) const { return had[x] > had[y] || (had[x] == had[y] && x < y); }
+    void push(int32_t v) {
+        a.push_back(v);
+        size_t i = a.size() - 1;
+        while (i > 0) {
+            size_t p = (i - 1) / 2;
+            if (!above(a[i], a[p])) break;
+            std::swap(a[i], a[p]);
+            i = p;
+        }
+    }
+    int32_t pop() {
+        int32_t top = a[0];
+        a[0] = a.back();
+        a.pop_back();
+        size_t i = 0;
+        for (;;) {
+            size_t l = 2 * i + 1, r = l + 1, m = i;
+            if (l < a.size() && above(a[l], a[m])) m = l;
+            if (r < a.size() && above(a[r], a[m])) m = r;
+            if (m == i) break;
+            std::swap(a[i], a[m]);
+            i = m;
+        }
+        return top;
+    }
+};
+
+}  // namespace
+
+// ================================================================== C ABI
+
+extern "C" {
+
+const char *hcc_status_string(hcc_status s) {
+    switch (s) {
+        case HCC_OK: return "HCC_OK";
+        case HCC_ERR_INVALID_ARG: return "HCC_ERR_INVALID_ARG";
+        case HCC_ERR_OOM: return "HCC_ERR_OOM";
+        case HCC_ERR_CUDA: return "HCC_ERR_CUDA";
+        case HCC_ERR_UNSUPPORTED: return "HCC_ERR_UNSUPPORTED";
+        case HCC_ERR_STACK_OVERFLOW: return "HCC_ERR_STACK_OVERFLOW";
+        case HCC_ERR_TIMEOUT: return "HCC_ERR_TIMEOUT";
+    }
+    return "HCC_ERR_UNKNOWN";
+}
+
+const char *hcc_last_error(const hcc_ctx *ctx) { return ctx ? ctx->last_error.c_str() : "NULL context"; }
+
+hcc_status hcc_create(hcc_ctx **out, int device, void *stream) {
+    if (!out) return HCC_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+        cudaGetLastError();
+        return HCC_ERR_CUDA;
+    }
+    if (device < 0 || device >= ndev) return HCC_ERR_INVALID_ARG;
+    hcc_ctx *c = new (std::nothrow) hcc_ctx;
+    if (!c) return HCC_ERR_OOM;
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(stream);
+    DeviceGuard g(device);
+    if (cudaMalloc(&c->d_err, sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return HCC_ERR_OOM;
+    }
+    if (cudaMemset(c->d_err, 0, sizeof(uint32_t)) != cudaSuccess) {
+        cudaFree(c->d_err);
+        delete c;
+        return HCC_ERR_CUDA;
+    }
+    *out = c;
+    return HCC_OK;
+}
+
+hcc_status hcc_destroy(hcc_ctx *ctx) {
+    if (!ctx) return HCC_ERR_INVALID_ARG;
+    {
+        DeviceGuard g(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+        for (DevBuf *b : {&ctx->sort_scratch, &ctx->keys, &ctx->perm, &ctx->sorted_org, &ctx->sorted_dir,
+                          &ctx->in_org, &ctx->in_dir, &ctx->hits})
+            release(*b);
+        if (ctx->d_err) cudaFree(ctx->d_err);
+    }
+    delete ctx;
+    return HCC_OK;
+}
+
+hcc_status hcc_set_stream(hcc_ctx *ctx, void *stream) {
+    if (!ctx) return HCC_ERR_INVALID_ARG;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    return HCC_OK;
+}
+
+hcc_status hcc_reserve(hcc_ctx *ctx, uint64_t max_n, uint32_t max_key_bits) {
+    if (!ctx) return HCC_ERR_INVALID_ARG;
+    if (max_key_bits < 1 || max_key_bits > 64) return fail(ctx, HCC_ERR_INVALID_ARG, "max_key_bits must be 1..64");
+    if (max_n > HCC_MAX_SORT_N) return fail(ctx, HCC_ERR_INVALID_ARG, "max_n above HCC_MAX_SORT_N");
+    DeviceGuard g(ctx->device);
+    const size_t ksz = max_key_bits > 32 ? 8 : 4;
+    hcc_status st;
+    if ((st = ensure(ctx, ctx->sort_scratch, sort_scratch_bytes(max_n, max_key_bits), "sort scratch")) != HCC_OK)
+        return st;
+    if ((st = ensure(ctx, ctx->keys, max_n * ksz, "keys")) != HCC_OK) return st;
+    if ((st = ensure(ctx, ctx->perm, max_n * 4, "perm")) != HCC_OK) return st;
+    if ((st = ensure(ctx, ctx->sorted_org, max_n * 16, "sorted rays")) != HCC_OK) return st;
+    if ((st = ensure(ctx, ctx->sorted_dir, max_n * 16, "sorted rays")) != HCC_OK) return st;
+    return HCC_OK;
+}
+
+hcc_status hcc_sync(hcc_ctx *ctx) {
+    if (!ctx) return HCC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+    uint32_t err = 0;
+    e = cudaMemcpy(&err, ctx->d_err, sizeof err, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reading the device error word");
+    if (err) {
+        e = cudaMemset(ctx->d_err, 0, sizeof(uint32_t));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "clearing the device error word");
+        if (err & ERR_STACK)
+            return fail(ctx, HCC_ERR_STACK_OVERFLOW, "a ray needed more than %d traversal-stack entries",
+                        HCC_TRACE_STACK);
+        if (err & ERR_TIMEOUT) return fail(ctx, HCC_ERR_TIMEOUT, "a bounded wait in the sort gave up");
+        if (err & ERR_INDEX)
+            return fail(ctx, HCC_ERR_INVALID_ARG, "a permutation or scatter entry was out of range (skipped)");
+    }
+    return HCC_OK;
+}
+
+// ------------------------------------------------------------------- BVH
+
+hcc_status hcc_bvh_upload(hcc_ctx *ctx, const hcc_bvh_desc *d, hcc_bvh **out) {
+    if (!ctx || !d || !out) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (d->num_nodes == 0 || d->num_tris == 0) return fail(ctx, HCC_ERR_INVALID_ARG, "empty BVH");
+    if (!d->lo || !d->hi || !d->left || !d->right || !d->first || !d->count || !d->tris || !d->order)
+        return fail(ctx, HCC_ERR_INVALID_ARG, "NULL array in hcc_bvh_desc");
+    if (d->num_nodes > 0x7FFFFFFFu || d->num_tris > REF_TRI_MASK)
+        return fail(ctx, HCC_ERR_INVALID_ARG, "BVH too large for the node layout");
+    const uint32_t N = d->num_nodes, T = d->num_tris;
+    for (uint32_t k = 0; k < T; ++k)
+        if (d->order[k] >= T) return fail(ctx, HCC_ERR_INVALID_ARG, "order[%u] out of range", k);
+    // walk the tree from the root: validates structure, numbers internal nodes
+    // in pre-order and measures the depth
+    std::vector<int32_t> qidx(N, -1);
+    std::vector<uint8_t> seen(N, 0);
+    std::vector<std::pair<int32_t, uint32_t>> todo{{0, 0u}};
+    std::vector<int32_t> internal;
+    uint32_t depth = 0;
+    while (!todo.empty()) {
+        auto [k, dep] = todo.back();
+        todo.pop_back();
+        if (seen[k]) return fail(ctx, HCC_ERR_INVALID_ARG, "node %d reached twice", k);
+        seen[k] = 1;
+        depth = std::max(depth, dep);
+        const int32_t l = d->left[k], r = d->right[k];
+        if (l < 0 || r < 0) {
+            if (l >= 0 || r >= 0) return fail(ctx, HCC_ERR_INVALID_ARG, "node %d has one child", k);
+            if (d->count[k] < 1 || d->count[k] > 4)
+                return fail(ctx, HCC_ERR_INVALID_ARG, "leaf %d holds %u triangles (1..4 allowed)", k, d->count[k]);
+            if ((uint64_t)d->first[k] + d->count[k] > T)
+                return fail(ctx, HCC_ERR_INVALID_ARG, "leaf %d range out of bounds", k);
+            continue;
+        }
+        if ((uint32_t)l >= N || (uint32_t)r >= N || l == r)
+            return fail(ctx, HCC_ERR_INVALID_ARG, "node %d has bad children", k);
+        qidx[k] = (int32_t)internal.size();
+        internal.push_back(k);
+        todo.push_back({r, dep + 1});
+        todo.push_back({l, dep + 1});
+    }
+    auto ref_of = [&](int32_t k) -> uint32_t {
+        if (d->left[k] < 0) return REF_LEAF | ((d->count[k] - 1u) << 29) | d->first[k];
+        return (uint32_t)qidx[k];
+    };
+    std::vector<uint32_t> words((size_t)std::max<size_t>(internal.size(), 1) * 8, 0u);
+    for (size_t i = 0; i < internal.size(); ++i) {
+        const int32_t k = internal[i], l = d->left[k], r = d->right[k];
+        quantise_node(d->lo + 3 * l, d->hi + 3 * l, d->lo + 3 * r, d->hi + 3 * r, ref_of(l), ref_of(r), &words[8 * i]);
+    }
+    std::vector<float> tri((size_t)T * 12);
+    for (uint32_t k = 0; k < T; ++k) {
+        const uint32_t id = d->order[k];
+        const float *v = d->tris + 9 * (size_t)id;
+        float *o = &tri[12 * (size_t)k];
+        o[0] = v[0];
+        o[1] = v[1];
+        o[2] = v[2];
+        std::memcpy(&o[3], &id, 4);
+        for (int a = 0; a < 3; ++a) {
+            o[4 + a] = v[3 + a] - v[a];
+            o[8 + a] = v[6 + a] - v[a];
+        }
+        o[7] = 0.0f;
+        o[11] = 0.0f;
+    }
+    hcc_bvh *b = new (std::nothrow) hcc_bvh;
+    if (!b) return fail(ctx, HCC_ERR_OOM, "host allocation");
+    b->device = ctx->device;
+    b->num_nodes = N;
+    b->num_internal = (uint32_t)internal.size();
+    b->num_tris = T;
+    b->depth = depth;
+    b->root_ref = ref_of(0);
+    b->lo.assign(d->lo, d->lo + 3 * (size_t)N);
+    b->hi.assign(d->hi, d->hi + 3 * (size_t)N);
+    b->left.assign(d->left, d->left + N);
+    b->right.assign(d->right, d->right + N);
+    b->count.assign(d->count, d->count + N);
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaMalloc(&b->d_nodes, words.size() * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_tris, tri.size() * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_nodes, words.data(), words.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_tris, tri.data(), tri.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        hcc_bvh_destroy(b);
+        return cuda_fail(ctx, e, "BVH upload");
+    }
+    *out = b;
+    return HCC_OK;
+}
+
+hcc_status hcc_bvh_info(const hcc_bvh *b, uint32_t *num_nodes, uint32_t *num_tris, uint32_t *depth, float *lo3,
+                        float *hi3) {
+    if (!b) return HCC_ERR_INVALID_ARG;
+    if (num_nodes) *num_nodes = b->num_nodes;
+    if (num_tris) *num_tris = b->num_tris;
+    if (depth) *depth = b->depth;
+    for (int a = 0; a < 3; ++a) {
+        if (lo3) lo3[a] = b->lo[a];
+        if (hi3) hi3[a] = b->hi[a];
+    }
+    return HCC_OK;
+}
+
+hcc_status hcc_bvh_destroy(hcc_bvh *b) {
+    if (!b) return HCC_ERR_INVALID_ARG;
+    {
+        DeviceGuard g(b->device);
+        if (b->d_nodes) cudaFree(b->d_nodes);
+        if (b->d_tris) cudaFree(b->d_tris);
+    }
+    delete b;
+    return HCC_OK;
+}
+
+// ------------------------------------------------------------------- cut
+
+hcc_status hcc_select_cut(hcc_ctx *ctx, const hcc_bvh *bvh, uint32_t cut_size, double lambda, hcc_cut **out) {
+    if (!ctx || !bvh || !out) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (cut_size == 0) return fail(ctx, HCC_ERR_INVALID_ARG, "cut_size must be positive");
+    if (!(lambda >= 0.0) || !std::isfinite(lambda))
+        return fail(ctx, HCC_ERR_INVALID_ARG, "lambda must be finite and non-negative");
+    const std::vector<double> had = compute_had(bvh, lambda);
+    // Algorithm 2
+    HadHeap pq(had);
+    std::vector<int32_t> cut;
+    uint32_t max_queue = cut_size;
+    pq.push(0);
+    while (!pq.a.empty() && pq.a.size() < max_queue) {
+        const int32_t k = pq.pop();
+        if (bvh->left[k] < 0) {
+            cut.push_back(k);
+            --max_queue;
+        } else {
+            pq.push(bvh->left[k]);
+            pq.push(bvh->right[k]);
+        }
+    }
+    cut.insert(cut.end(), pq.a.begin(), pq.a.end());
+    std::sort(cut.begin(), cut.end(),
+              [&](int32_t x, int32_t y) { return had[x] > had[y] || (had[x] == had[y] && x < y); });
+    hcc_cut *c = new (std::nothrow) hcc_cut;
+    if (!c) return fail(ctx, HCC_ERR_OOM, "host allocation");
+    c->device = ctx->device;
+    c->ids = cut;
+    c->on_device = (uint32_t)std::min<size_t>(cut.size(), MAX_KEY_NODES);
+    std::vector<float4> boxes(2 * (size_t)std::max<uint32_t>(c->on_device, 1));
+    for (uint32_t r = 0; r < c->on_device; ++r) {
+        const int32_t k = cut[r];
+        boxes[2 * r] = make_float4(bvh->lo[3 * k], bvh->lo[3 * k + 1], bvh->lo[3 * k + 2], 0.0f);
+        boxes[2 * r + 1] = make_float4(bvh->hi[3 * k], bvh->hi[3 * k + 1], bvh->hi[3 * k + 2], 0.0f);
+    }
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaMalloc(&c->d_boxes, boxes.size() * sizeof(float4));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_boxes, boxes.data(), boxes.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        hcc_cut_destroy(c);
+        return cuda_fail(ctx, e, "cut upload");
+    }
+    *out = c;
+    return HCC_OK;
+}
+
+hcc_status hcc_cut_info(const hcc_cut *cut, uint32_t *size, int32_t *node_ids) {
+    if (!cut || !size) return HCC_ERR_INVALID_ARG;
+    *size = (uint32_t)cut->ids.size();
+    if (node_ids) std::memcpy(node_ids, cut->ids.data(), cut->ids.size() * sizeof(int32_t));
+    return HCC_OK;
+}
+
+hcc_status hcc_cut_destroy(hcc_cut *cut) {
+    if (!cut) return HCC_ERR_INVALID_ARG;
+    {
+        DeviceGuard g(cut->device);
+        if (cut->d_boxes) cudaFree(cut->d_boxes);
+    }
+    delete cut;
+    return HCC_OK;
+}
+
+// ---------------------------------------------------------------- encode
+
+hcc_status hcc_encode(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const hcc_cut *cut,
+                      const hcc_rays *rays, uint32_t key_bits, void *keys) {
+    if (!ctx) return HCC_ERR_INVALID_ARG;
+    hcc_status st = check_rays(ctx, rays, "rays");
+    if (st != HCC_OK) return st;
+    if (key_bits < 1 || key_bits > 64) return fail(ctx, HCC_ERR_INVALID_ARG, "key_bits must be 1..64");
+    if (method != HCC_METHOD_HCC && method != HCC_METHOD_TWOPOINT)
+        return fail(ctx, HCC_ERR_INVALID_ARG, "hcc_encode needs HCC or TWOPOINT");
+    if (method == HCC_METHOD_HCC && !cut) return fail(ctx, HCC_ERR_INVALID_ARG, "HCC needs a cut");
+    if (method == HCC_METHOD_TWOPOINT && !bvh) return fail(ctx, HCC_ERR_INVALID_ARG, "TWOPOINT needs the BVH");
+    if (rays->n == 0) return HCC_OK;
+    if (!keys || !aligned(keys, key_bits > 32 ? 8 : 4))
+        return fail(ctx, HCC_ERR_INVALID_ARG, "keys NULL or misaligned");
+    DeviceGuard g(ctx->device);
+    const float4 *o = reinterpret_cast<const float4 *>(rays->org_tmin);
+    const float4 *d = reinterpret_cast<const float4 *>(rays->dir_tmax);
+    cudaError_t e;
+    if (method == HCC_METHOD_HCC) {
+        const uint32_t used = std::min<uint32_t>(cut->on_device, key_bits);
+        e = launch_encode_hcc(ctx->stream, o, d, rays->n, cut->d_boxes, used, key_bits, keys);
+    } else {
+        float lo[3], ext[3];
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = bvh->lo[a];
+            ext[a] = bvh->hi[a] - bvh->lo[a];
+        }
+        const float L = 0.25f * std::max(ext[0], std::max(ext[1], ext[2]));
+        e = launch_encode_twopoint(ctx->stream, o, d, rays->n, lo, ext, L, key_bits, keys);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "encode launch");
+    return HCC_OK;
+}
+
+// ------------------------------------------------------------------ sort
+
+hcc_status hcc_sort(hcc_ctx *ctx, const void *keys, uint32_t key_bits, uint64_t n, uint32_t *perm) {
+    if (!ctx) return HCC_ERR_INVALID_ARG;
+    if (key_bits < 1 || key_bits > 64) return fail(ctx, HCC_ERR_INVALID_ARG, "key_bits must be 1..64");
+    if (n > HCC_MAX_SORT_N) return fail(ctx, HCC_ERR_INVALID_ARG, "n above HCC_MAX_SORT_N");
+    if (n == 0) return HCC_OK;
+    const size_t ksz = key_bits > 32 ? 8 : 4;
+    if (!keys || !perm || !aligned(keys, ksz) || !aligned(perm, 4))
+        return fail(ctx, HCC_ERR_INVALID_ARG, "keys/perm NULL or misaligned");
+    const uintptr_t k0 = (uintptr_t)keys, k1 = k0 + n * ksz, p0 = (uintptr_t)perm, p1 = p0 + n * 4;
+    if (k0 < p1 && p0 < k1) return fail(ctx, HCC_ERR_INVALID_ARG, "keys and perm overlap");
+    DeviceGuard g(ctx->device);
+    hcc_status st = ensure(ctx, ctx->sort_scratch, sort_scratch_bytes(n, key_bits), "sort scratch");
+    if (st != HCC_OK) return st;
+    cudaError_t e = launch_sort(ctx->stream, keys, key_bits, n, perm, ctx->sort_scratch.p, ctx->d_err);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sort launch");
+    return HCC_OK;
+}
+
+// ---------------------------------------------------------------- gather
+
+hcc_status hcc_gather(hcc_ctx *ctx, const hcc_rays *in, const uint32_t *perm, const hcc_rays *out) {
+    if (!ctx) return HCC_ERR_INVALID_ARG;
+    hcc_status st;
+    if ((st = check_rays(ctx, in, "in")) != HCC_OK) return st;
+    if ((st = check_rays(ctx, out, "out")) != HCC_OK) return st;
+    if (out->n == 0) return HCC_OK;
+    if (!perm || !aligned(perm, 4)) return fail(ctx, HCC_ERR_INVALID_ARG, "perm NULL or misaligned");
+    if (in->n == 0) return fail(ctx, HCC_ERR_INVALID_ARG, "gather from an empty ray set");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = launch_gather(ctx->stream, reinterpret_cast<const float4 *>(in->org_tmin),
+                                  reinterpret_cast<const float4 *>(in->dir_tmax), in->n, perm,
+                                  reinterpret_cast<float4 *>(out->org_tmin), reinterpret_cast<float4 *>(out->dir_tmax),
+                                  out->n, ctx->d_err);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gather launch");
+    return HCC_OK;
+}
+
+// ----------------------------------------------------------------- trace
+
+hcc_status hcc_trace(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *rays, int any_hit, const uint32_t *scatter,
+                     hcc_hit *hits) {
+    if (!ctx) return HCC_ERR_INVALID_ARG;
+    hcc_status st = check_rays(ctx, rays, "rays");
+    if (st != HCC_OK) return st;
+    if (!bvh) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL BVH");
+    if (rays->n == 0) return HCC_OK;
+    if (!hits || !aligned(hits, 16)) return fail(ctx, HCC_ERR_INVALID_ARG, "hits NULL or not 16-byte aligned");
+    if (scatter && !aligned(scatter, 4)) return fail(ctx, HCC_ERR_INVALID_ARG, "scatter misaligned");
+    DeviceGuard g(ctx->device);
+    TraceArgs a;
+    a.nodes = bvh->d_nodes;
+    a.tris = bvh->d_tris;
+    a.root_ref = bvh->root_ref;
+    a.org = reinterpret_cast<const float4 *>(rays->org_tmin);
+    a.dir = reinterpret_cast<const float4 *>(rays->dir_tmax);
+    a.n = rays->n;
+    a.scatter = scatter;
+    a.hits = reinterpret_cast<int4 *>(hits);
+    a.err = ctx->d_err;
+    a.counts = nullptr;
+    cudaError_t e = launch_trace(ctx->stream, a, any_hit);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "trace launch");
+    return HCC_OK;
+}
+
+hcc_status hcc_trace_counts(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *rays, int any_hit,
+                            uint64_t *node_visits, uint64_t *tri_tests) {
+    if (!ctx) return HCC_ERR_INVALID_ARG;
+    hcc_status st = check_rays(ctx, rays, "rays");
+    if (st != HCC_OK) return st;
+    if (!bvh || !node_visits || !tri_tests) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL argument");
+    *node_visits = 0;
+    *tri_tests = 0;
+    if (rays->n == 0) return HCC_OK;
+    DeviceGuard g(ctx->device);
+    DevBuf tmp;
+    if ((st = ensure(ctx, tmp, rays->n * sizeof(hcc_hit) + 256, "counting trace output")) != HCC_OK) return st;
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(static_cast<char *>(tmp.p) +
+                                                                     rays->n * sizeof(hcc_hit));
+    cudaError_t e = cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), ctx->stream);
+    TraceArgs a;
+    a.nodes = bvh->d_nodes;
+    a.tris = bvh->d_tris;
+    a.root_ref = bvh->root_ref;
+    a.org = reinterpret_cast<const float4 *>(rays->org_tmin);
+    a.dir = reinterpret_cast<const float4 *>(rays->dir_tmax);
+    a.n = rays->n;
+    a.scatter = nullptr;
+    a.hits = reinterpret_cast<int4 *>(tmp.p);
+    a.err = ctx->d_err;
+    a.counts = cnt;
+    if (e == cudaSuccess) e = launch_trace(ctx->stream, a, any_hit);
+    unsigned long long host[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, cnt, sizeof host, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    release(tmp);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "counting trace");
+    *node_visits = host[0];
+    *tri_tests = host[1];
+    return HCC_OK;
+}
+
+// -------------------------------------------------------------- pipeline
+
+hcc_status hcc_run(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const hcc_cut *cut, const hcc_rays *rays,
+                   uint32_t key_bits, int any_hit, hcc_hit *hits) {
+    if (!ctx) return HCC_ERR_INVALID_ARG;
+    hcc_status st = check_rays(ctx, rays, "rays");
+    if (st != HCC_OK) return st;
+    if (!bvh) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL BVH");
+    if (method != HCC_METHOD_NOSORT && method != HCC_METHOD_HCC && method != HCC_METHOD_TWOPOINT)
+        return fail(ctx, HCC_ERR_INVALID_ARG, "unknown method");
+    if (rays->n == 0) return HCC_OK;
+    if (method == HCC_METHOD_NOSORT) return hcc_trace(ctx, bvh, rays, any_hit, nullptr, hits);
+    if (key_bits < 1 || key_bits > 64) return fail(ctx, HCC_ERR_INVALID_ARG, "key_bits must be 1..64");
+    if (method == HCC_METHOD_HCC && !cut) return fail(ctx, HCC_ERR_INVALID_ARG, "HCC needs a cut");
+    const uint64_t n = rays->n;
+    if (n > HCC_MAX_SORT_N) return fail(ctx, HCC_ERR_INVALID_ARG, "n above HCC_MAX_SORT_N");
+    DeviceGuard g(ctx->device);
+    const size_t ksz = key_bits > 32 ? 8 : 4;
+    if ((st = ensure(ctx, ctx->keys, n * ksz, "keys")) != HCC_OK) return st;
+    if ((st = ensure(ctx, ctx->perm, n * 4, "perm")) != HCC_OK) return st;
+    if ((st = ensure(ctx, ctx->sorted_org, n * 16, "sorted rays")) != HCC_OK) return st;
+    if ((st = ensure(ctx, ctx->sorted_dir, n * 16, "sorted rays")) != HCC_OK) return st;
+    if ((st = hcc_encode(ctx, method, bvh, cut, rays, key_bits, ctx->keys.p)) != HCC_OK) return st;
+    uint32_t *perm = static_cast<uint32_t *>(ctx->perm.p);
+    if ((st = hcc_sort(ctx, ctx->keys.p, key_bits, n, perm)) != HCC_OK) return st;
+    hcc_rays sorted{static_cast<float *>(ctx->sorted_org.p), static_cast<float *>(ctx->sorted_dir.p), n};
+    if ((st = hcc_gather(ctx, rays, perm, &sorted)) != HCC_OK) return st;
+    return hcc_trace(ctx, bvh, &sorted, any_hit, perm, hits);
+}
+
+hcc_status hcc_run_host(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const hcc_cut *cut,
+                        const float *org_tmin, const float *dir_tmax, uint64_t n, uint32_t key_bits, int any_hit,
+                        hcc_hit *hits) {
+    if (!ctx) return HCC_ERR_INVALID_ARG;
+    if (n == 0) return HCC_OK;
+    if (!org_tmin || !dir_tmax || !hits) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL host buffer");
+    if (n > HCC_MAX_SORT_N) return fail(ctx, HCC_ERR_INVALID_ARG, "n above HCC_MAX_SORT_N");
+    DeviceGuard g(ctx->device);
+    hcc_status st;
+    if ((st = ensure(ctx, ctx->in_org, n * 16, "input rays")) != HCC_OK) return st;
+    if ((st = ensure(ctx, ctx->in_dir, n * 16, "input rays")) != HCC_OK) return st;
+    if ((st = ensure(ctx, ctx->hits, n * sizeof(hcc_hit), "hits")) != HCC_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(ctx->in_org.p, org_tmin, n * 16, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->in_dir.p, dir_tmax, n * 16, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "host-to-device copy of rays");
+    hcc_rays r{static_cast<float *>(ctx->in_org.p), static_cast<float *>(ctx->in_dir.p), n};
+    if ((st = hcc_run(ctx, method, bvh, cut, &r, key_bits, any_hit, static_cast<hcc_hit *>(ctx->hits.p))) != HCC_OK)
+        return st;
+    e = cudaMemcpyAsync(hits, ctx->hits.p, n * sizeof(hcc_hit), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "device-to-host copy of hits");
+    return hcc_sync(ctx);
+}
+
+}  // extern "C"

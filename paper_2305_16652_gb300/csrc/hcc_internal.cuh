@@ -1,0 +1,69 @@
+// Internal declarations of the hcc library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hcc.h"
+
+namespace hcc {
+
+// Bits of the per-context device error word.
+constexpr uint32_t ERR_STACK = 1u;
+constexpr uint32_t ERR_TIMEOUT = 2u;
+constexpr uint32_t ERR_INDEX = 4u;  // a permutation entry was out of range (access skipped)
+
+// ----------------------------------------------------------------- BVH layout
+//
+// One internal BVH2 node = 32 bytes = two uint4 (w0..w7):
+//   w0..w2  node origin x/y/z: a float whose low 8 mantissa bits are cleared
+//           (rounded toward -inf), with the biased exponent E+127 of the
+//           quantisation step 2^E of that axis stored in those 8 bits
+//   w3      child0 lo.x lo.y lo.z hi.x   (one byte each, low byte first)
+//   w4      child0 hi.y hi.z, child1 lo.x lo.y
+//   w5      child1 lo.z hi.x hi.y hi.z
+//   w6, w7  child references
+// A decoded bound is origin + q * 2^E, computed with outward rounding, so the
+// decoded box always contains the child's exact box.
+// Child reference: bit 31 set = leaf, bits 29..30 = triangle count - 1,
+// bits 0..28 = first triangle record; bit 31 clear = internal node index.
+constexpr uint32_t REF_LEAF = 0x80000000u;
+constexpr uint32_t REF_TRI_MASK = 0x1FFFFFFFu;
+
+// Triangle record = three float4: (v0.xyz, id bits), (e1.xyz, 0), (e2.xyz, 0)
+// with e1 = v1 - v0, e2 = v2 - v0 rounded to float.
+
+// ------------------------------------------------------------------ launchers
+// All return the launch error (cudaSuccess when queued).
+
+cudaError_t launch_encode_hcc(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n,
+                              const float4 *cut_boxes, uint32_t used, uint32_t key_bits, void *keys);
+
+cudaError_t launch_encode_twopoint(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n,
+                                   const float lo[3], const float ext[3], float L, uint32_t key_bits, void *keys);
+
+// Radix sort scratch bytes for n keys of key_bits bits.
+size_t sort_scratch_bytes(uint64_t n, uint32_t key_bits);
+
+cudaError_t launch_sort(cudaStream_t s, const void *keys, uint32_t key_bits, uint64_t n, uint32_t *perm,
+                        void *scratch, uint32_t *err_word);
+
+cudaError_t launch_gather(cudaStream_t s, const float4 *in_org, const float4 *in_dir, uint64_t in_n,
+                          const uint32_t *perm, float4 *out_org, float4 *out_dir, uint64_t n, uint32_t *err);
+
+struct TraceArgs {
+    const uint4 *nodes;  // 2 per node
+    const float4 *tris;  // 3 per triangle
+    uint32_t root_ref;
+    const float4 *org;
+    const float4 *dir;
+    uint64_t n;
+    const uint32_t *scatter;
+    int4 *hits;
+    uint32_t *err;
+    unsigned long long *counts;  // diagnostic: node visits, triangle tests (NULL = off)
+};
+
+cudaError_t launch_trace(cudaStream_t s, const TraceArgs &a, int any_hit);
+
+}  // namespace hcc

@@ -1,0 +1,370 @@
+// Stable LSD radix sort of ray ids by key (Sec. 4.2.3 "Sorting": keys are
+// sorted as natural numbers; Sec. 5: the sort orders ray indices).
+//
+// Design (one pass per 8-bit digit, "onesweep" structure):
+//   k_hist   one read of every key builds the digit histograms of all passes
+//   k_plan   exclusive scan of each histogram; passes whose digit is the same
+//            for every key are marked inactive (skipping them cannot change a
+//            stable result); the ping-pong buffer of every active pass is
+//            chosen so that the first active pass reads the caller's keys and
+//            synthesises ids, and the last one writes only the permutation
+//   k_pass   per 4096-key tile: warp-level ranking with match.any, per-digit
+//            tile counts published to a decoupled look-back chain (bounded
+//            waits), keys reordered in shared memory and written out in runs
+//            of equal digits (coalesced)
+//   k_ident  perm = identity when no pass is active (all keys equal, n <= 1)
+// Tiles take their position from an atomic counter in launch order, so a tile
+// only ever waits for tiles that are already running.
+#include "hcc_internal.cuh"
+
+namespace hcc {
+namespace {
+
+constexpr int RADIX = 256;
+constexpr int MAX_PASSES = 8;
+constexpr int SORT_BLOCK = 256;  // one thread per digit in the scan / look-back
+constexpr int SORT_WARPS = SORT_BLOCK / 32;
+constexpr int SORT_ITEMS = 16;
+constexpr int SORT_TILE = SORT_BLOCK * SORT_ITEMS;
+constexpr uint32_t ST_AGG = 1u << 30;  // tile count of this digit available
+constexpr uint32_t ST_INC = 2u << 30;  // inclusive prefix of this digit available
+constexpr uint32_t ST_VALUE = (1u << 30) - 1u;
+constexpr uint32_t SPIN_LIMIT = 1u << 22;
+
+enum : int { KB_USER = 0, KB_A = 1, KB_B = 2, KB_NONE = 3 };
+enum : int { VB_SYNTH = 0, VB_A = 1, VB_PERM = 2 };
+
+struct PassPlan {
+    int active, src_keys, dst_keys, src_vals, dst_vals, pad[3];
+};
+
+// Scratch header, followed by the status words [passes][tiles][RADIX] and
+// the ping-pong buffers.
+struct SortHeader {
+    uint32_t hist[MAX_PASSES][RADIX];
+    uint32_t start[MAX_PASSES][RADIX];
+    PassPlan plan[MAX_PASSES];
+    uint32_t tile_counter[MAX_PASSES];
+    uint32_t identity;
+    uint32_t abort;
+    uint32_t pad[14];
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t header, status, ka, kb, va, total;
+};
+
+Layout layout(uint64_t n, uint32_t key_bits) {
+    const uint32_t passes = (key_bits + 7) / 8;
+    const uint64_t tiles = (n + SORT_TILE - 1) / SORT_TILE;
+    const size_t ksz = key_bits > 32 ? 8 : 4;
+    Layout L;
+    L.header = 0;
+    L.status = align256(sizeof(SortHeader));
+    L.ka = L.status + align256((size_t)passes * tiles * RADIX * sizeof(uint32_t));
+    L.kb = L.ka + align256(n * ksz);
+    L.va = L.kb + align256(n * ksz);
+    L.total = L.va + align256(n * sizeof(uint32_t));
+    return L;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <typename K>
+__device__ __forceinline__ K key_mask(uint32_t key_bits) {
+    return key_bits >= 8 * sizeof(K) ? (K)~(K)0 : (K)(((K)1 << key_bits) - 1);
+}
+
+// One read of all keys: digit histograms of every pass.  Equal digits within
+// a warp are combined with match.any before the shared-memory atomic.
+template <typename K>
+__global__ void __launch_bounds__(SORT_BLOCK) k_hist(const K *__restrict__ keys, uint64_t n, uint32_t key_bits,
+                                                     int passes, SortHeader *h) {
+    __shared__ uint32_t sh[MAX_PASSES * RADIX];
+    for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const K mask = key_mask<K>(key_bits);
+    const uint32_t lt = lanemask_lt();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t nround = (n + stride - 1) / stride * stride;  // uniform trip count per warp
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nround; i += stride) {
+        const bool valid = i < n;
+        const K k = valid ? (__ldcs(keys + i) & mask) : (K)0;
+        for (int p = 0; p < passes; ++p) {
+            const uint32_t d = valid ? (uint32_t)(k >> (8 * p)) & 255u : 256u + (threadIdx.x & 31);
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+            if (valid && (peers & lt) == 0) atomicAdd(&sh[p * RADIX + d], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x)
+        if (sh[i]) atomicAdd(&h->hist[0][0] + i, sh[i]);
+}
+
+// Exclusive scan per pass, pass activity and buffer plan.  One block.
+__global__ void __launch_bounds__(RADIX) k_plan(SortHeader *h, int passes, uint64_t n) {
+    __shared__ uint32_t s_scan[RADIX];
+    __shared__ int s_trivial[MAX_PASSES];
+    const int t = threadIdx.x;
+    for (int p = 0; p < passes; ++p) {
+        const uint32_t c = h->hist[p][t];
+        s_scan[t] = c;
+        __syncthreads();
+        for (int off = 1; off < RADIX; off <<= 1) {
+            const uint32_t v = t >= off ? s_scan[t - off] : 0u;
+            __syncthreads();
+            s_scan[t] += v;
+            __syncthreads();
+        }
+        h->start[p][t] = s_scan[t] - c;
+        if (t == 0) s_trivial[p] = 0;
+        __syncthreads();
+        if ((uint64_t)c == n) s_trivial[p] = 1;
+        __syncthreads();
+    }
+    if (t == 0) {
+        int act[MAX_PASSES], m = 0;
+        for (int p = 0; p < passes; ++p) {
+            h->plan[p].active = 0;
+            if (!s_trivial[p]) act[m++] = p;
+        }
+        for (int idx = 0; idx < m; ++idx) {
+            PassPlan &pl = h->plan[act[idx]];
+            pl.active = 1;
+            pl.dst_vals = ((m - 1 - idx) % 2 == 0) ? VB_PERM : VB_A;
+            pl.dst_keys = (idx == m - 1) ? KB_NONE : (((m - 2 - idx) % 2 == 0) ? KB_A : KB_B);
+        }
+        for (int idx = 0; idx < m; ++idx) {
+            PassPlan &pl = h->plan[act[idx]];
+            pl.src_keys = idx == 0 ? KB_USER : h->plan[act[idx - 1]].dst_keys;
+            pl.src_vals = idx == 0 ? VB_SYNTH : h->plan[act[idx - 1]].dst_vals;
+        }
+        h->identity = (m == 0);
+    }
+}
+
+template <typename K>
+struct PassArgs {
+    const K *user_keys;
+    K *ka, *kb;
+    uint32_t *va, *perm;
+    uint32_t *status;
+    SortHeader *h;
+    uint64_t n;
+    uint32_t key_bits, num_tiles;
+    uint32_t *err;
+};
+
+template <typename K>
+__global__ void __launch_bounds__(SORT_BLOCK, 3) k_pass(PassArgs<K> a, int pass) {
+    const PassPlan pl = a.h->plan[pass];
+    if (!pl.active) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    K *s_keys = reinterpret_cast<K *>(smem_raw);
+    uint32_t *s_vals = reinterpret_cast<uint32_t *>(smem_raw + sizeof(K) * SORT_TILE);
+    __shared__ uint32_t s_whist[SORT_WARPS][RADIX];
+    __shared__ uint32_t s_local[RADIX];
+    __shared__ uint32_t s_base[RADIX];
+    __shared__ uint32_t s_wsum[SORT_WARPS];
+    __shared__ uint32_t s_tile, s_abort;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        s_tile = atomicAdd(&a.h->tile_counter[pass], 1u);
+        s_abort = 0;
+    }
+    for (int i = tid; i < SORT_WARPS * RADIX; i += SORT_BLOCK) (&s_whist[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint64_t base = (uint64_t)tile * SORT_TILE;
+    const uint32_t shift = 8u * (uint32_t)pass;
+    const K mask = key_mask<K>(a.key_bits);
+    const K *kin = pl.src_keys == KB_USER ? a.user_keys : (pl.src_keys == KB_A ? a.ka : a.kb);
+    const uint32_t *vin = pl.src_vals == VB_A ? a.va : a.perm;
+
+    // Load: warp w owns the contiguous run [w*ITEMS*32, (w+1)*ITEMS*32) of the
+    // tile; item i of a lane sits at i*32 + lane, so each load is coalesced
+    // and the (item, lane) order is the input order within the warp.
+    K key[SORT_ITEMS];
+    uint32_t val[SORT_ITEMS], rank[SORT_ITEMS];
+    const uint32_t tile_n = (uint32_t)((a.n - base) < (uint64_t)SORT_TILE ? (a.n - base) : SORT_TILE);
+    const uint32_t wfirst = (uint32_t)warp * (SORT_ITEMS * 32) + lane;  // tile position of item 0
+#pragma unroll
+    for (int i = 0; i < SORT_ITEMS; ++i) {
+        const uint32_t pos = wfirst + (uint32_t)i * 32;
+        const bool valid = pos < tile_n;
+        const uint64_t idx = base + pos;
+        key[i] = valid ? (__ldcs(kin + idx) & mask) : (K)0;
+        val[i] = valid ? (pl.src_vals == VB_SYNTH ? (uint32_t)idx : __ldcs(vin + idx)) : 0u;
+    }
+    // Warp-level stable ranking: peers with the same digit, counted in item order.
+    const uint32_t lt = lanemask_lt();
+    uint32_t *wh = s_whist[warp];
+#pragma unroll
+    for (int i = 0; i < SORT_ITEMS; ++i) {
+        const bool valid = wfirst + (uint32_t)i * 32 < tile_n;
+        const uint32_t d = valid ? ((uint32_t)(key[i] >> shift) & 255u) : (256u + lane);
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+        const uint32_t below = __popc(peers & lt);
+        const uint32_t prior = valid ? wh[d] : 0u;
+        rank[i] = prior + below;
+        __syncwarp();
+        if (valid && below == 0) wh[d] = prior + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // Thread tid now owns digit tid: offsets of each warp within the tile.
+    uint32_t total = 0;
+#pragma unroll
+    for (int w = 0; w < SORT_WARPS; ++w) {
+        const uint32_t c = s_whist[w][tid];
+        s_whist[w][tid] = total;
+        total += c;
+    }
+    // Publish this tile's count, then look back for the exclusive prefix.
+    uint32_t *st = a.status + ((size_t)pass * a.num_tiles + tile) * RADIX;
+    uint32_t excl;
+    if (tile == 0) {
+        excl = a.h->start[pass][tid];
+        st_relaxed(st + tid, ST_INC | ((excl + total) & ST_VALUE));
+    } else {
+        st_relaxed(st + tid, ST_AGG | total);
+        excl = 0;
+        int64_t j = (int64_t)tile - 1;
+        uint32_t spins = 0;
+        bool timed_out = false;
+        while (j >= 0) {
+            const uint32_t s = ld_relaxed(a.status + ((size_t)pass * a.num_tiles + (uint64_t)j) * RADIX + tid);
+            const uint32_t flag = s & ~ST_VALUE;
+            if (flag == 0) {
+                if (++spins > SPIN_LIMIT || ld_relaxed(&a.h->abort)) {
+                    timed_out = true;
+                    break;
+                }
+                continue;
+            }
+            excl += s & ST_VALUE;
+            if (flag == ST_INC) break;
+            --j;
+        }
+        if (timed_out) {
+            atomicOr(a.err, ERR_TIMEOUT);
+            atomicExch(&a.h->abort, 1u);
+            s_abort = 1;
+        }
+        st_relaxed(st + tid, ST_INC | ((excl + total) & ST_VALUE));
+    }
+    s_base[tid] = excl;
+    // Exclusive scan of the tile's digit counts (positions in shared memory).
+    uint32_t incl = total;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    if (lane == 31) s_wsum[warp] = incl;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += s_wsum[w];
+    s_local[tid] = wpre + incl - total;
+    __syncthreads();
+    if (s_abort) return;
+
+    // Reorder the tile by digit in shared memory (stable).
+#pragma unroll
+    for (int i = 0; i < SORT_ITEMS; ++i) {
+        if (wfirst + (uint32_t)i * 32 < tile_n) {
+            const uint32_t d = (uint32_t)(key[i] >> shift) & 255u;
+            const uint32_t pos = s_local[d] + wh[d] + rank[i];
+            s_keys[pos] = key[i];
+            s_vals[pos] = val[i];
+        }
+    }
+    __syncthreads();
+    // Write runs of equal digits to their global positions.
+    K *kout = pl.dst_keys == KB_A ? a.ka : (pl.dst_keys == KB_B ? a.kb : nullptr);
+    uint32_t *vout = pl.dst_vals == VB_A ? a.va : a.perm;
+#pragma unroll 4
+    for (uint32_t p = tid; p < tile_n; p += SORT_BLOCK) {
+        const K k = s_keys[p];
+        const uint32_t d = (uint32_t)(k >> shift) & 255u;
+        const uint32_t g = s_base[d] + (p - s_local[d]);
+        if (kout) __stcs(kout + g, k);
+        __stcs(vout + g, s_vals[p]);
+    }
+}
+
+__global__ void k_ident(const SortHeader *h, uint32_t *perm, uint64_t n) {
+    if (!h->identity) return;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) perm[i] = (uint32_t)i;
+}
+
+template <typename K>
+cudaError_t run_sort(cudaStream_t s, const K *keys, uint32_t key_bits, uint64_t n, uint32_t *perm,
+                     unsigned char *scratch, uint32_t *err) {
+    const Layout L = layout(n, key_bits);
+    const int passes = (int)((key_bits + 7) / 8);
+    const uint32_t tiles = (uint32_t)((n + SORT_TILE - 1) / SORT_TILE);
+    SortHeader *h = reinterpret_cast<SortHeader *>(scratch + L.header);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, L.ka, s);  // header + status words
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint64_t hblocks = (n + SORT_BLOCK * 8 - 1) / (SORT_BLOCK * 8);
+    const uint64_t hcap = (uint64_t)(sms > 0 ? sms : 1) * 4;
+    if (hblocks > hcap) hblocks = hcap;
+    if (hblocks == 0) hblocks = 1;
+    k_hist<K><<<(unsigned)hblocks, SORT_BLOCK, 0, s>>>(keys, n, key_bits, passes, h);
+    k_plan<<<1, RADIX, 0, s>>>(h, passes, n);
+    PassArgs<K> a;
+    a.user_keys = keys;
+    a.ka = reinterpret_cast<K *>(scratch + L.ka);
+    a.kb = reinterpret_cast<K *>(scratch + L.kb);
+    a.va = reinterpret_cast<uint32_t *>(scratch + L.va);
+    a.perm = perm;
+    a.status = reinterpret_cast<uint32_t *>(scratch + L.status);
+    a.h = h;
+    a.n = n;
+    a.key_bits = key_bits;
+    a.num_tiles = tiles;
+    a.err = err;
+    const size_t dyn = (sizeof(K) + sizeof(uint32_t)) * SORT_TILE;
+    e = cudaFuncSetAttribute(k_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    for (int p = 0; p < passes; ++p) k_pass<K><<<tiles, SORT_BLOCK, dyn, s>>>(a, p);
+    uint64_t iblocks = (n + 255) / 256;
+    if (iblocks > 4096) iblocks = 4096;
+    k_ident<<<(unsigned)iblocks, 256, 0, s>>>(h, perm, n);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t sort_scratch_bytes(uint64_t n, uint32_t key_bits) { return layout(n, key_bits).total; }
+
+cudaError_t launch_sort(cudaStream_t s, const void *keys, uint32_t key_bits, uint64_t n, uint32_t *perm,
+                        void *scratch, uint32_t *err_word) {
+    if (n == 0) return cudaSuccess;
+    unsigned char *sc = static_cast<unsigned char *>(scratch);
+    if (key_bits <= 32) return run_sort<uint32_t>(s, (const uint32_t *)keys, key_bits, n, perm, sc, err_word);
+    return run_sort<uint64_t>(s, (const uint64_t *)keys, key_bits, n, perm, sc, err_word);
+}
+
+}  // namespace hcc

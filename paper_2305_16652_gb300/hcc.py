@@ -1,0 +1,240 @@
+"""Python binding of the hcc C ABI (include/hcc.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls and takes torch
+tensors (device memory) or numpy arrays (host memory) in place of pointers.
+All computation happens in libhcc.so; if that library is missing or fails
+to load, every call raises -- there is no fallback path.
+
+Tensor conventions:
+  rays: two contiguous (n, 4) float32 CUDA tensors (org_tmin, dir_tmax)
+  keys: (n,) int32 (key_bits <= 32) or int64 (key_bits > 32) CUDA tensor,
+        read as unsigned by the library
+  perm: (n,) int32 CUDA tensor (unsigned ray ids)
+  hits: (n, 4) int32 CUDA tensor: prim, then the bits of t, u, v
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "csrc", "_build", "libhcc.so")
+
+HCC_METHOD_NOSORT, HCC_METHOD_HCC, HCC_METHOD_TWOPOINT = 0, 1, 2
+METHODS = {"nosort": HCC_METHOD_NOSORT, "hcc": HCC_METHOD_HCC, "twopoint": HCC_METHOD_TWOPOINT}
+STATUS = {0: "HCC_OK", 1: "HCC_ERR_INVALID_ARG", 2: "HCC_ERR_OOM", 3: "HCC_ERR_CUDA", 4: "HCC_ERR_UNSUPPORTED",
+          5: "HCC_ERR_STACK_OVERFLOW", 6: "HCC_ERR_TIMEOUT"}
+HIT_DTYPE = np.dtype([("prim", np.int32), ("t", np.float32), ("u", np.float32), ("v", np.float32)])
+
+
+class HccError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Rays(ctypes.Structure):
+    _fields_ = [("org_tmin", ctypes.c_void_p), ("dir_tmax", ctypes.c_void_p), ("n", ctypes.c_uint64)]
+
+
+class _BvhDesc(ctypes.Structure):
+    _fields_ = [("num_nodes", ctypes.c_uint32), ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p),
+                ("left", ctypes.c_void_p), ("right", ctypes.c_void_p), ("first", ctypes.c_void_p),
+                ("count", ctypes.c_void_p), ("num_tris", ctypes.c_uint32), ("tris", ctypes.c_void_p),
+                ("order", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libhcc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    P, u32, u64, i32, f64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "hcc_create": [PP, i32, P],
+        "hcc_destroy": [P],
+        "hcc_set_stream": [P, P],
+        "hcc_reserve": [P, u64, u32],
+        "hcc_sync": [P],
+        "hcc_bvh_upload": [P, ctypes.POINTER(_BvhDesc), PP],
+        "hcc_bvh_info": [P, P, P, P, P, P],
+        "hcc_bvh_destroy": [P],
+        "hcc_select_cut": [P, P, u32, f64, PP],
+        "hcc_cut_info": [P, P, P],
+        "hcc_cut_destroy": [P],
+        "hcc_encode": [P, i32, P, P, ctypes.POINTER(_Rays), u32, P],
+        "hcc_sort": [P, P, u32, u64, P],
+        "hcc_gather": [P, ctypes.POINTER(_Rays), P, ctypes.POINTER(_Rays)],
+        "hcc_trace": [P, P, ctypes.POINTER(_Rays), i32, P, P],
+        "hcc_run": [P, i32, P, P, ctypes.POINTER(_Rays), u32, i32, P],
+        "hcc_run_host": [P, i32, P, P, P, P, u64, u32, i32, P],
+        "hcc_trace_counts": [P, P, ctypes.POINTER(_Rays), i32, P, P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.hcc_last_error.argtypes = [P]
+    lib.hcc_last_error.restype = ctypes.c_char_p
+    lib.hcc_status_string.argtypes = [ctypes.c_int]
+    lib.hcc_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status: int, ctx=None):
+    if status != 0:
+        msg = load().hcc_last_error(ctx).decode() if ctx else ""
+        raise HccError(status, msg)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _rays(org, dir_):
+    n = int(org.shape[0])
+    if dir_.shape[0] != n:
+        raise ValueError("org_tmin and dir_tmax differ in length")
+    return _Rays(_ptr(org), _ptr(dir_), n)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+# ------------------------------------------------------------------ context
+
+def hcc_create(device: int = 0, stream=None):
+    h = ctypes.c_void_p()
+    _check(load().hcc_create(ctypes.byref(h), device, _stream_handle(stream)))
+    return h
+
+
+def hcc_destroy(ctx):
+    _check(load().hcc_destroy(ctx))
+
+
+def hcc_set_stream(ctx, stream=None):
+    _check(load().hcc_set_stream(ctx, _stream_handle(stream)), ctx)
+
+
+def hcc_reserve(ctx, max_n: int, max_key_bits: int):
+    _check(load().hcc_reserve(ctx, max_n, max_key_bits), ctx)
+
+
+def hcc_sync(ctx):
+    _check(load().hcc_sync(ctx), ctx)
+
+
+# ---------------------------------------------------------------------- BVH
+
+def hcc_bvh_upload(ctx, bvh):
+    """bvh: an object with lo, hi, left, right, first, count, order, tris numpy arrays."""
+    arrs = dict(lo=np.ascontiguousarray(bvh.lo, np.float32), hi=np.ascontiguousarray(bvh.hi, np.float32),
+                left=np.ascontiguousarray(bvh.left, np.int32), right=np.ascontiguousarray(bvh.right, np.int32),
+                first=np.ascontiguousarray(bvh.first, np.uint32), count=np.ascontiguousarray(bvh.count, np.uint32),
+                tris=np.ascontiguousarray(bvh.tris, np.float32), order=np.ascontiguousarray(bvh.order, np.uint32))
+    d = _BvhDesc(arrs["lo"].shape[0], _ptr(arrs["lo"]), _ptr(arrs["hi"]), _ptr(arrs["left"]), _ptr(arrs["right"]),
+                 _ptr(arrs["first"]), _ptr(arrs["count"]), arrs["tris"].shape[0], _ptr(arrs["tris"]),
+                 _ptr(arrs["order"]))
+    h = ctypes.c_void_p()
+    _check(load().hcc_bvh_upload(ctx, ctypes.byref(d), ctypes.byref(h)), ctx)
+    return h
+
+
+def hcc_bvh_info(bvh):
+    nn, nt, dep = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    lo, hi = (ctypes.c_float * 3)(), (ctypes.c_float * 3)()
+    _check(load().hcc_bvh_info(bvh, ctypes.byref(nn), ctypes.byref(nt), ctypes.byref(dep), lo, hi))
+    return dict(num_nodes=nn.value, num_tris=nt.value, depth=dep.value, scene_lo=list(lo), scene_hi=list(hi))
+
+
+def hcc_bvh_destroy(bvh):
+    _check(load().hcc_bvh_destroy(bvh))
+
+
+# ---------------------------------------------------------------------- cut
+
+def hcc_select_cut(ctx, bvh, cut_size: int, lam: float = 0.125):
+    h = ctypes.c_void_p()
+    _check(load().hcc_select_cut(ctx, bvh, cut_size, lam, ctypes.byref(h)), ctx)
+    return h
+
+
+def hcc_cut_info(cut) -> np.ndarray:
+    n = ctypes.c_uint32()
+    _check(load().hcc_cut_info(cut, ctypes.byref(n), None))
+    ids = np.zeros(n.value, np.int32)
+    _check(load().hcc_cut_info(cut, ctypes.byref(n), _ptr(ids)))
+    return ids
+
+
+def hcc_cut_destroy(cut):
+    _check(load().hcc_cut_destroy(cut))
+
+
+# ------------------------------------------------------------- hot-path calls
+
+def hcc_encode(ctx, method, bvh, cut, org, dir_, key_bits: int, keys):
+    r = _rays(org, dir_)
+    _check(load().hcc_encode(ctx, METHODS.get(method, method), bvh, cut, ctypes.byref(r), key_bits, _ptr(keys)), ctx)
+
+
+def hcc_sort(ctx, keys, key_bits: int, n: int, perm):
+    _check(load().hcc_sort(ctx, _ptr(keys), key_bits, n, _ptr(perm)), ctx)
+
+
+def hcc_gather(ctx, in_org, in_dir, perm, out_org, out_dir):
+    ri, ro = _rays(in_org, in_dir), _rays(out_org, out_dir)
+    _check(load().hcc_gather(ctx, ctypes.byref(ri), _ptr(perm), ctypes.byref(ro)), ctx)
+
+
+def hcc_trace(ctx, bvh, org, dir_, hits, any_hit: bool = False, scatter=None):
+    r = _rays(org, dir_)
+    _check(load().hcc_trace(ctx, bvh, ctypes.byref(r), int(any_hit), _ptr(scatter), _ptr(hits)), ctx)
+
+
+def hcc_trace_counts(ctx, bvh, org, dir_, any_hit: bool = False):
+    """Diagnostic: total internal-node visits and triangle tests of a trace."""
+    r = _rays(org, dir_)
+    nv, nt = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().hcc_trace_counts(ctx, bvh, ctypes.byref(r), int(any_hit), ctypes.byref(nv), ctypes.byref(nt)),
+           ctx)
+    return {"node_visits": int(nv.value), "tri_tests": int(nt.value)}
+
+
+def hcc_run(ctx, method, bvh, cut, org, dir_, key_bits: int, hits, any_hit: bool = False):
+    r = _rays(org, dir_)
+    _check(load().hcc_run(ctx, METHODS.get(method, method), bvh, cut, ctypes.byref(r), key_bits, int(any_hit),
+                          _ptr(hits)), ctx)
+
+
+def hcc_run_host(ctx, method, bvh, cut, org: np.ndarray, dir_: np.ndarray, key_bits: int, hits: np.ndarray,
+                 any_hit: bool = False):
+    """Host buffers in and out (numpy arrays or pinned CPU tensors)."""
+    n = int(org.shape[0])
+    _check(load().hcc_run_host(ctx, METHODS.get(method, method), bvh, cut, _ptr(org), _ptr(dir_), n, key_bits,
+                               int(any_hit), _ptr(hits)), ctx)
+
+
+def hits_to_numpy(hits_tensor) -> np.ndarray:
+    """(n, 4) int32 hit tensor -> structured numpy array with prim, t, u, v."""
+    a = hits_tensor.detach().cpu().numpy() if hasattr(hits_tensor, "detach") else np.asarray(hits_tensor)
+    return np.ascontiguousarray(a, dtype=np.int32).view(HIT_DTYPE).reshape(-1)

@@ -1,0 +1,441 @@
+"""CUDA path against the CPU oracle, element by element (needs a GB300).
+
+Every check goes through the C ABI (libhcc.so via the ctypes binding).
+Integer results (cut ids, keys, permutations, gathered bytes) must be equal
+bit for bit.  Keys may differ only on rays within 1e-6 (relative) of a cut
+box boundary; hit records must be bit-identical except where two triangles
+tie in t within 1e-5 relative or the hit sits within 1e-6 of a triangle edge
+in barycentric terms.  Such exceptions are counted and bounded.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_16652_gb300 import gen, hcc
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+# ------------------------------------------------------------------ fixtures
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = hcc.hcc_create(0)
+    yield c
+    hcc.hcc_destroy(c)
+
+
+class Scene:
+    def __init__(self, ctx, w):
+        self.w = w
+        self.bvh = hcc.hcc_bvh_upload(ctx, w.bvh)
+        self.org = torch.from_numpy(w.rays.org).to(DEV)
+        self.dir = torch.from_numpy(w.rays.dir).to(DEV)
+        self.n = w.rays.n
+
+
+def _dense_workload(seed=4, ntris=3000, nrays=3000):
+    tris = gen.random_tris(seed, ntris, mu=-2.0)
+    b = gen.build_bvh(tris)
+    sec, _, prim = gen.camera_rays(tris, (0.5, 0.5, -1.2), (0.5, 0.5, 0.5), 45.0, 48, 48, 16, seed,
+                                   sample_major=True, max_rays=nrays)
+    return gen.Workload("dense", tris, b, sec, None, prim)
+
+
+@pytest.fixture(scope="module")
+def tiny(ctx):
+    return Scene(ctx, gen.tiny_workload(0))
+
+
+@pytest.fixture(scope="module")
+def dense(ctx):
+    return Scene(ctx, _dense_workload())
+
+
+@pytest.fixture(scope="module")
+def room(ctx):
+    return Scene(ctx, gen.room_workload(1, target_tris=60_000, W=160, H=90, spp=2))
+
+
+def _keys_tensor(n, k):
+    return torch.zeros(n, dtype=torch.int32 if k <= 32 else torch.int64, device=DEV)
+
+
+def _u64(keys_t, k):
+    a = keys_t.cpu().numpy()
+    return (a.view(np.uint32) if k <= 32 else a.view(np.uint64)).astype(np.uint64)
+
+
+def gpu_encode(ctx, sc, method, k, cut=None, org=None, dir_=None):
+    org = sc.org if org is None else org
+    dir_ = sc.dir if dir_ is None else dir_
+    keys = _keys_tensor(org.shape[0], k)
+    hcc.hcc_encode(ctx, method, sc.bvh, cut, org, dir_, k, keys)
+    hcc.hcc_sync(ctx)
+    return _u64(keys, k)
+
+
+def gpu_sort(ctx, keys_u64, k):
+    n = keys_u64.shape[0]
+    if k <= 32:
+        kt = torch.from_numpy(keys_u64.astype(np.uint32).view(np.int32)).to(DEV)
+    else:
+        kt = torch.from_numpy(keys_u64.view(np.int64)).to(DEV)
+    perm = torch.full((max(n, 1),), -7, dtype=torch.int32, device=DEV)
+    hcc.hcc_sort(ctx, kt, k, n, perm)
+    hcc.hcc_sync(ctx)
+    return perm[:n].cpu().numpy().view(np.uint32)
+
+
+def gpu_trace(ctx, sc, org, dir_, any_hit=False, scatter=None):
+    hits = torch.zeros((org.shape[0], 4), dtype=torch.int32, device=DEV)
+    hcc.hcc_trace(ctx, sc.bvh, org, dir_, hits, any_hit=any_hit, scatter=scatter)
+    hcc.hcc_sync(ctx)
+    return hcc.hits_to_numpy(hits)
+
+
+def compare_hits(g, o, tol_t=1e-5, tol_b=1e-6, max_frac=1e-3):
+    """Bit-exact except counted near ties; returns the number of exceptions."""
+    gi32 = np.ascontiguousarray(g).view(np.int32).reshape(-1, 4)
+    oi32 = np.ascontiguousarray(o).view(np.int32).reshape(-1, 4)
+    bad = np.nonzero(np.any(gi32 != oi32, axis=1))[0]
+    exceptions = 0
+    for i in bad:
+        gi, oi = g[i], o[i]
+        if gi["prim"] >= 0 and oi["prim"] >= 0 and gi["prim"] == oi["prim"]:
+            raise AssertionError(f"ray {i}: same triangle, different numbers {gi} vs {oi}")
+        both = gi["prim"] >= 0 and oi["prim"] >= 0
+        if both and abs(float(gi["t"]) - float(oi["t"])) <= tol_t * max(1.0, abs(float(oi["t"]))):
+            exceptions += 1
+            continue
+        ref = oi if oi["prim"] >= 0 else gi
+        margin = min(float(ref["u"]), float(ref["v"]), 1.0 - float(ref["u"]) - float(ref["v"]))
+        if margin < tol_b:
+            exceptions += 1
+            continue
+        raise AssertionError(f"ray {i}: GPU {gi} vs oracle {oi}")
+    assert exceptions <= max(1, max_frac * len(g)), exceptions
+    return exceptions
+
+
+# --------------------------------------------------------------------- cut
+
+@pytest.mark.parametrize("which", ["tiny", "room"])
+def test_cut_matches_oracle(ctx, which, request):
+    sc = request.getfixturevalue(which)
+    nleaves = int(np.sum(sc.w.bvh.left < 0))
+    for C in (1, 2, 3, 32, 64, 256, 4096, nleaves, nleaves + 5):
+        for lam in (0.125, 0.0, 1.0):
+            cut = hcc.hcc_select_cut(ctx, sc.bvh, C, lam)
+            try:
+                assert np.array_equal(hcc.hcc_cut_info(cut), oracle.select_cut(sc.w.bvh, C, lam)), (C, lam)
+            finally:
+                hcc.hcc_cut_destroy(cut)
+
+
+# ------------------------------------------------------------------ encode
+
+@pytest.mark.parametrize("k", [1, 16, 24, 31, 32, 33, 48, 64])
+@pytest.mark.parametrize("C", [32, 64])
+@pytest.mark.parametrize("which", ["tiny", "room"])
+def test_encode_hcc_matches_oracle(ctx, which, C, k, request):
+    sc = request.getfixturevalue(which)
+    cut = hcc.hcc_select_cut(ctx, sc.bvh, C, 0.125)
+    ids = hcc.hcc_cut_info(cut)
+    try:
+        g = gpu_encode(ctx, sc, "hcc", k, cut=cut)
+    finally:
+        hcc.hcc_cut_destroy(cut)
+    lo, hi = sc.w.bvh.lo[ids], sc.w.bvh.hi[ids]
+    o = oracle.encode_hcc(sc.w.rays.org, sc.w.rays.dir, lo, hi, k)
+    bad = np.nonzero(g != o)[0]
+    if len(bad):
+        m = oracle.key_margin(sc.w.rays.org[bad], sc.w.rays.dir[bad], lo, hi, k)
+        assert np.all(m < 1e-6), f"{len(bad)} key mismatches on non-marginal rays"
+    assert len(bad) <= max(1, sc.n // 1000)
+    assert np.all(g < (np.uint64(1) << np.uint64(k)) if k < 64 else True)
+    assert len(np.unique(g)) > 1
+
+
+@pytest.mark.parametrize("k", [1, 5, 6, 16, 30, 32, 33, 60, 64])
+def test_encode_twopoint_matches_oracle(ctx, room, k):
+    g = gpu_encode(ctx, room, "twopoint", k)
+    o = oracle.encode_twopoint(room.w.rays.org, room.w.rays.dir, room.w.bvh.lo[0], room.w.bvh.hi[0], k)
+    assert np.array_equal(g, o)
+
+
+def test_encode_special_rays(ctx, tiny):
+    """Zero direction components, origins on box faces, NaN and Inf inputs."""
+    cut = hcc.hcc_select_cut(ctx, tiny.bvh, 32, 0.125)
+    ids = hcc.hcc_cut_info(cut)
+    lo, hi = tiny.w.bvh.lo[ids], tiny.w.bvh.hi[ids]
+    rng = np.random.default_rng(0)
+    n = 600
+    org = np.concatenate([rng.uniform(0, 1, (n, 3)), np.full((n, 1), 1e-4)], 1).astype(np.float32)
+    d = rng.normal(size=(n, 3))
+    d[: n // 3, rng.integers(0, 3)] = 0.0
+    d[n // 3: n // 2, :2] = 0.0
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    dir_ = np.concatenate([d, np.full((n, 1), np.inf)], 1).astype(np.float32)
+    org[:50, :3] = lo[np.arange(50) % len(ids)]  # origins exactly on box corners
+    org[50:60, 0] = np.nan
+    dir_[60:70, 1] = np.inf
+    dir_[70:80, 3] = np.nan
+    o_t, d_t = torch.from_numpy(org).to(DEV), torch.from_numpy(dir_).to(DEV)
+    try:
+        for k in (32, 64):
+            g = gpu_encode(ctx, tiny, "hcc", k, cut=cut, org=o_t, dir_=d_t)
+            assert np.array_equal(g, oracle.encode_hcc(org, dir_, lo, hi, k))
+        g = gpu_encode(ctx, tiny, "twopoint", 32, org=o_t, dir_=d_t)
+        assert np.array_equal(g, oracle.encode_twopoint(org, dir_, tiny.w.bvh.lo[0], tiny.w.bvh.hi[0], 32))
+    finally:
+        hcc.hcc_cut_destroy(cut)
+
+
+# -------------------------------------------------------------------- sort
+
+def _keys(kind, n, k, rng):
+    top = (1 << k) - 1 if k < 64 else (1 << 64) - 1
+    if kind == "uniform":
+        return rng.integers(0, top, n, dtype=np.uint64, endpoint=True)
+    if kind == "few":
+        return rng.integers(0, 4, n, dtype=np.uint64)
+    if kind == "equal":
+        return np.full(n, min(top, 12345), np.uint64)
+    if kind == "high_only":  # only the top digit varies: lower passes are skipped
+        return (rng.integers(0, 256, n, dtype=np.uint64) << np.uint64(max(k - 8, 0))) & np.uint64(top)
+    if kind == "distinct":
+        return (rng.permutation(n).astype(np.uint64) * np.uint64(2654435761)) & np.uint64(top)
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 31, 32, 33, 4095, 4096, 4097, 65537, 300_001])
+def test_sort_sizes(ctx, n):
+    rng = np.random.default_rng(n)
+    for k in (32, 17):
+        keys = _keys("uniform", n, k, rng)
+        assert np.array_equal(gpu_sort(ctx, keys, k), oracle.stable_sort(keys))
+
+
+@pytest.mark.parametrize("k", [1, 8, 16, 24, 31, 32, 33, 48, 64])
+@pytest.mark.parametrize("kind", ["uniform", "few", "equal", "high_only", "distinct"])
+def test_sort_key_widths(ctx, k, kind):
+    rng = np.random.default_rng(k * 31 + len(kind))
+    n = 100_003
+    keys = _keys(kind, n, k, rng)
+    assert np.array_equal(gpu_sort(ctx, keys, k), oracle.stable_sort(keys))
+
+
+def test_sort_ignores_bits_above_key_bits(ctx):
+    rng = np.random.default_rng(5)
+    keys = rng.integers(0, 2 ** 32 - 1, 50_000, dtype=np.uint64)
+    k = 20
+    g = gpu_sort(ctx, keys, k)
+    assert np.array_equal(g, oracle.stable_sort(keys & np.uint64((1 << k) - 1)))
+
+
+def test_sort_hcc_keys(ctx, room):
+    cut = hcc.hcc_select_cut(ctx, room.bvh, 32, 0.125)
+    try:
+        g = gpu_encode(ctx, room, "hcc", 32, cut=cut)
+    finally:
+        hcc.hcc_cut_destroy(cut)
+    assert np.array_equal(gpu_sort(ctx, g, 32), oracle.stable_sort(g))
+
+
+# ------------------------------------------------------------------ gather
+
+@pytest.mark.parametrize("n", [1, 33, 1000, 65_541])
+def test_gather_bit_exact(ctx, n):
+    rng = np.random.default_rng(n)
+    org = rng.integers(-2 ** 31, 2 ** 31 - 1, (n, 4), dtype=np.int64).astype(np.int32).view(np.float32)
+    dir_ = rng.integers(-2 ** 31, 2 ** 31 - 1, (n, 4), dtype=np.int64).astype(np.int32).view(np.float32)
+    perm = rng.permutation(n).astype(np.uint32)
+    oo, od = oracle.gather(org, dir_, perm)
+    ti, td = torch.from_numpy(org.copy()).to(DEV), torch.from_numpy(dir_.copy()).to(DEV)
+    po, pd = torch.zeros_like(ti), torch.zeros_like(td)
+    hcc.hcc_gather(ctx, ti, td, torch.from_numpy(perm.view(np.int32)).to(DEV), po, pd)
+    hcc.hcc_sync(ctx)
+    assert po.cpu().numpy().tobytes() == oo.tobytes() and pd.cpu().numpy().tobytes() == od.tobytes()
+
+
+# ------------------------------------------------------------------- trace
+
+@pytest.mark.parametrize("which", ["tiny", "dense", "room"])
+def test_trace_closest_matches_oracle(ctx, which, request):
+    sc = request.getfixturevalue(which)
+    g = gpu_trace(ctx, sc, sc.org, sc.dir)
+    o = oracle.trace_bvh(sc.w.bvh, sc.w.rays.org, sc.w.rays.dir)
+    compare_hits(g, o)
+    assert (g["prim"] >= 0).mean() > 0.2
+
+
+def test_trace_matches_brute_force_definition(ctx, dense):
+    g = gpu_trace(ctx, dense, dense.org, dense.dir)
+    o = oracle.trace_brute(dense.w.tris, dense.w.rays.org, dense.w.rays.dir)
+    compare_hits(g, o)
+
+
+def test_trace_any_hit_shadow_rays(ctx, room):
+    sh = room.w.shadow
+    org, dir_ = torch.from_numpy(sh.org).to(DEV), torch.from_numpy(sh.dir).to(DEV)
+    g = gpu_trace(ctx, room, org, dir_, any_hit=True)
+    o = oracle.trace_bvh(room.w.bvh, sh.org, sh.dir)
+    occl_g, occl_o = g["prim"] >= 0, o["prim"] >= 0
+    assert np.array_equal(occl_g, occl_o)
+    assert 0.01 < occl_g.mean() < 0.99
+    for i in np.nonzero(occl_g)[0][:500]:
+        ok, t, u, v = oracle.intersect(sh.org[i, :3], sh.dir[i, :3], sh.org[i, 3], sh.dir[i, 3],
+                                       room.w.tris[g["prim"][i]])
+        assert ok and np.float32(t) == g["t"][i]
+
+
+def test_trace_special_rays(ctx, dense):
+    rng = np.random.default_rng(1)
+    n = 400
+    org = np.concatenate([rng.uniform(0, 1, (n, 3)), np.full((n, 1), 1e-4)], 1).astype(np.float32)
+    d = rng.normal(size=(n, 3))
+    d[:100, 0] = 0.0
+    d[100:150, :2] = 0.0
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    dir_ = np.concatenate([d, np.full((n, 1), np.inf)], 1).astype(np.float32)
+    dir_[150:200, 3] = 0.3          # finite tmax
+    org[200:210, 1] = np.nan        # invalid inputs are misses on both sides
+    dir_[210:220, 2] = np.nan
+    org[220:230, 3] = np.inf        # empty interval
+    g = gpu_trace(ctx, dense, torch.from_numpy(org).to(DEV), torch.from_numpy(dir_).to(DEV))
+    o = oracle.trace_bvh(dense.w.bvh, org, dir_)
+    compare_hits(g, o)
+    assert np.all(g["prim"][200:230] == -1)
+
+
+def test_trace_scatter_and_reorder_invariance(ctx, room):
+    rng = np.random.default_rng(3)
+    perm = rng.permutation(room.n).astype(np.uint32)
+    po, pd = oracle.gather(room.w.rays.org, room.w.rays.dir, perm)
+    plain = gpu_trace(ctx, room, room.org, room.dir)
+    perm_t = torch.from_numpy(perm.view(np.int32)).to(DEV)
+    scattered = gpu_trace(ctx, room, torch.from_numpy(po).to(DEV), torch.from_numpy(pd).to(DEV), scatter=perm_t)
+    assert plain.tobytes() == scattered.tobytes()
+
+
+# ---------------------------------------------------------------- pipeline
+
+def run_pipeline(ctx, sc, method, k=32, C=32, any_hit=False):
+    cut = hcc.hcc_select_cut(ctx, sc.bvh, C, 0.125) if method == "hcc" else None
+    hits = torch.zeros((sc.n, 4), dtype=torch.int32, device=DEV)
+    try:
+        hcc.hcc_run(ctx, method, sc.bvh, cut, sc.org, sc.dir, k, hits, any_hit=any_hit)
+        hcc.hcc_sync(ctx)
+    finally:
+        if cut is not None:
+            hcc.hcc_cut_destroy(cut)
+    return hcc.hits_to_numpy(hits)
+
+
+@pytest.mark.parametrize("which", ["tiny", "room"])
+def test_pipeline_methods_agree_bit_for_bit(ctx, which, request):
+    sc = request.getfixturevalue(which)
+    base = run_pipeline(ctx, sc, "nosort")
+    for method, k, C in (("hcc", 32, 32), ("hcc", 32, 256), ("hcc", 64, 64), ("hcc", 16, 4096), ("twopoint", 32, 0),
+                         ("twopoint", 64, 0)):
+        assert run_pipeline(ctx, sc, method, k, C).tobytes() == base.tobytes(), (method, k, C)
+    compare_hits(base, oracle.trace_bvh(sc.w.bvh, sc.w.rays.org, sc.w.rays.dir))
+
+
+def test_pipeline_host_buffers(ctx, room):
+    cut = hcc.hcc_select_cut(ctx, room.bvh, 32, 0.125)
+    try:
+        out = np.zeros(room.n, hcc.HIT_DTYPE)
+        hcc.hcc_run_host(ctx, "hcc", room.bvh, cut, room.w.rays.org, room.w.rays.dir, 32, out)
+    finally:
+        hcc.hcc_cut_destroy(cut)
+    assert out.tobytes() == run_pipeline(ctx, room, "nosort").tobytes()
+
+
+def test_deterministic(ctx, room):
+    a = run_pipeline(ctx, room, "hcc")
+    b = run_pipeline(ctx, room, "hcc")
+    assert a.tobytes() == b.tobytes()
+
+
+# ------------------------------------------------------------- edge cases
+
+def test_empty_inputs_are_noops(ctx, tiny):
+    e = torch.zeros((0, 4), dtype=torch.float32, device=DEV)
+    k = torch.zeros(0, dtype=torch.int32, device=DEV)
+    h = torch.zeros((0, 4), dtype=torch.int32, device=DEV)
+    cut = hcc.hcc_select_cut(ctx, tiny.bvh, 32, 0.125)
+    hcc.hcc_encode(ctx, "hcc", tiny.bvh, cut, e, e, 32, k)
+    hcc.hcc_sort(ctx, k, 32, 0, k)
+    hcc.hcc_gather(ctx, e, e, k, e, e)
+    hcc.hcc_trace(ctx, tiny.bvh, e, e, h)
+    hcc.hcc_run(ctx, "hcc", tiny.bvh, cut, e, e, 32, h)
+    hcc.hcc_sync(ctx)
+    hcc.hcc_cut_destroy(cut)
+
+
+def test_invalid_arguments_are_rejected(ctx, tiny):
+    cut = hcc.hcc_select_cut(ctx, tiny.bvh, 32, 0.125)
+    keys = torch.zeros(tiny.n, dtype=torch.int32, device=DEV)
+    try:
+        for bad_k in (0, 65):
+            with pytest.raises(hcc.HccError) as ei:
+                hcc.hcc_encode(ctx, "hcc", tiny.bvh, cut, tiny.org, tiny.dir, bad_k, keys)
+            assert ei.value.status == 1
+        with pytest.raises(hcc.HccError):
+            hcc.hcc_encode(ctx, "hcc", tiny.bvh, None, tiny.org, tiny.dir, 32, keys)  # HCC without a cut
+        with pytest.raises(hcc.HccError):
+            hcc.hcc_encode(ctx, "nosort", tiny.bvh, cut, tiny.org, tiny.dir, 32, keys)
+        with pytest.raises(hcc.HccError):
+            hcc.hcc_select_cut(ctx, tiny.bvh, 0, 0.125)
+        with pytest.raises(hcc.HccError):
+            hcc.hcc_select_cut(ctx, tiny.bvh, 8, -1.0)
+        with pytest.raises(hcc.HccError):  # keys and perm overlap
+            hcc.hcc_sort(ctx, keys, 32, tiny.n, keys)
+        with pytest.raises(hcc.HccError):  # misaligned ray stream
+            hcc.hcc_trace(ctx, tiny.bvh, tiny.org.view(-1)[1:].view(-1)[: 4 * (tiny.n - 1)].view(-1, 4), tiny.dir[1:],
+                          torch.zeros((tiny.n - 1, 4), dtype=torch.int32, device=DEV))
+    finally:
+        hcc.hcc_cut_destroy(cut)
+    hcc.hcc_sync(ctx)  # nothing was launched by the rejected calls
+
+
+def _chain_bvh(depth):
+    """Every node's box is the whole scene; left = deeper internal node, right = leaf."""
+    tris = gen.random_tris(1, depth + 1, mu=-1.0)
+    lo = np.tile(tris.reshape(-1, 3).min(0), (2 * depth + 1, 1)).astype(np.float32)
+    hi = np.tile(tris.reshape(-1, 3).max(0), (2 * depth + 1, 1)).astype(np.float32)
+    left = np.full(2 * depth + 1, -1, np.int32)
+    right = np.full(2 * depth + 1, -1, np.int32)
+    first = np.zeros(2 * depth + 1, np.uint32)
+    count = np.zeros(2 * depth + 1, np.uint32)
+    # internal nodes 0..depth-1 at even ids 2i; leaves at odd ids
+    for i in range(depth):
+        node = 2 * i
+        left[node] = 2 * (i + 1) if i + 1 < depth else 2 * depth
+        right[node] = 2 * i + 1
+        first[2 * i + 1], count[2 * i + 1] = i, 1
+    first[2 * depth], count[2 * depth] = depth, 1
+    return gen.BVH(lo, hi, left, right, first, count, np.arange(depth + 1, dtype=np.uint32), tris, depth)
+
+
+def test_stack_overflow_is_reported_and_context_survives(ctx, tiny):
+    deep = _chain_bvh(100)
+    h = hcc.hcc_bvh_upload(ctx, deep)
+    assert hcc.hcc_bvh_info(h)["depth"] == 100
+    c = deep.tris.reshape(-1, 3).mean(0)
+    org = torch.tensor([[c[0], c[1], c[2] - 5.0, 0.0]], dtype=torch.float32, device=DEV)
+    dir_ = torch.tensor([[0.0, 0.0, 1.0, float("inf")]], dtype=torch.float32, device=DEV)
+    hits = torch.zeros((1, 4), dtype=torch.int32, device=DEV)
+    hcc.hcc_trace(ctx, h, org, dir_, hits)
+    with pytest.raises(hcc.HccError) as ei:
+        hcc.hcc_sync(ctx)
+    assert ei.value.status == 5
+    assert int(hits[0, 0]) == -1
+    hcc.hcc_bvh_destroy(h)
+    # the context keeps working
+    g = gpu_trace(ctx, tiny, tiny.org, tiny.dir)
+    compare_hits(g, oracle.trace_bvh(tiny.w.bvh, tiny.w.rays.org, tiny.w.rays.dir))
