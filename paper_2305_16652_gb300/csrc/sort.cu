@@ -84,35 +84,56 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
+// Lanes of the warp whose digit equals this lane's, found with one ballot per
+// digit bit (data-independent cost, unlike match.any whose cost grows with
+// the number of distinct values).  valid_mask: lanes holding a real item.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, uint32_t dbits, uint32_t valid_mask) {
+    uint32_t peers = valid_mask;
+    for (uint32_t b = 0; b < dbits; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, bit);
+        peers &= bit ? bal : ~bal;
+    }
+    return peers;
+}
+
 template <typename K>
 __device__ __forceinline__ K key_mask(uint32_t key_bits) {
     return key_bits >= 8 * sizeof(K) ? (K)~(K)0 : (K)(((K)1 << key_bits) - 1);
 }
 
-// One read of all keys: digit histograms of every pass.  Equal digits within
-// a warp are combined with match.any before the shared-memory atomic.
+// One read of all keys: digit histograms of every pass.  Lanes with equal
+// digits are combined (ballot bit-split) so one leader adds their count;
+// each warp has its own shared-memory copy of the histograms.
 template <typename K>
 __global__ void __launch_bounds__(SORT_BLOCK) k_hist(const K *__restrict__ keys, uint64_t n, uint32_t key_bits,
                                                      int passes, SortHeader *h) {
-    __shared__ uint32_t sh[MAX_PASSES * RADIX];
-    for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) sh[i] = 0;
+    extern __shared__ uint32_t sh[];  // [SORT_WARPS][passes * RADIX]
+    const int nb = passes * RADIX;
+    for (int i = threadIdx.x; i < SORT_WARPS * nb; i += blockDim.x) sh[i] = 0;
     __syncthreads();
+    uint32_t *wh = sh + (threadIdx.x >> 5) * nb;
     const K mask = key_mask<K>(key_bits);
     const uint32_t lt = lanemask_lt();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t nround = (n + stride - 1) / stride * stride;  // uniform trip count per warp
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nround; i += stride) {
         const bool valid = i < n;
+        const uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
         const K k = valid ? (__ldcs(keys + i) & mask) : (K)0;
         for (int p = 0; p < passes; ++p) {
-            const uint32_t d = valid ? (uint32_t)(k >> (8 * p)) & 255u : 256u + (threadIdx.x & 31);
-            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
-            if (valid && (peers & lt) == 0) atomicAdd(&sh[p * RADIX + d], (uint32_t)__popc(peers));
+            const uint32_t d = (uint32_t)(k >> (8 * p)) & 255u;
+            const uint32_t dbits = key_bits - 8u * p < 8u ? key_bits - 8u * p : 8u;
+            const uint32_t peers = digit_peers(d, dbits, vmask);
+            if (valid && (peers & lt) == 0) wh[p * RADIX + d] += (uint32_t)__popc(peers);
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x)
-        if (sh[i]) atomicAdd(&h->hist[0][0] + i, sh[i]);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        uint32_t c = 0;
+        for (int w = 0; w < SORT_WARPS; ++w) c += sh[w * nb + i];
+        if (c) atomicAdd(&h->hist[0][0] + i, c);
+    }
 }
 
 // Exclusive scan per pass, pass activity and buffer plan.  One block.
@@ -213,12 +234,13 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) k_pass(PassArgs<K> a, int pass)
     }
     // Warp-level stable ranking: peers with the same digit, counted in item order.
     const uint32_t lt = lanemask_lt();
+    const uint32_t dbits = a.key_bits - shift < 8u ? a.key_bits - shift : 8u;
     uint32_t *wh = s_whist[warp];
 #pragma unroll
     for (int i = 0; i < SORT_ITEMS; ++i) {
         const bool valid = wfirst + (uint32_t)i * 32 < tile_n;
-        const uint32_t d = valid ? ((uint32_t)(key[i] >> shift) & 255u) : (256u + lane);
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+        const uint32_t d = (uint32_t)(key[i] >> shift) & 255u;
+        const uint32_t peers = digit_peers(d, dbits, __ballot_sync(0xFFFFFFFFu, valid));
         const uint32_t below = __popc(peers & lt);
         const uint32_t prior = valid ? wh[d] : 0u;
         rank[i] = prior + below;
@@ -331,7 +353,10 @@ cudaError_t run_sort(cudaStream_t s, const K *keys, uint32_t key_bits, uint64_t 
     const uint64_t hcap = (uint64_t)(sms > 0 ? sms : 1) * 4;
     if (hblocks > hcap) hblocks = hcap;
     if (hblocks == 0) hblocks = 1;
-    k_hist<K><<<(unsigned)hblocks, SORT_BLOCK, 0, s>>>(keys, n, key_bits, passes, h);
+    const size_t hsm = (size_t)SORT_WARPS * passes * RADIX * sizeof(uint32_t);
+    e = cudaFuncSetAttribute(k_hist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
+    if (e != cudaSuccess) return e;
+    k_hist<K><<<(unsigned)hblocks, SORT_BLOCK, hsm, s>>>(keys, n, key_bits, passes, h);
     k_plan<<<1, RADIX, 0, s>>>(h, passes, n);
     PassArgs<K> a;
     a.user_keys = keys;

@@ -324,7 +324,7 @@ static uint32_t build_rec(Builder *B, uint32_t b, uint32_t e, uint32_t depth) {
     memcpy(B->lo + me * 3, lo, sizeof lo);
     memcpy(B->hi + me * 3, hi, sizeof hi);
     uint32_t n = e - b;
-    if (n <= (uint32_t)B->max_leaf) {
+    if (n == 1) {
         B->left[me] = B->right[me] = -1;
         B->first[me] = b;
         B->count[me] = n;
@@ -386,6 +386,18 @@ static uint32_t build_rec(Builder *B, uint32_t b, uint32_t e, uint32_t depth) {
             }
         }
     }
+    /* SAH termination: a node of at most max_leaf triangles stays a leaf
+       unless splitting is cheaper (traversal step 1, triangle test 1). */
+    if (n <= (uint32_t)B->max_leaf) {
+        double parea = box_area(lo, hi);
+        double split_cost = (bax < 0 || !(parea > 0)) ? INFINITY : 1.0 + best / parea;
+        if ((double)n <= split_cost) {
+            B->left[me] = B->right[me] = -1;
+            B->first[me] = b;
+            B->count[me] = n;
+            return me;
+        }
+    }
     uint32_t mid;
     if (bax < 0) {
         mid = b + n / 2; /* all centroids coincide: split the range in half */
@@ -418,7 +430,11 @@ static uint32_t build_rec(Builder *B, uint32_t b, uint32_t e, uint32_t depth) {
 }
 
 /*
- * Binned-SAH BVH2 over ntris triangles (tv: 9 floats each).  Nodes are
+ * Binned-SAH BVH2 over ntris triangles (tv: 9 floats each): every node is
+ * split at the cheapest of the bins-1 candidate planes per axis (surface
+ * area heuristic); a node of at most max_leaf triangles becomes a leaf
+ * unless the split is cheaper than testing its triangles (traversal and
+ * triangle test both cost 1).  Nodes are
  * numbered in depth-first pre-order with the root at 0; a leaf has
  * left = right = -1 and owns order[first .. first+count).  Node boxes are
  * the exact FP32 union of their triangles' vertex bounds.  Arrays must hold

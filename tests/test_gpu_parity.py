@@ -156,7 +156,8 @@ def test_encode_hcc_matches_oracle(ctx, which, C, k, request):
         assert np.all(m < 1e-6), f"{len(bad)} key mismatches on non-marginal rays"
     assert len(bad) <= max(1, sc.n // 1000)
     assert np.all(g < (np.uint64(1) << np.uint64(k)) if k < 64 else True)
-    assert len(np.unique(g)) > 1
+    if k >= 16:
+        assert len(np.unique(g)) > 1
 
 
 @pytest.mark.parametrize("k", [1, 5, 6, 16, 30, 32, 33, 60, 64])
@@ -201,7 +202,7 @@ def _keys(kind, n, k, rng):
     if kind == "uniform":
         return rng.integers(0, top, n, dtype=np.uint64, endpoint=True)
     if kind == "few":
-        return rng.integers(0, 4, n, dtype=np.uint64)
+        return rng.integers(0, min(4, top + 1), n, dtype=np.uint64)
     if kind == "equal":
         return np.full(n, min(top, 12345), np.uint64)
     if kind == "high_only":  # only the top digit varies: lower passes are skipped
