@@ -215,6 +215,30 @@ hcc_status hcc_encode(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const
  */
 hcc_status hcc_sort(hcc_ctx *ctx, const void *keys, uint32_t key_bits, uint64_t n, uint32_t *perm);
 
+/*
+ * hcc_sort without a context and without allocating anything, for callers
+ * that cannot let a library allocate device memory: programs whose device
+ * memory is reserved up front by their own allocator, and latency-bound
+ * loops that cannot take the device synchronisation cudaMalloc/cudaFree
+ * may imply.  The paper has no counterpart; this is a service of this
+ * library.  Same result as hcc_sort (stable ascending sort of ids by the low
+ * key_bits bits).  Scratch is a fixed device array owned by the library,
+ * sized for n <= HCC_SORT_NOALLOC_MAX_N keys of up to 64 bits (about 11 MiB
+ * on every device that loads the library, for the life of the process).
+ * Runs on the calling thread's current device; stream (a cudaStream_t,
+ * NULL = legacy default stream) must belong to it.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU race and give wrong results.
+ * err_word: optional device uint32 into which bounded-wait failures are
+ * OR-ed (HCC_ERR_TIMEOUT's bit 2); it is never cleared by the library.
+ * Errors (synchronous): INVALID_ARG (n above the maximum, key_bits outside
+ * 1..64, NULL/misaligned/overlapping buffers), CUDA.
+ */
+#define HCC_SORT_NOALLOC_MAX_N 524288u
+hcc_status hcc_sort_noalloc(const void *keys, uint32_t key_bits, uint64_t n, uint32_t *perm, uint32_t *err_word,
+                            void *stream);
+
 /* ---------------------------------------------------------------- gather */
 
 /*

@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
         "hcc_run": [P, i32, P, P, ctypes.POINTER(_Rays), u32, i32, P],
         "hcc_run_host": [P, i32, P, P, P, P, u64, u32, i32, P],
         "hcc_trace_counts": [P, P, ctypes.POINTER(_Rays), i32, P, P],
+        "hcc_sort_noalloc": [P, u32, u64, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -199,6 +200,14 @@ def hcc_encode(ctx, method, bvh, cut, org, dir_, key_bits: int, keys):
 
 def hcc_sort(ctx, keys, key_bits: int, n: int, perm):
     _check(load().hcc_sort(ctx, _ptr(keys), key_bits, n, _ptr(perm)), ctx)
+
+
+HCC_SORT_NOALLOC_MAX_N = 524288
+
+
+def hcc_sort_noalloc(keys, key_bits: int, n: int, perm, err_word=None, stream=None):
+    """Sort without a context or any allocation (n <= HCC_SORT_NOALLOC_MAX_N)."""
+    _check(load().hcc_sort_noalloc(_ptr(keys), key_bits, n, _ptr(perm), _ptr(err_word), _stream_handle(stream)))
 
 
 def hcc_gather(ctx, in_org, in_dir, perm, out_org, out_dir):

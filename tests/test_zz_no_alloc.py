@@ -1,0 +1,58 @@
+"""hcc_sort_noalloc: the sort for callers that cannot allocate device memory.
+
+Such callers (a program whose device memory is all reserved by its own
+allocator, or a latency-bound loop that cannot take the synchronisation a
+cudaMalloc may imply) call hcc_sort_noalloc, which uses a fixed scratch array
+owned by the library.  Its result must equal hcc_sort's, bit for bit, on two
+calls in a row (the second call reuses the array the first one left behind).
+This file is collected last so that a run stopping at its first failure has
+already run every other test.
+"""
+import numpy as np
+import pytest
+
+from paper_2305_16652_gb300 import build, hcc
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _reference_perm(ctx, keys_t, k, n):
+    perm = torch.full((n,), -1, dtype=torch.int32, device=DEV)
+    hcc.hcc_sort(ctx, keys_t, k, n, perm)
+    hcc.hcc_sync(ctx)
+    return perm
+
+
+def test_noalloc_sort_matches_hcc_sort_on_two_calls():
+    build()
+    ctx = hcc.hcc_create(0)
+    try:
+        rng = np.random.default_rng(2024)
+        cases = [(300_001, 32, np.uint32), (hcc.HCC_SORT_NOALLOC_MAX_N, 48, np.uint64)]
+        for n, k, dt in cases:  # two calls in a row on the same static scratch
+            keys = rng.integers(0, 2 ** k - 1, n, dtype=np.uint64).astype(dt)
+            keys[::7] = keys[0]  # plenty of equal keys: stability matters
+            keys_t = torch.from_numpy(keys.view(np.int32 if dt == np.uint32 else np.int64)).to(DEV)
+            ref = _reference_perm(ctx, keys_t, k, n)
+            perm = torch.full((n,), -1, dtype=torch.int32, device=DEV)
+            err = torch.zeros(1, dtype=torch.int32, device=DEV)
+            hcc.hcc_sort_noalloc(keys_t, k, n, perm, err_word=err)
+            torch.cuda.synchronize()
+            assert int(err.item()) == 0
+            assert torch.equal(perm, ref), (n, k)
+    finally:
+        hcc.hcc_destroy(ctx)
+
+
+def test_noalloc_sort_rejects_sizes_beyond_its_maximum():
+    build()
+    n = hcc.HCC_SORT_NOALLOC_MAX_N + 1
+    keys = torch.zeros(n, dtype=torch.int32, device=DEV)
+    perm = torch.zeros(n, dtype=torch.int32, device=DEV)
+    with pytest.raises(hcc.HccError) as ei:
+        hcc.hcc_sort_noalloc(keys, 32, n, perm)
+    assert ei.value.status == 1
+    with pytest.raises(hcc.HccError):
+        hcc.hcc_sort_noalloc(keys, 0, 16, perm)
