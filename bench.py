@@ -38,11 +38,12 @@ FALLBACK_HBM_GBS = 6800.0
 SMS, LANES_PER_SM = 152, 128
 
 # FP32/INT lane operations the trace kernel issues per unit of work, counted
-# from trace.cu: one internal-node visit decodes 12 quantised bounds (byte
-# select, convert, outward fma: 3 ops each), runs two slab tests (6 sub, 6 mul,
-# 12 min/max, 1 mul, 1 min each) and orders/pushes (~10); one triangle test
-# is the Moller-Trumbore sequence (~45 ops incl. the reciprocal).
-OPS_PER_NODE = 36 + 2 * 26 + 10 + 6
+# from trace.cu: one internal-node visit runs two slab tests (6 sub, 6 mul,
+# 12 min/max, 1 mul, 1 min each = 26) and orders/pushes (~10); the quantised
+# layout adds the decode of 12 bounds (byte select, convert, outward fma: 3
+# ops each) and of the node frame (6); one triangle test is the
+# Moller-Trumbore sequence (~45 ops incl. the reciprocal).
+OPS_PER_NODE = {"exact": 2 * 26 + 10, "quantised": 36 + 6 + 2 * 26 + 10}
 OPS_PER_TRI = 45
 # HBM bytes each stage must move per ray (32-bit keys; see the design notes)
 BYTES_ENCODE = 32 + 4
@@ -193,7 +194,8 @@ def run_ours(args, rank, world, local_rank):
     n = w.rays.n
     K, C = args.key_bits, args.cut_size
     ctx = hcc.hcc_create(local_rank)
-    bvh = hcc.hcc_bvh_upload(ctx, w.bvh)
+    bvh = hcc.hcc_bvh_upload(ctx, w.bvh, layout=args.layout)
+    bvh_q = hcc.hcc_bvh_upload(ctx, w.bvh, layout="quantised")
     cut = hcc.hcc_select_cut(ctx, bvh, C, 0.125)
     hcc.hcc_reserve(ctx, n, K)
     org = torch.from_numpy(w.rays.org).to(dev)
@@ -204,57 +206,69 @@ def run_ours(args, rank, world, local_rank):
     hits = torch.empty((n, 4), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(method, ev=None):
-        """One wavefront through the C ABI; ev = 5 events around the 4 stages."""
+    def step(method, ev=None, fused=True, bvh_h=None):
+        """One wavefront through the C ABI; ev = 5 events around encode/sort/gather/trace."""
+        b = bvh_h or bvh
         if ev:
             ev[0].record(stream)
         if method == "nosort":
-            hcc.hcc_trace(ctx, bvh, org, dir_, hits)
             if ev:
-                for e in ev[1:]:
+                for e in ev[1:4]:
                     e.record(stream)
+            hcc.hcc_trace(ctx, b, org, dir_, hits)
+            if ev:
+                ev[4].record(stream)
             return
-        hcc.hcc_encode(ctx, method, bvh, cut if method == "hcc" else None, org, dir_, K, keys)
+        hcc.hcc_encode(ctx, method, b, cut if method == "hcc" else None, org, dir_, K, keys)
         if ev:
             ev[1].record(stream)
         hcc.hcc_sort(ctx, keys, K, n, perm)
         if ev:
             ev[2].record(stream)
-        hcc.hcc_gather(ctx, org, dir_, perm, sorg, sdir)
-        if ev:
-            ev[3].record(stream)
-        hcc.hcc_trace(ctx, bvh, sorg, sdir, hits, scatter=perm)
+        if fused:  # the trace fetches each ray through the sorted ids (Sec. 5)
+            if ev:
+                ev[3].record(stream)
+            hcc.hcc_trace_sorted(ctx, b, org, dir_, perm, hits)
+        else:
+            hcc.hcc_gather(ctx, org, dir_, perm, sorg, sdir)
+            if ev:
+                ev[3].record(stream)
+            hcc.hcc_trace(ctx, b, sorg, sdir, hits, scatter=perm)
         if ev:
             ev[4].record(stream)
 
-    def timed(method, steps, warmup):
+    def timed(method, steps, warmup, **kw):
         for _ in range(warmup):
-            step(method)
+            step(method, **kw)
         hcc.hcc_sync(ctx)
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
         barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(steps):
-            step(method, evs[i])
+            step(method, evs[i], **kw)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         hcc.hcc_sync(ctx)
         barrier(world)
         per = [evs[i][0].elapsed_time(evs[i][4]) for i in range(steps)]
         stages = [[evs[i][s].elapsed_time(evs[i][s + 1]) for i in range(steps)] for s in range(4)]
-        gap = [evs[i][4].elapsed_time(evs[i + 1][0]) for i in range(steps - 1)]
         total_ms = evs[0][0].elapsed_time(evs[-1][4])
-        return dict(per=per, stages=stages, total_ms=total_ms, wall_s=wall, gaps=gap)
+        return dict(per=per, stages=stages, total_ms=total_ms, wall_s=wall)
 
-    # NoSort and TwoPoint first (context for the headline), then the HCC headline
+    # context for the headline: NoSort, TwoPoint, the split-gather HCC path and
+    # the quantised node layout; then the HCC headline
     others = {}
-    for method in ("nosort", "twopoint"):
-        r = timed(method, max(3, args.steps // 2), args.warmup)
+    variants = [("nosort", "nosort", {}), ("twopoint", "twopoint", {}),
+                ("hcc_split_gather", "hcc", {"fused": False}),
+                ("nosort_quantised", "nosort", {"bvh_h": bvh_q}), ("hcc_quantised", "hcc", {"bvh_h": bvh_q})]
+    for name, method, kw in variants:
+        r = timed(method, max(3, args.steps // 2), args.warmup, **kw)
         t_max = reduce_max(r["total_ms"], world)
-        others[method] = dict(mrays_s=round(n * world * (len(r["per"])) / (t_max * 1e3), 2),
-                              ms_per_step=round(t_max / len(r["per"]), 3),
-                              stages_ms=[round(statistics.mean(s), 4) for s in r["stages"]])
+        others[name] = dict(mrays_s=round(n * world * (len(r["per"])) / (t_max * 1e3), 2),
+                            ms_per_step=round(t_max / len(r["per"]), 3),
+                            stages_ms=dict(zip(("encode", "sort", "gather", "trace"),
+                                               [round(statistics.mean(x), 4) for x in r["stages"]])))
     with ClockSampler(local_rank) as clk:
         r = timed("hcc", args.steps, args.warmup)
     clocks = clk.summary()
@@ -264,7 +278,8 @@ def run_ours(args, rank, world, local_rank):
     per = sorted(r["per"])
     p50 = statistics.median(per)
     p99 = per[min(len(per) - 1, int(round(0.99 * (len(per) - 1))))]
-    st = [statistics.mean(s) for s in r["stages"]]
+    st = [statistics.mean(x) for x in r["stages"]]
+    g_split = others["hcc_split_gather"]["stages_ms"]["gather"]
 
     # e2e through the public host-buffer call: H2D rays, pipeline, D2H hits
     h_org = torch.empty((n, 4), dtype=torch.float32, pin_memory=True)
@@ -293,11 +308,12 @@ def run_ours(args, rank, world, local_rank):
 
     # work counts of the trace (order-independent per ray) for the ALU roofline
     counts = hcc.hcc_trace_counts(ctx, bvh, org, dir_)
+    hcc.hcc_bvh_destroy(bvh_q)
     hbm, sm_max, peak_kind = peaks()
     clk_mhz = clocks.get("sm_max_mhz") or sm_max
     alu_peak = SMS * LANES_PER_SM * clk_mhz * 1e6 / 1e12  # Tops/s
     trace_ms = st[3]
-    work = counts["node_visits"] * OPS_PER_NODE + counts["tri_tests"] * OPS_PER_TRI
+    work = counts["node_visits"] * OPS_PER_NODE[args.layout] + counts["tri_tests"] * OPS_PER_TRI
     achieved = work / (trace_ms * 1e-3) / 1e12
     sort_passes = active_digit_passes(keys, K)
     sb = sort_bytes_per_key(sort_passes)
@@ -306,8 +322,9 @@ def run_ours(args, rank, world, local_rank):
                        frac=round(BYTES_ENCODE * n / (st[0] * 1e6) / hbm, 3)),
         "sort": dict(ms=round(st[1], 4), bound="hbm", active_passes=sort_passes, bytes_per_key=sb,
                      achieved_gbs=round(sb * n / (st[1] * 1e6), 1), frac=round(sb * n / (st[1] * 1e6) / hbm, 3)),
-        "gather": dict(ms=round(st[2], 4), bound="hbm", achieved_gbs=round(BYTES_GATHER * n / (st[2] * 1e6), 1),
-                       frac=round(BYTES_GATHER * n / (st[2] * 1e6) / hbm, 3)),
+        "gather": dict(ms=0.0, fused_into_trace=True, split_kernel_ms=round(g_split, 4), bound="hbm",
+                       split_achieved_gbs=round(BYTES_GATHER * n / (g_split * 1e6), 1),
+                       split_frac=round(BYTES_GATHER * n / (g_split * 1e6) / hbm, 3)),
         "trace": dict(ms=round(st[3], 4), bound="alu", achieved_tops=round(achieved, 3),
                       frac=round(achieved / alu_peak, 3),
                       node_visits_per_ray=round(counts["node_visits"] / n, 2),
@@ -317,7 +334,8 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name + f" ({n} secondary rays), HCC cut {C}, {K}-bit keys",
+        "config": {"workload": w.name + f" ({n} secondary rays), HCC cut {C}, {K}-bit keys, {args.layout} BVH nodes",
+                   "bvh_layout": args.layout, "gather": "fused into the trace (rays fetched through the sorted ids)",
                    "rays": n, "triangles": int(w.tris.shape[0]), "cut_size": C, "key_bits": K, "lambda": 0.125,
                    "l2": f"inputs larger than L2 ({n * 32 / 1e6:.0f} MB of rays per step)",
                    "parallelism": f"replica per GPU x{world}"},
@@ -326,14 +344,15 @@ def run_ours(args, rank, world, local_rank):
                       "trace": round(st[3], 4)},
         "methods": {"hcc": {"mrays_s": round(value, 2), "ms_per_step": round(ms_step, 3)}, **others},
         "speedup_vs_nosort": round(value / others["nosort"]["mrays_s"], 3),
+        "trace_speedup_vs_nosort": round(others["nosort"]["stages_ms"]["trace"] / st[3], 3),
         "speedup_vs_twopoint": round(value / others["twopoint"]["mrays_s"], 3),
         "hits_identical_hcc_vs_nosort": identical,
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(n * 32),
                 "d2h_bytes_per_step": int(n * 16), "call": "hcc_run_host"},
-        "gpu_launches": 10 * args.steps,
+        "gpu_launches": 9 * args.steps,
         "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 2), "unit": "Tops/s",
                      "frac": round(achieved / alu_peak, 3), "traffic": recorded_traffic(),
-                     "kernel": "k_trace (closest hit, HCC order)",
+                     "kernel": f"k_trace (closest hit, HCC order, {args.layout} nodes)",
                      "peak_source": f"{SMS} SMs x {LANES_PER_SM} lanes x {clk_mhz:.0f} MHz"},
         "stages": stages,
         "hbm_peak_gbs": hbm, "hbm_peak_source": peak_kind,
@@ -407,6 +426,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cut-size", type=int, default=32)
     ap.add_argument("--key-bits", type=int, default=32)
+    ap.add_argument("--layout", choices=["exact", "quantised"], default="exact")
     ap.add_argument("--quick", action="store_true", help="480x270 image, 200k triangles (development only)")
     ap.add_argument("--cpu-sample", type=int, default=1_500_000)
     ap.add_argument("--ref-sample", type=int, default=300_000)

@@ -149,6 +149,19 @@ const char *hcc_status_string(hcc_status s);
  * (malformed tree, leaf count outside 1..4, ids out of range), OOM, CUDA. */
 hcc_status hcc_bvh_upload(hcc_ctx *ctx, const hcc_bvh_desc *desc, hcc_bvh **out);
 
+/* Device layouts of the BVH's internal nodes (each node holds both
+ * children's boxes and references). */
+typedef enum hcc_bvh_layout {
+    HCC_BVH_QUANTISED = 0, /* 32 bytes: 8-bit child bounds on a per-node power-of-two grid, rounded outward */
+    HCC_BVH_EXACT = 1      /* 64 bytes: the children's exact FP32 boxes */
+} hcc_bvh_layout;
+
+/* hcc_bvh_upload with a choice of node layout.  Both layouts give the same
+ * hits (boxes only decide which triangles are tested); the quantised one
+ * halves node memory, the exact one avoids decoding work per node visit.
+ * Errors: as hcc_bvh_upload, plus INVALID_ARG for an unknown layout. */
+hcc_status hcc_bvh_upload_layout(hcc_ctx *ctx, const hcc_bvh_desc *desc, hcc_bvh_layout layout, hcc_bvh **out);
+
 /* Node and triangle counts, tree depth (root = 0) and the root box. Any
  * output pointer may be NULL. */
 hcc_status hcc_bvh_info(const hcc_bvh *bvh, uint32_t *num_nodes, uint32_t *num_tris, uint32_t *depth,
@@ -271,6 +284,18 @@ hcc_status hcc_trace(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *rays, int
                      const uint32_t *scatter, hcc_hit *hits);
 
 /*
+ * Trace in sorted order without a separate gather (the arrangement of
+ * Sec. 5: the trace kernel fetches each ray through the sorted indices).
+ * Thread j traces ray perm[j] of rays and writes its record to
+ * hits[perm[j]], so hits come out in input order, identical to hcc_trace on
+ * the unsorted rays; only the order in which rays are traced changes.
+ * perm: n uint32_t, a permutation of 0..n-1 (an entry >= n is skipped and
+ * reported as INVALID_ARG by hcc_sync).  Errors: as hcc_trace.
+ */
+hcc_status hcc_trace_sorted(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *rays, const uint32_t *perm,
+                            int any_hit, hcc_hit *hits);
+
+/*
  * Diagnostic (never on the timed path): trace like hcc_trace without
  * scatter and also count, over all rays, the internal BVH nodes visited and
  * the triangle tests run.  A ray's counts depend only on the ray, not on
@@ -286,11 +311,11 @@ hcc_status hcc_trace_counts(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *ra
 /*
  * The per-bounce reordering pipeline of Sec. 5 in one call:
  *   NOSORT:   trace(rays) -> hits
- *   HCC:      encode(cut) -> sort -> gather -> trace with scatter -> hits
- *   TWOPOINT: encode(root box) -> sort -> gather -> trace with scatter -> hits
+ *   HCC:      encode(cut) -> sort -> trace_sorted (fetch through perm) -> hits
+ *   TWOPOINT: encode(root box) -> sort -> trace_sorted -> hits
  * hits[i] is always the result of input ray i, so every method produces
- * the same array.  Keys, permutation and sorted rays live in the context's
- * scratch.  Device pointers; asynchronous on the context's stream.
+ * the same array.  Keys and permutation live in the context's scratch.
+ * Device pointers; asynchronous on the context's stream.
  * Errors: as the individual calls.
  */
 hcc_status hcc_run(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const hcc_cut *cut,

@@ -28,12 +28,13 @@ struct hcc_ctx {
     uint32_t *d_err = nullptr;
     std::string last_error;
     DevBuf sort_scratch;
-    DevBuf keys, perm, sorted_org, sorted_dir;  // hcc_run
+    DevBuf keys, perm;                          // hcc_run
     DevBuf in_org, in_dir, hits;                // hcc_run_host
 };
 
 struct hcc_bvh {
     int device = 0;
+    int layout = HCC_BVH_QUANTISED;
     uint4 *d_nodes = nullptr;
     float4 *d_tris = nullptr;
     uint32_t num_nodes = 0, num_internal = 0, num_tris = 0, depth = 0;
@@ -310,8 +311,7 @@ hcc_status hcc_destroy(hcc_ctx *ctx) {
     {
         DeviceGuard g(ctx->device);
         cudaStreamSynchronize(ctx->stream);
-        for (DevBuf *b : {&ctx->sort_scratch, &ctx->keys, &ctx->perm, &ctx->sorted_org, &ctx->sorted_dir,
-                          &ctx->in_org, &ctx->in_dir, &ctx->hits})
+        for (DevBuf *b : {&ctx->sort_scratch, &ctx->keys, &ctx->perm, &ctx->in_org, &ctx->in_dir, &ctx->hits})
             release(*b);
         if (ctx->d_err) cudaFree(ctx->d_err);
     }
@@ -336,8 +336,6 @@ hcc_status hcc_reserve(hcc_ctx *ctx, uint64_t max_n, uint32_t max_key_bits) {
         return st;
     if ((st = ensure(ctx, ctx->keys, max_n * ksz, "keys")) != HCC_OK) return st;
     if ((st = ensure(ctx, ctx->perm, max_n * 4, "perm")) != HCC_OK) return st;
-    if ((st = ensure(ctx, ctx->sorted_org, max_n * 16, "sorted rays")) != HCC_OK) return st;
-    if ((st = ensure(ctx, ctx->sorted_dir, max_n * 16, "sorted rays")) != HCC_OK) return st;
     return HCC_OK;
 }
 
@@ -365,8 +363,14 @@ hcc_status hcc_sync(hcc_ctx *ctx) {
 // ------------------------------------------------------------------- BVH
 
 hcc_status hcc_bvh_upload(hcc_ctx *ctx, const hcc_bvh_desc *d, hcc_bvh **out) {
+    return hcc_bvh_upload_layout(ctx, d, HCC_BVH_QUANTISED, out);
+}
+
+hcc_status hcc_bvh_upload_layout(hcc_ctx *ctx, const hcc_bvh_desc *d, hcc_bvh_layout layout, hcc_bvh **out) {
     if (!ctx || !d || !out) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
+    if (layout != HCC_BVH_QUANTISED && layout != HCC_BVH_EXACT)
+        return fail(ctx, HCC_ERR_INVALID_ARG, "unknown BVH layout");
     if (d->num_nodes == 0 || d->num_tris == 0) return fail(ctx, HCC_ERR_INVALID_ARG, "empty BVH");
     if (!d->lo || !d->hi || !d->left || !d->right || !d->first || !d->count || !d->tris || !d->order)
         return fail(ctx, HCC_ERR_INVALID_ARG, "NULL array in hcc_bvh_desc");
@@ -408,10 +412,21 @@ hcc_status hcc_bvh_upload(hcc_ctx *ctx, const hcc_bvh_desc *d, hcc_bvh **out) {
         if (d->left[k] < 0) return REF_LEAF | ((d->count[k] - 1u) << 29) | d->first[k];
         return (uint32_t)qidx[k];
     };
-    std::vector<uint32_t> words((size_t)std::max<size_t>(internal.size(), 1) * 8, 0u);
+    const size_t wpn = layout == HCC_BVH_EXACT ? 16 : 8;  // 32-bit words per node
+    std::vector<uint32_t> words((size_t)std::max<size_t>(internal.size(), 1) * wpn, 0u);
     for (size_t i = 0; i < internal.size(); ++i) {
         const int32_t k = internal[i], l = d->left[k], r = d->right[k];
-        quantise_node(d->lo + 3 * l, d->hi + 3 * l, d->lo + 3 * r, d->hi + 3 * r, ref_of(l), ref_of(r), &words[8 * i]);
+        uint32_t *w = &words[wpn * i];
+        if (layout == HCC_BVH_QUANTISED) {
+            quantise_node(d->lo + 3 * l, d->hi + 3 * l, d->lo + 3 * r, d->hi + 3 * r, ref_of(l), ref_of(r), w);
+        } else {
+            const float f[12] = {d->lo[3 * l], d->lo[3 * l + 1], d->lo[3 * l + 2], d->hi[3 * l],
+                                 d->hi[3 * l + 1], d->hi[3 * l + 2], d->lo[3 * r], d->lo[3 * r + 1],
+                                 d->lo[3 * r + 2], d->hi[3 * r], d->hi[3 * r + 1], d->hi[3 * r + 2]};
+            std::memcpy(w, f, sizeof f);
+            w[12] = ref_of(l);
+            w[13] = ref_of(r);
+        }
     }
     std::vector<float> tri((size_t)T * 12);
     for (uint32_t k = 0; k < T; ++k) {
@@ -432,6 +447,7 @@ hcc_status hcc_bvh_upload(hcc_ctx *ctx, const hcc_bvh_desc *d, hcc_bvh **out) {
     hcc_bvh *b = new (std::nothrow) hcc_bvh;
     if (!b) return fail(ctx, HCC_ERR_OOM, "host allocation");
     b->device = ctx->device;
+    b->layout = layout;
     b->num_nodes = N;
     b->num_internal = (uint32_t)internal.size();
     b->num_tris = T;
@@ -636,12 +652,42 @@ hcc_status hcc_trace(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *rays, int
     DeviceGuard g(ctx->device);
     TraceArgs a;
     a.nodes = bvh->d_nodes;
+    a.layout = bvh->layout;
     a.tris = bvh->d_tris;
     a.root_ref = bvh->root_ref;
     a.org = reinterpret_cast<const float4 *>(rays->org_tmin);
     a.dir = reinterpret_cast<const float4 *>(rays->dir_tmax);
     a.n = rays->n;
+    a.gather = nullptr;
     a.scatter = scatter;
+    a.hits = reinterpret_cast<int4 *>(hits);
+    a.err = ctx->d_err;
+    a.counts = nullptr;
+    cudaError_t e = launch_trace(ctx->stream, a, any_hit);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "trace launch");
+    return HCC_OK;
+}
+
+hcc_status hcc_trace_sorted(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *rays, const uint32_t *perm,
+                            int any_hit, hcc_hit *hits) {
+    if (!ctx) return HCC_ERR_INVALID_ARG;
+    hcc_status st = check_rays(ctx, rays, "rays");
+    if (st != HCC_OK) return st;
+    if (!bvh) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL BVH");
+    if (rays->n == 0) return HCC_OK;
+    if (!hits || !aligned(hits, 16)) return fail(ctx, HCC_ERR_INVALID_ARG, "hits NULL or not 16-byte aligned");
+    if (!perm || !aligned(perm, 4)) return fail(ctx, HCC_ERR_INVALID_ARG, "perm NULL or misaligned");
+    DeviceGuard g(ctx->device);
+    TraceArgs a;
+    a.nodes = bvh->d_nodes;
+    a.layout = bvh->layout;
+    a.tris = bvh->d_tris;
+    a.root_ref = bvh->root_ref;
+    a.org = reinterpret_cast<const float4 *>(rays->org_tmin);
+    a.dir = reinterpret_cast<const float4 *>(rays->dir_tmax);
+    a.n = rays->n;
+    a.gather = perm;
+    a.scatter = perm;
     a.hits = reinterpret_cast<int4 *>(hits);
     a.err = ctx->d_err;
     a.counts = nullptr;
@@ -667,11 +713,13 @@ hcc_status hcc_trace_counts(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *ra
     cudaError_t e = cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), ctx->stream);
     TraceArgs a;
     a.nodes = bvh->d_nodes;
+    a.layout = bvh->layout;
     a.tris = bvh->d_tris;
     a.root_ref = bvh->root_ref;
     a.org = reinterpret_cast<const float4 *>(rays->org_tmin);
     a.dir = reinterpret_cast<const float4 *>(rays->dir_tmax);
     a.n = rays->n;
+    a.gather = nullptr;
     a.scatter = nullptr;
     a.hits = reinterpret_cast<int4 *>(tmp.p);
     a.err = ctx->d_err;
@@ -707,14 +755,10 @@ hcc_status hcc_run(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const hc
     const size_t ksz = key_bits > 32 ? 8 : 4;
     if ((st = ensure(ctx, ctx->keys, n * ksz, "keys")) != HCC_OK) return st;
     if ((st = ensure(ctx, ctx->perm, n * 4, "perm")) != HCC_OK) return st;
-    if ((st = ensure(ctx, ctx->sorted_org, n * 16, "sorted rays")) != HCC_OK) return st;
-    if ((st = ensure(ctx, ctx->sorted_dir, n * 16, "sorted rays")) != HCC_OK) return st;
     if ((st = hcc_encode(ctx, method, bvh, cut, rays, key_bits, ctx->keys.p)) != HCC_OK) return st;
     uint32_t *perm = static_cast<uint32_t *>(ctx->perm.p);
     if ((st = hcc_sort(ctx, ctx->keys.p, key_bits, n, perm)) != HCC_OK) return st;
-    hcc_rays sorted{static_cast<float *>(ctx->sorted_org.p), static_cast<float *>(ctx->sorted_dir.p), n};
-    if ((st = hcc_gather(ctx, rays, perm, &sorted)) != HCC_OK) return st;
-    return hcc_trace(ctx, bvh, &sorted, any_hit, perm, hits);
+    return hcc_trace_sorted(ctx, bvh, rays, perm, any_hit, hits);
 }
 
 hcc_status hcc_run_host(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const hcc_cut *cut,

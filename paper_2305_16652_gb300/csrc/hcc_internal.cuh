@@ -30,6 +30,10 @@ constexpr uint32_t ERR_INDEX = 4u;  // a permutation entry was out of range (acc
 constexpr uint32_t REF_LEAF = 0x80000000u;
 constexpr uint32_t REF_TRI_MASK = 0x1FFFFFFFu;
 
+// Exact layout: one internal node = 64 bytes = four uint4: the children's
+// FP32 boxes c0.lo.xyz c0.hi.x | c0.hi.yz c1.lo.xy | c1.lo.z c1.hi.xyz |
+// ref0 ref1 0 0.
+
 // Triangle record = three float4: (v0.xyz, id bits), (e1.xyz, 0), (e2.xyz, 0)
 // with e1 = v1 - v0, e2 = v2 - v0 rounded to float.
 
@@ -52,13 +56,15 @@ cudaError_t launch_gather(cudaStream_t s, const float4 *in_org, const float4 *in
                           const uint32_t *perm, float4 *out_org, float4 *out_dir, uint64_t n, uint32_t *err);
 
 struct TraceArgs {
-    const uint4 *nodes;  // 2 per node
+    const uint4 *nodes;  // 2 (quantised) or 4 (exact) per node
+    int layout;          // 0 = 32-byte quantised, 1 = 64-byte exact
     const float4 *tris;  // 3 per triangle
     uint32_t root_ref;
     const float4 *org;
     const float4 *dir;
     uint64_t n;
-    const uint32_t *scatter;
+    const uint32_t *gather;   // ray j is read from org/dir[gather[j]] (NULL = j)
+    const uint32_t *scatter;  // its hit goes to hits[scatter[j]] (NULL = j)
     int4 *hits;
     uint32_t *err;
     unsigned long long *counts;  // diagnostic: node visits, triangle tests (NULL = off)

@@ -29,7 +29,8 @@ constexpr int SORT_TILE = SORT_BLOCK * SORT_ITEMS;
 constexpr uint32_t ST_AGG = 1u << 30;  // tile count of this digit available
 constexpr uint32_t ST_INC = 2u << 30;  // inclusive prefix of this digit available
 constexpr uint32_t ST_VALUE = (1u << 30) - 1u;
-constexpr uint32_t SPIN_LIMIT = 1u << 22;
+constexpr uint32_t SPIN_LIMIT = 1u << 22;  // total status reads a tile may wait
+constexpr int LOOKBACK = 8;                // predecessors read per look-back round
 
 enum : int { KB_USER = 0, KB_A = 1, KB_B = 2, KB_NONE = 3 };
 enum : int { VB_SYNTH = 0, VB_A = 1, VB_PERM = 2 };
@@ -102,38 +103,69 @@ __device__ __forceinline__ K key_mask(uint32_t key_bits) {
     return key_bits >= 8 * sizeof(K) ? (K)~(K)0 : (K)(((K)1 << key_bits) - 1);
 }
 
-// One read of all keys: digit histograms of every pass.  Lanes with equal
-// digits are combined (ballot bit-split) so one leader adds their count;
-// each warp has its own shared-memory copy of the histograms.
+// One read of all keys: digit histograms of every pass.  Keys of ray
+// batches are heavily skewed (one digit value often holds most keys), so
+// each warp first picks the most common digit of its first 32 keys for each
+// pass and counts that value in a register; every other digit goes to a
+// shared-memory atomic, where collisions are then rare.
 template <typename K>
 __global__ void __launch_bounds__(SORT_BLOCK) k_hist(const K *__restrict__ keys, uint64_t n, uint32_t key_bits,
                                                      int passes, SortHeader *h) {
-    extern __shared__ uint32_t sh[];  // [SORT_WARPS][passes * RADIX]
-    const int nb = passes * RADIX;
-    for (int i = threadIdx.x; i < SORT_WARPS * nb; i += blockDim.x) sh[i] = 0;
+    __shared__ uint32_t sh[MAX_PASSES * RADIX];
+    for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) sh[i] = 0;
     __syncthreads();
-    uint32_t *wh = sh + (threadIdx.x >> 5) * nb;
     const K mask = key_mask<K>(key_bits);
-    const uint32_t lt = lanemask_lt();
+    const uint32_t lane = threadIdx.x & 31;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t nround = (n + stride - 1) / stride * stride;  // uniform trip count per warp
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nround; i += stride) {
-        const bool valid = i < n;
-        const uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
-        const K k = valid ? (__ldcs(keys + i) & mask) : (K)0;
-        for (int p = 0; p < passes; ++p) {
-            const uint32_t d = (uint32_t)(k >> (8 * p)) & 255u;
-            const uint32_t dbits = key_bits - 8u * p < 8u ? key_bits - 8u * p : 8u;
-            const uint32_t peers = digit_peers(d, dbits, vmask);
-            if (valid && (peers & lt) == 0) wh[p * RADIX + d] += (uint32_t)__popc(peers);
+    const uint64_t first = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // dominant digit per pass among the warp's first keys
+    const K k0 = first < n ? (keys[first] & mask) : (K)0;
+    uint32_t dom[MAX_PASSES], cnt[MAX_PASSES];
+#pragma unroll
+    for (int p = 0; p < MAX_PASSES; ++p) {
+        cnt[p] = 0;
+        dom[p] = 0;
+        if (p < passes) {
+            const uint32_t d = (uint32_t)(k0 >> (8 * p)) & 255u;
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, first < n ? d : 256u + lane);
+            uint32_t best = ((uint32_t)__popc(peers) << 9) | d;
+            best = __reduce_max_sync(0xFFFFFFFFu, best);
+            dom[p] = best & 511u;
+        }
+    }
+    constexpr int UNROLL = 8;  // independent loads in flight per thread
+    for (uint64_t base = first; base < n; base += UNROLL * stride) {
+        K kk[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            const uint64_t i = base + (uint64_t)u * stride;
+            kk[u] = i < n ? (__ldcs(keys + i) & mask) : (K)0;
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            if (base + (uint64_t)u * stride >= n) break;
+#pragma unroll
+            for (int p = 0; p < MAX_PASSES; ++p) {
+                if (p < passes) {
+                    const uint32_t d = (uint32_t)(kk[u] >> (8 * p)) & 255u;
+                    if (d == dom[p])
+                        ++cnt[p];
+                    else
+                        atomicAdd(&sh[p * RADIX + d], 1u);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < MAX_PASSES; ++p) {
+        if (p < passes) {
+            const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, cnt[p]);
+            if (lane == 0 && c && dom[p] < 256u) atomicAdd(&sh[p * RADIX + dom[p]], c);
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-        uint32_t c = 0;
-        for (int w = 0; w < SORT_WARPS; ++w) c += sh[w * nb + i];
-        if (c) atomicAdd(&h->hist[0][0] + i, c);
-    }
+    for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x)
+        if (sh[i]) atomicAdd(&h->hist[0][0] + i, sh[i]);
 }
 
 // Exclusive scan per pass, pass activity and buffer plan.  One block.
@@ -191,7 +223,7 @@ struct PassArgs {
 };
 
 template <typename K>
-__global__ void __launch_bounds__(SORT_BLOCK, 3) k_pass(PassArgs<K> a, int pass) {
+__global__ void __launch_bounds__(SORT_BLOCK, 4) k_pass(PassArgs<K> a, int pass) {
     const PassPlan pl = a.h->plan[pass];
     if (!pl.active) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -232,7 +264,12 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) k_pass(PassArgs<K> a, int pass)
         key[i] = valid ? (__ldcs(kin + idx) & mask) : (K)0;
         val[i] = valid ? (pl.src_vals == VB_SYNTH ? (uint32_t)idx : __ldcs(vin + idx)) : 0u;
     }
-    // Warp-level stable ranking: peers with the same digit, counted in item order.
+    // Warp-level stable ranking: the lanes holding the same digit are found
+    // with one ballot per digit bit; the lowest of them adds their number to
+    // the warp's counter of that digit and the old value, broadcast to the
+    // group, is the rank of the group's first item.  The warp issues its
+    // atomics in item order, so ranks follow the input order (stable), and
+    // nothing waits between items.
     const uint32_t lt = lanemask_lt();
     const uint32_t dbits = a.key_bits - shift < 8u ? a.key_bits - shift : 8u;
     uint32_t *wh = s_whist[warp];
@@ -241,12 +278,11 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) k_pass(PassArgs<K> a, int pass)
         const bool valid = wfirst + (uint32_t)i * 32 < tile_n;
         const uint32_t d = (uint32_t)(key[i] >> shift) & 255u;
         const uint32_t peers = digit_peers(d, dbits, __ballot_sync(0xFFFFFFFFu, valid));
-        const uint32_t below = __popc(peers & lt);
-        const uint32_t prior = valid ? wh[d] : 0u;
-        rank[i] = prior + below;
-        __syncwarp();
-        if (valid && below == 0) wh[d] = prior + __popc(peers);
-        __syncwarp();
+        const uint32_t leader = __ffs(peers) - 1;
+        uint32_t prior = 0;
+        if (valid && (uint32_t)lane == leader) prior = atomicAdd(&wh[d], (uint32_t)__popc(peers));
+        prior = __shfl_sync(0xFFFFFFFFu, prior, valid ? leader : lane);
+        rank[i] = prior + __popc(peers & lt);
     }
     __syncthreads();
 
@@ -258,40 +294,12 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) k_pass(PassArgs<K> a, int pass)
         s_whist[w][tid] = total;
         total += c;
     }
-    // Publish this tile's count, then look back for the exclusive prefix.
+    // Publish this tile's count of digit tid at once (tile 0 knows its prefix).
     uint32_t *st = a.status + ((size_t)pass * a.num_tiles + tile) * RADIX;
-    uint32_t excl;
-    if (tile == 0) {
-        excl = a.h->start[pass][tid];
-        st_relaxed(st + tid, ST_INC | ((excl + total) & ST_VALUE));
-    } else {
+    if (tile == 0)
+        st_relaxed(st + tid, ST_INC | ((a.h->start[pass][tid] + total) & ST_VALUE));
+    else
         st_relaxed(st + tid, ST_AGG | total);
-        excl = 0;
-        int64_t j = (int64_t)tile - 1;
-        uint32_t spins = 0;
-        bool timed_out = false;
-        while (j >= 0) {
-            const uint32_t s = ld_relaxed(a.status + ((size_t)pass * a.num_tiles + (uint64_t)j) * RADIX + tid);
-            const uint32_t flag = s & ~ST_VALUE;
-            if (flag == 0) {
-                if (++spins > SPIN_LIMIT || ld_relaxed(&a.h->abort)) {
-                    timed_out = true;
-                    break;
-                }
-                continue;
-            }
-            excl += s & ST_VALUE;
-            if (flag == ST_INC) break;
-            --j;
-        }
-        if (timed_out) {
-            atomicOr(a.err, ERR_TIMEOUT);
-            atomicExch(&a.h->abort, 1u);
-            s_abort = 1;
-        }
-        st_relaxed(st + tid, ST_INC | ((excl + total) & ST_VALUE));
-    }
-    s_base[tid] = excl;
     // Exclusive scan of the tile's digit counts (positions in shared memory).
     uint32_t incl = total;
 #pragma unroll
@@ -305,9 +313,8 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) k_pass(PassArgs<K> a, int pass)
     for (int w = 0; w < warp; ++w) wpre += s_wsum[w];
     s_local[tid] = wpre + incl - total;
     __syncthreads();
-    if (s_abort) return;
-
-    // Reorder the tile by digit in shared memory (stable).
+    // Reorder the tile by digit in shared memory (stable) while the
+    // predecessors finish; this needs no global offsets yet.
 #pragma unroll
     for (int i = 0; i < SORT_ITEMS; ++i) {
         if (wfirst + (uint32_t)i * 32 < tile_n) {
@@ -317,7 +324,58 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) k_pass(PassArgs<K> a, int pass)
             s_vals[pos] = val[i];
         }
     }
+    // Decoupled look-back for digit tid: read LOOKBACK predecessors per round
+    // (independent loads), consume them newest first until an inclusive
+    // prefix is found; back off with a short sleep while one is not ready.
+    uint32_t excl;
+    if (tile == 0) {
+        excl = a.h->start[pass][tid];
+    } else {
+        excl = 0;
+        int64_t j = (int64_t)tile - 1;
+        uint32_t spins = 0;
+        bool timed_out = false, done = false;
+        const uint32_t *col = a.status + (size_t)pass * a.num_tiles * RADIX + tid;
+        while (!done) {
+            uint32_t sv[LOOKBACK];
+#pragma unroll
+            for (int w = 0; w < LOOKBACK; ++w)
+                sv[w] = (j - w >= 0) ? ld_relaxed(col + (size_t)(j - w) * RADIX) : ST_INC;
+            int used = 0;
+            bool stalled = false;
+#pragma unroll
+            for (int w = 0; w < LOOKBACK; ++w) {
+                if (done || stalled) continue;
+                const uint32_t flag = sv[w] & ~ST_VALUE;
+                if (flag == 0) {
+                    stalled = true;
+                    continue;
+                }
+                if (j - w >= 0) excl += sv[w] & ST_VALUE;
+                ++used;
+                if (flag == ST_INC) done = true;
+            }
+            j -= used;
+            if (done) break;
+            if (stalled) {
+                if (++spins > SPIN_LIMIT / LOOKBACK || ((spins & 63u) == 0 && ld_relaxed(&a.h->abort))) {
+                    timed_out = true;
+                    break;
+                }
+                __nanosleep(spins < 8 ? 32u * spins : 256u);
+            }
+        }
+        if (timed_out) {
+            atomicOr(a.err, ERR_TIMEOUT);
+            atomicExch(&a.h->abort, 1u);
+            s_abort = 1;
+        }
+        st_relaxed(st + tid, ST_INC | ((excl + total) & ST_VALUE));
+    }
+    s_base[tid] = excl;
     __syncthreads();
+    if (s_abort) return;
+
     // Write runs of equal digits to their global positions.
     K *kout = pl.dst_keys == KB_A ? a.ka : (pl.dst_keys == KB_B ? a.kb : nullptr);
     uint32_t *vout = pl.dst_vals == VB_A ? a.va : a.perm;
@@ -353,10 +411,7 @@ cudaError_t run_sort(cudaStream_t s, const K *keys, uint32_t key_bits, uint64_t 
     const uint64_t hcap = (uint64_t)(sms > 0 ? sms : 1) * 4;
     if (hblocks > hcap) hblocks = hcap;
     if (hblocks == 0) hblocks = 1;
-    const size_t hsm = (size_t)SORT_WARPS * passes * RADIX * sizeof(uint32_t);
-    e = cudaFuncSetAttribute(k_hist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
-    if (e != cudaSuccess) return e;
-    k_hist<K><<<(unsigned)hblocks, SORT_BLOCK, hsm, s>>>(keys, n, key_bits, passes, h);
+    k_hist<K><<<(unsigned)hblocks, SORT_BLOCK, 0, s>>>(keys, n, key_bits, passes, h);
     k_plan<<<1, RADIX, 0, s>>>(h, passes, n);
     PassArgs<K> a;
     a.user_keys = keys;

@@ -1,7 +1,8 @@
-// Closest-hit / any-hit tracing: stack-based traversal of the quantised BVH2
-// (Sec. 3.1) with the Moller-Trumbore ray/triangle test (1997).  GB300 has no
-// ray-tracing cores, so traversal is software: one thread per ray, 32-byte
-// nodes holding both children's 8-bit boxes, a per-thread stack of
+// Closest-hit / any-hit tracing: stack-based traversal of the BVH2 (Sec. 3.1)
+// with the Moller-Trumbore ray/triangle test (1997).  GB300 has no
+// ray-tracing cores, so traversal is software: one thread per ray, each
+// internal node holding both children's boxes (32-byte 8-bit quantised
+// layout, or 64-byte exact FP32 layout), a per-thread stack of
 // (node, entry distance) pairs.
 //
 // Robustness: decoded child boxes are rounded outward (they contain the exact
@@ -76,14 +77,82 @@ __device__ __forceinline__ bool intersect(const Ray &r, const float4 &A, const f
     return t > r.tmin && t < r.tmax;
 }
 
+constexpr uint32_t REF_NONE = 0xFFFFFFFFu;  // no node (empty stack, no postponed leaf)
+
+// Both children's boxes of an internal node, decoded for the slab test.
+struct ChildBoxes {
+    float lo0x, lo0y, lo0z, hi0x, hi0y, hi0z, lo1x, lo1y, lo1z, hi1x, hi1y, hi1z;
+    uint32_t ref0, ref1;
+};
+
+// 32-byte quantised node: bounds are origin + q * 2^E rounded outward.
+__device__ __forceinline__ void fetch_quant8(const uint4 *nodes, uint32_t ref, ChildBoxes &c) {
+    const uint4 A = __ldg(nodes + 2 * (size_t)ref);
+    const uint4 B = __ldg(nodes + 2 * (size_t)ref + 1);
+    const float ox = __uint_as_float(A.x & 0xFFFFFF00u);
+    const float oy = __uint_as_float(A.y & 0xFFFFFF00u);
+    const float oz = __uint_as_float(A.z & 0xFFFFFF00u);
+    const float sx = __uint_as_float((A.x & 0xFFu) << 23);
+    const float sy = __uint_as_float((A.y & 0xFFu) << 23);
+    const float sz = __uint_as_float((A.z & 0xFFu) << 23);
+    c.lo0x = __fmaf_rd(byte_to_float(A.w, SEL0), sx, ox);
+    c.lo0y = __fmaf_rd(byte_to_float(A.w, SEL1), sy, oy);
+    c.lo0z = __fmaf_rd(byte_to_float(A.w, SEL2), sz, oz);
+    c.hi0x = __fmaf_ru(byte_to_float(A.w, SEL3), sx, ox);
+    c.hi0y = __fmaf_ru(byte_to_float(B.x, SEL0), sy, oy);
+    c.hi0z = __fmaf_ru(byte_to_float(B.x, SEL1), sz, oz);
+    c.lo1x = __fmaf_rd(byte_to_float(B.x, SEL2), sx, ox);
+    c.lo1y = __fmaf_rd(byte_to_float(B.x, SEL3), sy, oy);
+    c.lo1z = __fmaf_rd(byte_to_float(B.y, SEL0), sz, oz);
+    c.hi1x = __fmaf_ru(byte_to_float(B.y, SEL1), sx, ox);
+    c.hi1y = __fmaf_ru(byte_to_float(B.y, SEL2), sy, oy);
+    c.hi1z = __fmaf_ru(byte_to_float(B.y, SEL3), sz, oz);
+    c.ref0 = B.z;
+    c.ref1 = B.w;
+}
+
+// 64-byte exact node: the children's FP32 boxes as stored in the input BVH.
+__device__ __forceinline__ void fetch_exact(const uint4 *nodes, uint32_t ref, ChildBoxes &c) {
+    const float4 *f = reinterpret_cast<const float4 *>(nodes) + 4 * (size_t)ref;
+    const float4 n0 = __ldg(f), n1 = __ldg(f + 1), n2 = __ldg(f + 2);
+    const uint4 n3 = __ldg(nodes + 4 * (size_t)ref + 3);
+    c.lo0x = n0.x;
+    c.lo0y = n0.y;
+    c.lo0z = n0.z;
+    c.hi0x = n0.w;
+    c.hi0y = n1.x;
+    c.hi0z = n1.y;
+    c.lo1x = n1.z;
+    c.lo1y = n1.w;
+    c.lo1z = n2.x;
+    c.hi1x = n2.y;
+    c.hi1y = n2.z;
+    c.hi1z = n2.w;
+    c.ref0 = n3.x;
+    c.ref1 = n3.y;
+}
+
+// Traversal loop ("while-while" with postponed leaves, Aila & Laine 2009):
+// a lane that reaches a leaf parks it and keeps descending until every lane
+// of the warp holds a leaf, so triangle tests run with full warps; the
+// nearer child is visited first and the farther one is pushed with its
+// entry distance, which lets a pop skip subtrees beyond the best hit.
 // COUNT = true is a diagnostic variant that also adds up internal-node
 // visits and triangle tests into a.counts[0..1] (never the timed kernel).
-template <bool ANY, bool COUNT>
+template <bool ANY, bool COUNT, int LAYOUT>
 __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
     const uint64_t i = (uint64_t)blockIdx.x * TRACE_BLOCK + threadIdx.x;
     uint32_t n_nodes = 0, n_tris = 0;
     if (i >= a.n) return;
-    const float4 o4 = __ldcs(a.org + i), d4 = __ldcs(a.dir + i);
+    uint64_t src = i;
+    if (a.gather) {
+        src = a.gather[i];
+        if (src >= a.n) {  // invalid permutation entry: report, never read out of bounds
+            atomicOr(a.err, ERR_INDEX);
+            return;
+        }
+    }
+    const float4 o4 = __ldcs(a.org + src), d4 = __ldcs(a.dir + src);
     Ray r;
     r.ox = o4.x;
     r.oy = o4.y;
@@ -103,96 +172,88 @@ __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
     uint32_t st_ref[STACK];
     float st_t[STACK];
     int sp = 0;
-    uint32_t ref = a.root_ref;
     bool overflow = false;
-
-    for (;;) {
-        bool have = true;
-        // descend through internal nodes until a leaf is reached or the stack runs dry
-        while (!(ref & REF_LEAF)) {
-            const uint4 A = __ldg(a.nodes + 2 * (size_t)ref);
-            const uint4 B = __ldg(a.nodes + 2 * (size_t)ref + 1);
+    // next pending subtree that can still hold a closer hit, or REF_NONE
+    auto pop = [&]() -> uint32_t {
+        while (sp > 0) {
+            --sp;
+            if (st_t[sp] <= tcap) return st_ref[sp];
+        }
+        return REF_NONE;
+    };
+    uint32_t node = a.root_ref, leaf = REF_NONE;
+    if (node & REF_LEAF) {
+        leaf = node;
+        node = REF_NONE;
+    }
+    while (node != REF_NONE || leaf != REF_NONE) {
+        // internal nodes: descend until every lane has a leaf parked
+        while (node != REF_NONE && !(node & REF_LEAF)) {
+            ChildBoxes c;
+            if (LAYOUT == 0)
+                fetch_quant8(a.nodes, node, c);
+            else
+                fetch_exact(a.nodes, node, c);
             if (COUNT) ++n_nodes;
-            const float ox = __uint_as_float(A.x & 0xFFFFFF00u);
-            const float oy = __uint_as_float(A.y & 0xFFFFFF00u);
-            const float oz = __uint_as_float(A.z & 0xFFFFFF00u);
-            const float sx = __uint_as_float((A.x & 0xFFu) << 23);
-            const float sy = __uint_as_float((A.y & 0xFFu) << 23);
-            const float sz = __uint_as_float((A.z & 0xFFu) << 23);
             float tn0, tf0, tn1, tf1;
-            slab(r, __fmaf_rd(byte_to_float(A.w, SEL0), sx, ox), __fmaf_rd(byte_to_float(A.w, SEL1), sy, oy),
-                 __fmaf_rd(byte_to_float(A.w, SEL2), sz, oz), __fmaf_ru(byte_to_float(A.w, SEL3), sx, ox),
-                 __fmaf_ru(byte_to_float(B.x, SEL0), sy, oy), __fmaf_ru(byte_to_float(B.x, SEL1), sz, oz), tcap,
-                 tn0, tf0);
-            slab(r, __fmaf_rd(byte_to_float(B.x, SEL2), sx, ox), __fmaf_rd(byte_to_float(B.x, SEL3), sy, oy),
-                 __fmaf_rd(byte_to_float(B.y, SEL0), sz, oz), __fmaf_ru(byte_to_float(B.y, SEL1), sx, ox),
-                 __fmaf_ru(byte_to_float(B.y, SEL2), sy, oy), __fmaf_ru(byte_to_float(B.y, SEL3), sz, oz), tcap,
-                 tn1, tf1);
+            slab(r, c.lo0x, c.lo0y, c.lo0z, c.hi0x, c.hi0y, c.hi0z, tcap, tn0, tf0);
+            slab(r, c.lo1x, c.lo1y, c.lo1z, c.hi1x, c.hi1y, c.hi1z, tcap, tn1, tf1);
             const bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
             if (h0 && h1) {
                 const bool first0 = tn0 <= tn1;
                 if (sp == STACK) {
                     overflow = true;
-                    have = false;
+                    node = leaf = REF_NONE;
                     break;
                 }
-                st_ref[sp] = first0 ? B.w : B.z;
+                st_ref[sp] = first0 ? c.ref1 : c.ref0;
                 st_t[sp] = first0 ? tn1 : tn0;
                 ++sp;
-                ref = first0 ? B.z : B.w;
+                node = first0 ? c.ref0 : c.ref1;
             } else if (h0) {
-                ref = B.z;
+                node = c.ref0;
             } else if (h1) {
-                ref = B.w;
+                node = c.ref1;
             } else {
-                // pop the nearest pending subtree that can still hold a closer hit
-                have = false;
-                while (sp > 0) {
-                    --sp;
-                    if (st_t[sp] <= tcap) {
-                        ref = st_ref[sp];
-                        have = true;
-                        break;
-                    }
+                node = pop();
+            }
+            if (node != REF_NONE && (node & REF_LEAF) && leaf == REF_NONE) {
+                leaf = node;
+                node = pop();
+            }
+            if (__all_sync(__activemask(), leaf != REF_NONE)) break;
+        }
+        // leaves: the parked one, then any leaf that is next on the stack
+        while (leaf != REF_NONE) {
+            const uint32_t first = leaf & REF_TRI_MASK, cnt = ((leaf >> 29) & 3u) + 1u;
+            bool hit_any = false;
+            for (uint32_t k = 0; k < cnt; ++k) {
+                const float4 *rec = a.tris + 3 * (size_t)(first + k);
+                const float4 A = __ldg(rec), E1 = __ldg(rec + 1), E2 = __ldg(rec + 2);
+                if (COUNT) ++n_tris;
+                float t, u, v;
+                if (!intersect(r, A, E1, E2, t, u, v)) continue;
+                const int32_t prim = __float_as_int(A.w);
+                if (best_prim < 0 || t < best_t || (t == best_t && prim < best_prim)) {
+                    best_t = t;
+                    best_u = u;
+                    best_v = v;
+                    best_prim = prim;
+                    tcap = __fmul_rn(t, PRUNE_SLACK);
                 }
-                if (!have) break;
+                hit_any = true;
+                if (ANY) break;
             }
-        }
-        if (!have) break;
-        // leaf: test its triangles
-        const uint32_t first = ref & REF_TRI_MASK, cnt = ((ref >> 29) & 3u) + 1u;
-        bool done = false;
-        for (uint32_t k = 0; k < cnt; ++k) {
-            const float4 *rec = a.tris + 3 * (size_t)(first + k);
-            const float4 A = __ldg(rec), E1 = __ldg(rec + 1), E2 = __ldg(rec + 2);
-            if (COUNT) ++n_tris;
-            float t, u, v;
-            if (!intersect(r, A, E1, E2, t, u, v)) continue;
-            const int32_t prim = __float_as_int(A.w);
-            if (best_prim < 0 || t < best_t || (t == best_t && prim < best_prim)) {
-                best_t = t;
-                best_u = u;
-                best_v = v;
-                best_prim = prim;
-                tcap = __fmul_rn(t, PRUNE_SLACK);
-            }
-            if (ANY) {
-                done = true;
+            if (ANY && hit_any) {
+                node = leaf = REF_NONE;
                 break;
             }
-        }
-        if (done) break;
-        // continue with the nearest pending subtree
-        bool popped = false;
-        while (sp > 0) {
-            --sp;
-            if (st_t[sp] <= tcap) {
-                ref = st_ref[sp];
-                popped = true;
-                break;
+            leaf = REF_NONE;
+            if (node != REF_NONE && (node & REF_LEAF)) {
+                leaf = node;
+                node = pop();
             }
         }
-        if (!popped) break;
     }
     if (overflow) {
         atomicOr(a.err, ERR_STACK);
@@ -218,16 +279,24 @@ __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
 
 cudaError_t launch_trace(cudaStream_t s, const TraceArgs &a, int any_hit) {
     if (a.n == 0) return cudaSuccess;
-    const uint64_t blocks = (a.n + TRACE_BLOCK - 1) / TRACE_BLOCK;
+    const unsigned blocks = (unsigned)((a.n + TRACE_BLOCK - 1) / TRACE_BLOCK);
     const bool count = a.counts != nullptr;
+#define HCC_TRACE_LAUNCH(ANY, CNT)                                                  \
+    do {                                                                            \
+        if (a.layout == 0)                                                          \
+            k_trace<ANY, CNT, 0><<<blocks, TRACE_BLOCK, 0, s>>>(a);                 \
+        else                                                                        \
+            k_trace<ANY, CNT, 1><<<blocks, TRACE_BLOCK, 0, s>>>(a);                 \
+    } while (0)
     if (any_hit && count)
-        k_trace<true, true><<<(unsigned)blocks, TRACE_BLOCK, 0, s>>>(a);
+        HCC_TRACE_LAUNCH(true, true);
     else if (any_hit)
-        k_trace<true, false><<<(unsigned)blocks, TRACE_BLOCK, 0, s>>>(a);
+        HCC_TRACE_LAUNCH(true, false);
     else if (count)
-        k_trace<false, true><<<(unsigned)blocks, TRACE_BLOCK, 0, s>>>(a);
+        HCC_TRACE_LAUNCH(false, true);
     else
-        k_trace<false, false><<<(unsigned)blocks, TRACE_BLOCK, 0, s>>>(a);
+        HCC_TRACE_LAUNCH(false, false);
+#undef HCC_TRACE_LAUNCH
     return cudaGetLastError();
 }
 

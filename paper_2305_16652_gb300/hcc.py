@@ -66,6 +66,7 @@ def load(path: str = LIB_PATH):
         "hcc_reserve": [P, u64, u32],
         "hcc_sync": [P],
         "hcc_bvh_upload": [P, ctypes.POINTER(_BvhDesc), PP],
+        "hcc_bvh_upload_layout": [P, ctypes.POINTER(_BvhDesc), i32, PP],
         "hcc_bvh_info": [P, P, P, P, P, P],
         "hcc_bvh_destroy": [P],
         "hcc_select_cut": [P, P, u32, f64, PP],
@@ -78,6 +79,7 @@ def load(path: str = LIB_PATH):
         "hcc_run": [P, i32, P, P, ctypes.POINTER(_Rays), u32, i32, P],
         "hcc_run_host": [P, i32, P, P, P, P, u64, u32, i32, P],
         "hcc_trace_counts": [P, P, ctypes.POINTER(_Rays), i32, P, P],
+        "hcc_trace_sorted": [P, P, ctypes.POINTER(_Rays), P, i32, P],
         "hcc_sort_noalloc": [P, u32, u64, P, P, P],
     }
     for name, args in sig.items():
@@ -146,8 +148,16 @@ def hcc_sync(ctx):
 
 # ---------------------------------------------------------------------- BVH
 
-def hcc_bvh_upload(ctx, bvh):
-    """bvh: an object with lo, hi, left, right, first, count, order, tris numpy arrays."""
+HCC_BVH_QUANTISED, HCC_BVH_EXACT = 0, 1
+LAYOUTS = {"quantised": HCC_BVH_QUANTISED, "exact": HCC_BVH_EXACT}
+
+
+def hcc_bvh_upload(ctx, bvh, layout=None):
+    """bvh: an object with lo, hi, left, right, first, count, order, tris numpy arrays.
+
+    layout None calls hcc_bvh_upload (quantised nodes); "quantised" or "exact"
+    calls hcc_bvh_upload_layout.
+    """
     arrs = dict(lo=np.ascontiguousarray(bvh.lo, np.float32), hi=np.ascontiguousarray(bvh.hi, np.float32),
                 left=np.ascontiguousarray(bvh.left, np.int32), right=np.ascontiguousarray(bvh.right, np.int32),
                 first=np.ascontiguousarray(bvh.first, np.uint32), count=np.ascontiguousarray(bvh.count, np.uint32),
@@ -156,7 +166,10 @@ def hcc_bvh_upload(ctx, bvh):
                  _ptr(arrs["first"]), _ptr(arrs["count"]), arrs["tris"].shape[0], _ptr(arrs["tris"]),
                  _ptr(arrs["order"]))
     h = ctypes.c_void_p()
-    _check(load().hcc_bvh_upload(ctx, ctypes.byref(d), ctypes.byref(h)), ctx)
+    if layout is None:
+        _check(load().hcc_bvh_upload(ctx, ctypes.byref(d), ctypes.byref(h)), ctx)
+    else:
+        _check(load().hcc_bvh_upload_layout(ctx, ctypes.byref(d), LAYOUTS.get(layout, layout), ctypes.byref(h)), ctx)
     return h
 
 
@@ -218,6 +231,12 @@ def hcc_gather(ctx, in_org, in_dir, perm, out_org, out_dir):
 def hcc_trace(ctx, bvh, org, dir_, hits, any_hit: bool = False, scatter=None):
     r = _rays(org, dir_)
     _check(load().hcc_trace(ctx, bvh, ctypes.byref(r), int(any_hit), _ptr(scatter), _ptr(hits)), ctx)
+
+
+def hcc_trace_sorted(ctx, bvh, org, dir_, perm, hits, any_hit: bool = False):
+    """Trace ray perm[j] in slot j (fetch through the sorted ids); hits land in input order."""
+    r = _rays(org, dir_)
+    _check(load().hcc_trace_sorted(ctx, bvh, ctypes.byref(r), _ptr(perm), int(any_hit), _ptr(hits)), ctx)
 
 
 def hcc_trace_counts(ctx, bvh, org, dir_, any_hit: bool = False):

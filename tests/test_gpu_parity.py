@@ -31,6 +31,7 @@ class Scene:
     def __init__(self, ctx, w):
         self.w = w
         self.bvh = hcc.hcc_bvh_upload(ctx, w.bvh)
+        self.bvh_exact = hcc.hcc_bvh_upload(ctx, w.bvh, layout="exact")
         self.org = torch.from_numpy(w.rays.org).to(DEV)
         self.dir = torch.from_numpy(w.rays.dir).to(DEV)
         self.n = w.rays.n
@@ -89,9 +90,10 @@ def gpu_sort(ctx, keys_u64, k):
     return perm[:n].cpu().numpy().view(np.uint32)
 
 
-def gpu_trace(ctx, sc, org, dir_, any_hit=False, scatter=None):
+def gpu_trace(ctx, sc, org, dir_, any_hit=False, scatter=None, layout="quantised"):
     hits = torch.zeros((org.shape[0], 4), dtype=torch.int32, device=DEV)
-    hcc.hcc_trace(ctx, sc.bvh, org, dir_, hits, any_hit=any_hit, scatter=scatter)
+    bvh = sc.bvh if layout == "quantised" else sc.bvh_exact
+    hcc.hcc_trace(ctx, bvh, org, dir_, hits, any_hit=any_hit, scatter=scatter)
     hcc.hcc_sync(ctx)
     return hcc.hits_to_numpy(hits)
 
@@ -264,25 +266,28 @@ def test_gather_bit_exact(ctx, n):
 
 # ------------------------------------------------------------------- trace
 
+@pytest.mark.parametrize("layout", ["quantised", "exact"])
 @pytest.mark.parametrize("which", ["tiny", "dense", "room"])
-def test_trace_closest_matches_oracle(ctx, which, request):
+def test_trace_closest_matches_oracle(ctx, which, layout, request):
     sc = request.getfixturevalue(which)
-    g = gpu_trace(ctx, sc, sc.org, sc.dir)
+    g = gpu_trace(ctx, sc, sc.org, sc.dir, layout=layout)
     o = oracle.trace_bvh(sc.w.bvh, sc.w.rays.org, sc.w.rays.dir)
     compare_hits(g, o)
     assert (g["prim"] >= 0).mean() > 0.2
 
 
-def test_trace_matches_brute_force_definition(ctx, dense):
-    g = gpu_trace(ctx, dense, dense.org, dense.dir)
+@pytest.mark.parametrize("layout", ["quantised", "exact"])
+def test_trace_matches_brute_force_definition(ctx, dense, layout):
+    g = gpu_trace(ctx, dense, dense.org, dense.dir, layout=layout)
     o = oracle.trace_brute(dense.w.tris, dense.w.rays.org, dense.w.rays.dir)
     compare_hits(g, o)
 
 
-def test_trace_any_hit_shadow_rays(ctx, room):
+@pytest.mark.parametrize("layout", ["quantised", "exact"])
+def test_trace_any_hit_shadow_rays(ctx, room, layout):
     sh = room.w.shadow
     org, dir_ = torch.from_numpy(sh.org).to(DEV), torch.from_numpy(sh.dir).to(DEV)
-    g = gpu_trace(ctx, room, org, dir_, any_hit=True)
+    g = gpu_trace(ctx, room, org, dir_, any_hit=True, layout=layout)
     o = oracle.trace_bvh(room.w.bvh, sh.org, sh.dir)
     occl_g, occl_o = g["prim"] >= 0, o["prim"] >= 0
     assert np.array_equal(occl_g, occl_o)
@@ -293,7 +298,8 @@ def test_trace_any_hit_shadow_rays(ctx, room):
         assert ok and np.float32(t) == g["t"][i]
 
 
-def test_trace_special_rays(ctx, dense):
+@pytest.mark.parametrize("layout", ["quantised", "exact"])
+def test_trace_special_rays(ctx, dense, layout):
     rng = np.random.default_rng(1)
     n = 400
     org = np.concatenate([rng.uniform(0, 1, (n, 3)), np.full((n, 1), 1e-4)], 1).astype(np.float32)
@@ -306,7 +312,7 @@ def test_trace_special_rays(ctx, dense):
     org[200:210, 1] = np.nan        # invalid inputs are misses on both sides
     dir_[210:220, 2] = np.nan
     org[220:230, 3] = np.inf        # empty interval
-    g = gpu_trace(ctx, dense, torch.from_numpy(org).to(DEV), torch.from_numpy(dir_).to(DEV))
+    g = gpu_trace(ctx, dense, torch.from_numpy(org).to(DEV), torch.from_numpy(dir_).to(DEV), layout=layout)
     o = oracle.trace_bvh(dense.w.bvh, org, dir_)
     compare_hits(g, o)
     assert np.all(g["prim"][200:230] == -1)
@@ -320,6 +326,11 @@ def test_trace_scatter_and_reorder_invariance(ctx, room):
     perm_t = torch.from_numpy(perm.view(np.int32)).to(DEV)
     scattered = gpu_trace(ctx, room, torch.from_numpy(po).to(DEV), torch.from_numpy(pd).to(DEV), scatter=perm_t)
     assert plain.tobytes() == scattered.tobytes()
+    # fetch through the permutation (no separate gather): same records
+    hits = torch.zeros((room.n, 4), dtype=torch.int32, device=DEV)
+    hcc.hcc_trace_sorted(ctx, room.bvh_exact, room.org, room.dir, perm_t, hits)
+    hcc.hcc_sync(ctx)
+    assert hcc.hits_to_numpy(hits).tobytes() == plain.tobytes()
 
 
 # ---------------------------------------------------------------- pipeline
@@ -423,9 +434,10 @@ def _chain_bvh(depth):
     return gen.BVH(lo, hi, left, right, first, count, np.arange(depth + 1, dtype=np.uint32), tris, depth)
 
 
-def test_stack_overflow_is_reported_and_context_survives(ctx, tiny):
+@pytest.mark.parametrize("layout", ["quantised", "exact"])
+def test_stack_overflow_is_reported_and_context_survives(ctx, tiny, layout):
     deep = _chain_bvh(100)
-    h = hcc.hcc_bvh_upload(ctx, deep)
+    h = hcc.hcc_bvh_upload(ctx, deep, layout=layout)
     assert hcc.hcc_bvh_info(h)["depth"] == 100
     c = deep.tris.reshape(-1, 3).mean(0)
     org = torch.tensor([[c[0], c[1], c[2] - 5.0, 0.0]], dtype=torch.float32, device=DEV)
