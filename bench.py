@@ -33,7 +33,7 @@ if ROOT not in sys.path:
 METRIC = "secondary Mrays/s incl. encode+sort, HCC vs NoSort/TwoPoint; p50/p99 latency"
 UNIT = "Mrays/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "trace_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "trace_room_1080p_dram.txt")
 FALLBACK_HBM_GBS = 6800.0
 SMS, LANES_PER_SM = 152, 128
 
@@ -171,13 +171,18 @@ def peaks():
 
 
 def recorded_traffic():
-    """DRAM bytes per trace launch from a committed ncu summary, if the kernel is unchanged."""
+    """DRAM bytes per trace launch from the committed ncu summary, if trace.cu is unchanged."""
     try:
-        rec = json.load(open(TRAFFIC_FILE))
+        rec = {}
+        for line in open(TRAFFIC_FILE):
+            if line.startswith("#") or ":" not in line:
+                continue
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip()
         src = open(os.path.join(ROOT, "paper_2305_16652_gb300", "csrc", "trace.cu"), "rb").read()
         if rec.get("trace_cu_sha256") != hashlib.sha256(src).hexdigest():
             return None
-        return rec.get("dram_bytes_per_launch")
+        return int(rec["dram_bytes_per_launch"])
     except Exception:
         return None
 
@@ -418,6 +423,44 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def profile_case(name: str):
+    """Small, fixed workloads for ncu captures (not a benchmark: nothing is timed).
+
+    trace-small: 480x270x8spp room, 200k triangles, exact nodes: HCC encode,
+                 sort, trace through the sorted ids, then the NoSort trace.
+    sort-16m:    two sorts of 16,588,800 seeded uniform 32-bit keys.
+    """
+    import torch
+    from paper_2305_16652_gb300 import build, hcc
+    build()
+    ctx = hcc.hcc_create(0)
+    if name == "sort-16m":
+        n = 16_588_800
+        k = np.random.default_rng(0).integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+        kt = torch.from_numpy(k.view(np.int32)).cuda()
+        perm = torch.empty(n, dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            hcc.hcc_sort(ctx, kt, 32, n, perm)
+    elif name == "trace-small":
+        w = make_workload(1, True)
+        n = w.rays.n
+        bvh = hcc.hcc_bvh_upload(ctx, w.bvh, layout="exact")
+        cut = hcc.hcc_select_cut(ctx, bvh, 32, 0.125)
+        org, dir_ = torch.from_numpy(w.rays.org).cuda(), torch.from_numpy(w.rays.dir).cuda()
+        keys = torch.empty(n, dtype=torch.int32, device="cuda")
+        perm = torch.empty(n, dtype=torch.int32, device="cuda")
+        hits = torch.empty((n, 4), dtype=torch.int32, device="cuda")
+        hcc.hcc_encode(ctx, "hcc", bvh, cut, org, dir_, 32, keys)
+        hcc.hcc_sort(ctx, keys, 32, n, perm)
+        hcc.hcc_trace_sorted(ctx, bvh, org, dir_, perm, hits)
+        hcc.hcc_trace(ctx, bvh, org, dir_, hits)
+    else:
+        raise SystemExit(f"unknown case {name}")
+    hcc.hcc_sync(ctx)
+    hcc.hcc_destroy(ctx)
+    print(f"case {name} ok")
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -431,7 +474,10 @@ def main(argv=None):
     ap.add_argument("--cpu-sample", type=int, default=1_500_000)
     ap.add_argument("--ref-sample", type=int, default=300_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", choices=["trace-small", "sort-16m"], help="run a small profiling case and exit")
     args = ap.parse_args(argv)
+    if args.case:
+        return profile_case(args.case)
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = dist_env()
     if world > 1:
