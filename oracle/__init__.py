@@ -52,6 +52,14 @@ def _load():
     lib.oracle_key_margin.restype = None
     lib.oracle_encode_twopoint.argtypes = [u64, P, P, P, P, u32, P]
     lib.oracle_encode_twopoint.restype = None
+    lib.oracle_encode_origin.argtypes = [u64, P, P, P, u32, P]
+    lib.oracle_encode_origin.restype = None
+    lib.oracle_encode_origin_dir.argtypes = [u64, P, P, P, P, u32, P]
+    lib.oracle_encode_origin_dir.restype = None
+    lib.oracle_octahedral.argtypes = [P, P, P]
+    lib.oracle_octahedral.restype = None
+    lib.oracle_anc.argtypes = [u64, P, P]
+    lib.oracle_anc.restype = f64
     lib.oracle_stable_sort.argtypes = [u64, P, P]
     lib.oracle_stable_sort.restype = None
     lib.oracle_gather.argtypes = [u64, P, P, P, P, P]
@@ -125,6 +133,36 @@ def encode_twopoint(org, dir, scene_lo, scene_hi, key_bits: int) -> np.ndarray:
     keys = np.zeros(n, np.uint64)
     _load().oracle_encode_twopoint(n, _p(org), _p(dir), _p(lo), _p(hi), key_bits, _p(keys))
     return keys
+
+
+def encode_origin(org, scene_lo, scene_hi, key_bits: int) -> np.ndarray:
+    org = _c(org, np.float32)
+    lo, hi = _c(scene_lo, np.float32), _c(scene_hi, np.float32)
+    n = org.shape[0]
+    keys = np.zeros(n, np.uint64)
+    _load().oracle_encode_origin(n, _p(org), _p(lo), _p(hi), key_bits, _p(keys))
+    return keys
+
+
+def encode_origin_dir(org, dir, scene_lo, scene_hi, key_bits: int) -> np.ndarray:
+    org, dir = _c(org, np.float32), _c(dir, np.float32)
+    lo, hi = _c(scene_lo, np.float32), _c(scene_hi, np.float32)
+    n = org.shape[0]
+    keys = np.zeros(n, np.uint64)
+    _load().oracle_encode_origin_dir(n, _p(org), _p(dir), _p(lo), _p(hi), key_bits, _p(keys))
+    return keys
+
+
+def octahedral(d):
+    d = _c(d, np.float32)
+    u, v = ctypes.c_float(), ctypes.c_float()
+    _load().oracle_octahedral(_p(d), ctypes.byref(u), ctypes.byref(v))
+    return u.value, v.value
+
+
+def anc(keys, perm) -> float:
+    keys, perm = _c(keys, np.uint64), _c(perm, np.uint32)
+    return float(_load().oracle_anc(keys.shape[0], _p(keys), _p(perm)))
 
 
 def stable_sort(keys) -> np.ndarray:

@@ -19,6 +19,11 @@
 //   oracle_key_margin     distance of a ray from flipping any HCC bit
 //   oracle_encode_twopoint  TwoPoint key (Sec. 3.2 "Two Point", Sec. 5:
 //                         fixed-length termination estimate 0.25 x largest extent)
+//   oracle_encode_origin  Origin key: 3D Morton code of the ray origin (Sec. 3.2 "Origin")
+//   oracle_encode_origin_dir  Origin-Direction key (Sec. 3.2, after Reis et al.):
+//                         origin Morton code in the high bits, a Morton code
+//                         of the octahedral parametrisation of the direction
+//                         in the low bits
 //   oracle_stable_sort    sort keys as natural numbers (Sec. 4.2.3 "Sorting",
 //                         Sec. 5: sort of ray indices)
 //   oracle_gather         rays fetched through the sorted indices (Sec. 5)
@@ -37,6 +42,11 @@
 //  * key bit (k-1-r) <- cut node r for r < min(cut size, k); other bits 0;
 //  * TwoPoint: b = floor(k/6) bits per coordinate, interleaved MSB-first in
 //    the order o.x o.y o.z t.x t.y t.z, left-justified in k bits;
+//  * Origin: b = floor(k/3) bits per axis, MSB-first in the order x y z,
+//    left-justified; origin normalised to the scene box as for TwoPoint;
+//  * Origin-Direction: bd = floor(k/6) bits per direction coordinate, bo =
+//    floor((k - 2 bd)/3) bits per origin axis; direction parametrised by the
+//    octahedral map (L1-normalise, fold the lower hemisphere), u = x/2 + 1/2;
 //  * sort: stable and ascending on all k key bits;
 //  * closest hit: lexicographic minimum of (t, triangle id) over every
 //    triangle with a Moller-Trumbore hit and tmin < t < tmax.
@@ -243,6 +253,99 @@ void oracle_encode_twopoint(uint64_t n, const float *org, const float *dir, cons
         if (key_bits > 6 * b) key <<= (key_bits - 6 * b);
         keys[i] = key;
     }
+}
+
+// Quantise coordinate p of the scene box [lo, lo + ext] to bits b
+// (normalise, clamp to [0, 1], scale by 2^b, truncate, cap at 2^b - 1).
+static uint32_t quantise(float p, float lo, float ext, uint32_t b) {
+    if (b == 0) return 0;
+    float u = (ext == 0.0f) ? 0.0f : (p - lo) / ext;
+    u = std::fmin(std::fmax(u, 0.0f), 1.0f);
+    uint32_t q = (uint32_t)(u * (float)std::ldexp(1.0, (int)b));
+    uint32_t qmax = (1u << b) - 1u;
+    return std::min(q, qmax);
+}
+
+// Morton interleave of m coordinates of b bits each, most significant level
+// first, coordinates in the given order.
+static uint64_t interleave(const uint32_t *q, int m, uint32_t b) {
+    uint64_t key = 0;
+    for (int j = (int)b - 1; j >= 0; --j)
+        for (int c = 0; c < m; ++c) key = (key << 1) | ((q[c] >> j) & 1u);
+    return key;
+}
+
+// Origin key (Sec. 3.2 "Origin"): 3D Morton code of the origin in the scene
+// box, b = floor(k/3) bits per axis, left-justified in k bits.
+void oracle_encode_origin(uint64_t n, const float *org, const float *scene_lo, const float *scene_hi,
+                          uint32_t key_bits, uint64_t *keys) {
+    float ext[3] = {scene_hi[0] - scene_lo[0], scene_hi[1] - scene_lo[1], scene_hi[2] - scene_lo[2]};
+    uint32_t b = key_bits / 3;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint32_t q[3];
+        for (int a = 0; a < 3; ++a) q[a] = quantise(org[4 * i + a], scene_lo[a], ext[a], b);
+        uint64_t key = interleave(q, 3, b);
+        if (key_bits > 3 * b) key <<= (key_bits - 3 * b);
+        keys[i] = key;
+    }
+}
+
+// Octahedral parametrisation of a direction onto [0, 1]^2: divide by the L1
+// norm, fold the lower hemisphere (z < 0) over the diagonals, map [-1, 1] to
+// [0, 1].  A zero direction maps to the centre.
+void oracle_octahedral(const float *d, float *u, float *v) {
+    float s = (std::fabs(d[0]) + std::fabs(d[1])) + std::fabs(d[2]);
+    if (!(s > 0.0f)) {
+        *u = 0.5f;
+        *v = 0.5f;
+        return;
+    }
+    float nx = d[0] / s, ny = d[1] / s, nz = d[2] / s;
+    float x = nx, y = ny;
+    if (nz < 0.0f) {
+        x = (1.0f - std::fabs(ny)) * (nx >= 0.0f ? 1.0f : -1.0f);
+        y = (1.0f - std::fabs(nx)) * (ny >= 0.0f ? 1.0f : -1.0f);
+    }
+    *u = x * 0.5f + 0.5f;
+    *v = y * 0.5f + 0.5f;
+}
+
+// Origin-Direction key (Sec. 3.2, Reis et al.): origin Morton code (bo bits
+// per axis) in the high bits, direction Morton code (bd bits per octahedral
+// coordinate) in the low bits, bd = floor(k/6), bo = floor((k - 2 bd)/3),
+// left-justified in k bits.
+void oracle_encode_origin_dir(uint64_t n, const float *org, const float *dir, const float *scene_lo,
+                              const float *scene_hi, uint32_t key_bits, uint64_t *keys) {
+    float ext[3] = {scene_hi[0] - scene_lo[0], scene_hi[1] - scene_lo[1], scene_hi[2] - scene_lo[2]};
+    uint32_t bd = key_bits / 6, bo = (key_bits - 2 * bd) / 3;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint32_t qo[3], qd[2];
+        for (int a = 0; a < 3; ++a) qo[a] = quantise(org[4 * i + a], scene_lo[a], ext[a], bo);
+        float u, v;
+        oracle_octahedral(dir + 4 * i, &u, &v);
+        qd[0] = quantise(u, 0.0f, 1.0f, bd);
+        qd[1] = quantise(v, 0.0f, 1.0f, bd);
+        uint64_t key = (interleave(qo, 3, bo) << (2 * bd)) | interleave(qd, 2, bd);
+        uint32_t used = 3 * bo + 2 * bd;
+        if (key_bits > used) key <<= (key_bits - used);
+        keys[i] = key;
+    }
+}
+
+// Average number of distinct codes per warp (Sec. 6.5, Table 6): the keys in
+// sorted order cut into consecutive groups of 32 rays; the mean number of
+// distinct keys per group (the last group may be shorter).
+double oracle_anc(uint64_t n, const uint64_t *keys, const uint32_t *perm) {
+    if (n == 0) return 0.0;
+    uint64_t groups = 0, distinct = 0;
+    for (uint64_t g = 0; g < n; g += 32) {
+        std::vector<uint64_t> w;
+        for (uint64_t j = g; j < std::min<uint64_t>(g + 32, n); ++j) w.push_back(keys[perm[j]]);
+        std::sort(w.begin(), w.end());
+        distinct += (uint64_t)(std::unique(w.begin(), w.end()) - w.begin());
+        ++groups;
+    }
+    return (double)distinct / (double)groups;
 }
 
 // Rays sorted by key as natural numbers (Sec. 4.2.3), realised as a stable

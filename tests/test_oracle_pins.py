@@ -479,3 +479,62 @@ def test_trace_reorder_invariance():
     a = oracle.trace_bvh(w.bvh, w.rays.org, w.rays.dir)
     b = oracle.trace_bvh(w.bvh, o2, d2)
     assert a[perm].tobytes() == b.tobytes()
+
+
+# ------------------------------------------------- Origin, Origin-Direction
+
+def test_origin_key_is_textbook_morton():
+    rng = np.random.default_rng(21)
+    n = 400
+    org = np.concatenate([rng.uniform(0, 1, (n, 3)), np.zeros((n, 1))], 1).astype(np.float32)
+    lo, hi = np.zeros(3, np.float32), np.ones(3, np.float32)
+    keys = oracle.encode_origin(org, lo, hi, 32)  # 10 bits per axis, 2 spare bits
+    for i in range(n):
+        q = [min(int(np.float32(org[i, a]) * np.float32(1024.0)), 1023) for a in range(3)]
+        assert int(keys[i]) == _morton3_magic(*q) << 2
+
+
+@pytest.mark.parametrize("d,uv", [((0, 0, 1), (0.5, 0.5)), ((1, 0, 0), (1.0, 0.5)), ((-1, 0, 0), (0.0, 0.5)),
+                                  ((0, 1, 0), (0.5, 1.0)), ((0, -1, 0), (0.5, 0.0)), ((0, 0, -1), (1.0, 1.0)),
+                                  ((1, 1, 1), (2 / 3, 2 / 3)), ((0, 0, 0), (0.5, 0.5))])
+def test_octahedral_map_closed_forms(d, uv):
+    u, v = oracle.octahedral(np.array(d, np.float32))
+    assert abs(u - uv[0]) < 1e-6 and abs(v - uv[1]) < 1e-6
+
+
+def test_octahedral_map_inverts():
+    """Decode (u, v) with the inverse octahedral map and recover the direction."""
+    rng = np.random.default_rng(4)
+    for _ in range(300):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        u, v = oracle.octahedral(d.astype(np.float32))
+        x, y = 2 * u - 1, 2 * v - 1
+        z = 1 - abs(x) - abs(y)
+        if z < 0:
+            x, y = (1 - abs(y)) * np.sign(x if x != 0 else 1), (1 - abs(x)) * np.sign(y if y != 0 else 1)
+        r = np.array([x, y, z])
+        r /= np.linalg.norm(r)
+        assert np.allclose(r, d, atol=1e-5)
+
+
+def test_origin_dir_hand_computed():
+    # k = 16: bd = 2 bits per direction coordinate, bo = 4 bits per origin axis.
+    # o = (.5, .25, .75) -> q = (8, 4, 12): levels x y z: 101, 011, 000, 000 -> 101011000000
+    # d = +z -> (u, v) = (.5, .5) -> q = (2, 2): levels u v: 11, 00 -> 1100
+    # key = 101011000000 1100 = 0xAC0C
+    org = np.array([[.5, .25, .75, 0]], np.float32)
+    dir_ = np.array([[0, 0, 1, np.inf]], np.float32)
+    k = oracle.encode_origin_dir(org, dir_, np.zeros(3, np.float32), np.ones(3, np.float32), 16)
+    assert int(k[0]) == 0xAC0C
+    # 32 bits: bd = 5, bo = 7 -> 31 bits used, one pad bit at the bottom
+    k32 = int(oracle.encode_origin_dir(org, dir_, np.zeros(3, np.float32), np.ones(3, np.float32), 32)[0])
+    assert k32 & 1 == 0 and k32 >> 11 == _morton3_magic(64, 32, 96)  # origin part: 7-bit coords
+
+
+def test_anc_closed_forms():
+    perm = np.arange(64, dtype=np.uint32)
+    assert oracle.anc(np.zeros(64, np.uint64), perm) == 1.0
+    assert oracle.anc(np.arange(64, dtype=np.uint64), perm) == 32.0
+    keys = np.repeat(np.arange(8, dtype=np.uint64), 8)  # each warp of 32 holds 4 codes
+    assert oracle.anc(keys, perm) == 4.0
