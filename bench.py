@@ -312,7 +312,8 @@ def run_ours(args, rank, world, local_rank):
     identical = bool(torch.equal(h_hcc, hits))
 
     # work counts of the trace (order-independent per ray) for the ALU roofline
-    counts = hcc.hcc_trace_counts(ctx, bvh, org, dir_)
+    counts = hcc.hcc_trace_counts(ctx, bvh, org, dir_, perm=perm)
+    counts0 = hcc.hcc_trace_counts(ctx, bvh, org, dir_)
     hcc.hcc_bvh_destroy(bvh_q)
     hbm, sm_max, peak_kind = peaks()
     clk_mhz = clocks.get("sm_max_mhz") or sm_max
@@ -333,7 +334,9 @@ def run_ours(args, rank, world, local_rank):
         "trace": dict(ms=round(st[3], 4), bound="alu", achieved_tops=round(achieved, 3),
                       frac=round(achieved / alu_peak, 3),
                       node_visits_per_ray=round(counts["node_visits"] / n, 2),
-                      tri_tests_per_ray=round(counts["tri_tests"] / n, 2)),
+                      tri_tests_per_ray=round(counts["tri_tests"] / n, 2),
+                      warp_efficiency=round(counts["node_visits"] / (32.0 * max(1, counts["warp_node_steps"])), 4),
+                      warp_efficiency_nosort=round(counts0["node_visits"] / (32.0 * max(1, counts0["warp_node_steps"])), 4)),
     }
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -423,6 +426,71 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_keylen_sweep(args):
+    """Key-length study (Sec. 6.5, Tables 5-6): HCC (cut size = key bits), TwoPoint and
+    Origin-Direction at 16/24/32/48/64 bits on the same wavefront; per point the stage
+    times, ANC, distinct keys and the trace's warp execution efficiency."""
+    import torch
+    from paper_2305_16652_gb300 import build, hcc
+    build()
+    dev = torch.device("cuda", 0)
+    w = make_workload(1, args.quick)
+    n = w.rays.n
+    ctx = hcc.hcc_create(0)
+    bvh = hcc.hcc_bvh_upload(ctx, w.bvh, layout=args.layout)
+    hcc.hcc_reserve(ctx, n, 64)
+    org = torch.from_numpy(w.rays.org).to(dev)
+    dir_ = torch.from_numpy(w.rays.dir).to(dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    hits = torch.empty((n, 4), dtype=torch.int32, device=dev)
+
+    def tm(f, reps=5):
+        ts = []
+        for _ in range(reps + 2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            f()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts[2:])
+
+    def eff(c):
+        return round(c["node_visits"] / (32.0 * max(1, c["warp_node_steps"])), 4)
+
+    c0 = hcc.hcc_trace_counts(ctx, bvh, org, dir_)
+    nosort = {"trace_ms": round(tm(lambda: hcc.hcc_trace(ctx, bvh, org, dir_, hits)), 4),
+              "warp_efficiency": eff(c0), "node_visits_per_ray": round(c0["node_visits"] / n, 3)}
+    points = []
+    for k in (16, 24, 32, 48, 64):
+        keys = torch.empty(n, dtype=torch.int32 if k <= 32 else torch.int64, device=dev)
+        for method in ("hcc", "twopoint", "origin_dir"):
+            cut = hcc.hcc_select_cut(ctx, bvh, k, 0.125) if method == "hcc" else None
+            te = tm(lambda: hcc.hcc_encode(ctx, method, bvh, cut, org, dir_, k, keys))
+            ts = tm(lambda: hcc.hcc_sort(ctx, keys, k, n, perm))
+            tt = tm(lambda: hcc.hcc_trace_sorted(ctx, bvh, org, dir_, perm, hits))
+            st = hcc.hcc_key_stats(ctx, keys, k, perm, n)
+            c = hcc.hcc_trace_counts(ctx, bvh, org, dir_, perm=perm)
+            hcc.hcc_sync(ctx)
+            tot = te + ts + tt
+            points.append({"method": method, "key_bits": k, "encode_ms": round(te, 4), "sort_ms": round(ts, 4),
+                           "trace_ms": round(tt, 4), "total_ms": round(tot, 4),
+                           "mrays_s": round(n / (tot * 1e3), 2),
+                           "trace_speedup_vs_nosort": round(nosort["trace_ms"] / tt, 3),
+                           "anc": round(st["anc"], 4), "distinct_keys": st["distinct"],
+                           "warp_efficiency": eff(c), "warp_node_steps_per_32_rays":
+                               round(32.0 * c["warp_node_steps"] / n, 2)})
+            if cut is not None:
+                hcc.hcc_cut_destroy(cut)
+    out = {"metric": "key-length sweep: secondary Mrays/s, ANC and warp execution efficiency",
+           "unit": "Mrays/s", "config": {"workload": w.name + f" ({n} secondary rays)", "bvh_layout": args.layout,
+                                         "hcc_cut_size": "= key bits"},
+           "nosort": nosort, "points": points}
+    hcc.hcc_bvh_destroy(bvh)
+    hcc.hcc_destroy(ctx)
+    print(json.dumps(out), flush=True)
+
+
 def profile_case(name: str):
     """Small, fixed workloads for ncu captures (not a benchmark: nothing is timed).
 
@@ -475,9 +543,12 @@ def main(argv=None):
     ap.add_argument("--ref-sample", type=int, default=300_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", choices=["trace-small", "sort-16m"], help="run a small profiling case and exit")
+    ap.add_argument("--sweep", choices=["keylen"], help="run a study instead of the headline benchmark")
     args = ap.parse_args(argv)
     if args.case:
         return profile_case(args.case)
+    if args.sweep == "keylen":
+        return run_keylen_sweep(args)
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = dist_env()
     if world > 1:

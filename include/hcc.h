@@ -52,9 +52,11 @@ typedef enum hcc_status {
 
 /* Ray-ordering methods (Sec. 5 and Table 1 of the paper). */
 typedef enum hcc_method {
-    HCC_METHOD_NOSORT = 0,   /* trace in generation order (Table 1, NoSort) */
-    HCC_METHOD_HCC = 1,      /* hierarchy cut code (Sec. 4.2) */
-    HCC_METHOD_TWOPOINT = 2  /* origin + estimated termination Morton code (Sec. 3.2, Sec. 5) */
+    HCC_METHOD_NOSORT = 0,    /* trace in generation order (Table 1, NoSort) */
+    HCC_METHOD_HCC = 1,       /* hierarchy cut code (Sec. 4.2) */
+    HCC_METHOD_TWOPOINT = 2,  /* origin + estimated termination Morton code (Sec. 3.2, Sec. 5) */
+    HCC_METHOD_ORIGIN = 3,    /* Morton code of the origin (Sec. 3.2 "Origin", Table 1) */
+    HCC_METHOD_ORIGIN_DIR = 4 /* origin Morton above direction Morton (Sec. 3.2 "Origin-Direction") */
 } hcc_method;
 
 typedef struct hcc_ctx hcc_ctx; /* device, stream, scratch, device error word */
@@ -206,11 +208,30 @@ hcc_status hcc_cut_destroy(hcc_cut *cut);
  *     the root box and quantised to floor(key_bits / 6) bits, interleaved
  *     most significant level first in the order o.x o.y o.z t.x t.y t.z and
  *     left-justified in key_bits.  Requires bvh; cut may be NULL.
+ *   ORIGIN (Sec. 3.2): origin normalised to the root box, floor(k/3) bits
+ *     per axis, Morton-interleaved x y z most significant level first,
+ *     left-justified.  Requires bvh.
+ *   ORIGIN_DIR (Sec. 3.2, after Reis et al.): origin Morton code with
+ *     bo = floor((k - 2 bd)/3) bits per axis in the high bits, then a Morton
+ *     code (u, v) of the octahedral map of the direction (L1-normalise, fold
+ *     z < 0 over the diagonals, map [-1, 1] to [0, 1]) with bd = floor(k/6)
+ *     bits per coordinate, left-justified.  Requires bvh.
  *   NOSORT: INVALID_ARG (nothing to encode).
  * Errors: INVALID_ARG, CUDA.
  */
 hcc_status hcc_encode(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const hcc_cut *cut,
                       const hcc_rays *rays, uint32_t key_bits, void *keys);
+
+/*
+ * Diagnostic (not on the timed path): statistics of keys in sorted order,
+ * i.e. of keys[perm[j]], j = 0..n-1, which must be ascending.  *distinct =
+ * number of different keys; *anc = average number of different codes per
+ * warp, the groups of 32 consecutive sorted rays (Sec. 6.5, Table 6).
+ * Waits for the stream; outputs are valid on return.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+hcc_status hcc_key_stats(hcc_ctx *ctx, const void *keys, uint32_t key_bits, const uint32_t *perm, uint64_t n,
+                         double *anc, uint64_t *distinct);
 
 /* ------------------------------------------------------------------ sort */
 
@@ -296,15 +317,19 @@ hcc_status hcc_trace_sorted(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *ra
                             int any_hit, hcc_hit *hits);
 
 /*
- * Diagnostic (never on the timed path): trace like hcc_trace without
- * scatter and also count, over all rays, the internal BVH nodes visited and
- * the triangle tests run.  A ray's counts depend only on the ray, not on
- * its position in the batch, so they are the same for every ray order.
- * Allocates a temporary hit buffer and waits for the stream; the counts are
- * valid on return.  Errors: INVALID_ARG, OOM, CUDA.
+ * Diagnostic (never on the timed path): trace like hcc_trace (perm NULL) or
+ * hcc_trace_sorted (perm given) and count, over all rays: counts[0] internal
+ * node visits, counts[1] triangle tests, counts[2] warp-level node steps
+ * (loop iterations of a warp in which any lane visits a node), counts[3]
+ * warp-level leaf steps.  counts[0] / (32 counts[2]) is the warp execution
+ * efficiency of the node loop.  All four depend on which rays share a warp
+ * (a lane that has parked a leaf keeps descending until its warp-mates
+ * have one too), which is what ray order changes; the hits do not.  Allocates a
+ * temporary hit buffer and waits for the stream.
+ * Errors: INVALID_ARG, OOM, CUDA.
  */
-hcc_status hcc_trace_counts(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *rays, int any_hit,
-                            uint64_t *node_visits, uint64_t *tri_tests);
+hcc_status hcc_trace_counts(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *rays, const uint32_t *perm,
+                            int any_hit, uint64_t counts[4]);
 
 /* ------------------------------------------------------- whole pipeline */
 

@@ -96,7 +96,140 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_twopoint(const float4 *__r
     }
 }
 
+// Normalise p to the box [lo, lo + ext], clamp to [0, 1], quantise to b bits.
+__device__ __forceinline__ uint32_t quantise(float p, float lo, float ext, uint32_t b) {
+    if (b == 0) return 0u;
+    float u = (ext == 0.0f) ? 0.0f : __fdiv_rn(__fsub_rn(p, lo), ext);
+    u = fminf(fmaxf(u, 0.0f), 1.0f);
+    const uint32_t q = __float2uint_rz(__fmul_rn(u, (float)(1u << b)));
+    const uint32_t qmax = (1u << b) - 1u;
+    return q < qmax ? q : qmax;
+}
+
+// Morton interleave, most significant level first, coordinates in order.
+template <typename K, int M>
+__device__ __forceinline__ K interleave(const uint32_t (&q)[M], uint32_t b) {
+    K key = 0;
+    for (int j = (int)b - 1; j >= 0; --j) {
+#pragma unroll
+        for (int c = 0; c < M; ++c) key = (key << 1) | (K)((q[c] >> j) & 1u);
+    }
+    return key;
+}
+
+// Origin key: 3D Morton code of the origin, floor(k/3) bits per axis,
+// left-justified in k bits.
+template <typename K>
+__global__ void __launch_bounds__(ENC_BLOCK) k_encode_origin(const float4 *__restrict__ org, uint64_t n, float lox,
+                                                             float loy, float loz, float ex, float ey, float ez,
+                                                             uint32_t key_bits, K *__restrict__ keys) {
+    const uint32_t b = key_bits / 3, pad = key_bits - 3 * b;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float4 o = __ldcs(org + i);
+        const uint32_t q[3] = {quantise(o.x, lox, ex, b), quantise(o.y, loy, ey, b), quantise(o.z, loz, ez, b)};
+        K key = interleave<K, 3>(q, b);
+        if (pad) key <<= pad;
+        __stcs(keys + i, key);
+    }
+}
+
+// Origin-Direction key: origin Morton code (bo bits per axis) above a Morton
+// code of the octahedral map of the direction (bd bits per coordinate),
+// bd = floor(k/6), bo = floor((k - 2 bd)/3), left-justified in k bits.
+template <typename K>
+__global__ void __launch_bounds__(ENC_BLOCK) k_encode_origin_dir(const float4 *__restrict__ org,
+                                                                 const float4 *__restrict__ dir, uint64_t n,
+                                                                 float lox, float loy, float loz, float ex,
+                                                                 float ey, float ez, uint32_t key_bits,
+                                                                 K *__restrict__ keys) {
+    const uint32_t bd = key_bits / 6, bo = (key_bits - 2 * bd) / 3;
+    const uint32_t pad = key_bits - (3 * bo + 2 * bd);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float4 o = __ldcs(org + i);
+        const float4 d = __ldcs(dir + i);
+        // octahedral map: L1-normalise, fold the lower hemisphere, map to [0, 1]^2
+        float u = 0.5f, v = 0.5f;
+        const float s = __fadd_rn(__fadd_rn(fabsf(d.x), fabsf(d.y)), fabsf(d.z));
+        if (s > 0.0f) {
+            const float nx = __fdiv_rn(d.x, s), ny = __fdiv_rn(d.y, s), nz = __fdiv_rn(d.z, s);
+            float x = nx, y = ny;
+            if (nz < 0.0f) {
+                x = __fmul_rn(__fsub_rn(1.0f, fabsf(ny)), nx >= 0.0f ? 1.0f : -1.0f);
+                y = __fmul_rn(__fsub_rn(1.0f, fabsf(nx)), ny >= 0.0f ? 1.0f : -1.0f);
+            }
+            u = __fadd_rn(__fmul_rn(x, 0.5f), 0.5f);
+            v = __fadd_rn(__fmul_rn(y, 0.5f), 0.5f);
+        }
+        const uint32_t qo[3] = {quantise(o.x, lox, ex, bo), quantise(o.y, loy, ey, bo), quantise(o.z, loz, ez, bo)};
+        const uint32_t qd[2] = {quantise(u, 0.0f, 1.0f, bd), quantise(v, 0.0f, 1.0f, bd)};
+        K key = (interleave<K, 3>(qo, bo) << (2 * bd)) | interleave<K, 2>(qd, bd);
+        if (pad) key <<= pad;
+        __stcs(keys + i, key);
+    }
+}
+
+// Key statistics over keys in sorted order (keys[perm[j]] ascending):
+// cnt[0] += changes of key between consecutive positions, cnt[1] += changes
+// inside groups of 32 consecutive positions.
+template <typename K>
+__global__ void __launch_bounds__(ENC_BLOCK) k_key_stats(const K *__restrict__ keys, const uint32_t *__restrict__ perm,
+                                                         uint64_t n, K mask, unsigned long long *cnt) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    unsigned long long all = 0, inner = 0;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; j < n; j += stride) {
+        const uint32_t a = perm[j - 1], b = perm[j];
+        if (a < n && b < n && ((keys[a] & mask) != (keys[b] & mask))) {
+            ++all;
+            if (j % 32 != 0) ++inner;
+        }
+    }
+    if (all) atomicAdd(cnt, all);
+    if (inner) atomicAdd(cnt + 1, inner);
+}
+
 }  // namespace
+
+cudaError_t launch_key_stats(cudaStream_t s, const void *keys, uint32_t key_bits, const uint32_t *perm, uint64_t n,
+                             unsigned long long *cnt) {
+    if (n < 2) return cudaSuccess;
+    const int grid = encode_grid(n, ENC_BLOCK, 8);
+    if (key_bits <= 32) {
+        const uint32_t mask = key_bits == 32 ? 0xFFFFFFFFu : ((1u << key_bits) - 1u);
+        k_key_stats<uint32_t><<<grid, ENC_BLOCK, 0, s>>>((const uint32_t *)keys, perm, n, mask, cnt);
+    } else {
+        const uint64_t mask = key_bits == 64 ? ~0ull : ((1ull << key_bits) - 1ull);
+        k_key_stats<uint64_t><<<grid, ENC_BLOCK, 0, s>>>((const uint64_t *)keys, perm, n, mask, cnt);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encode_origin(cudaStream_t s, const float4 *org, uint64_t n, const float lo[3], const float ext[3],
+                                 uint32_t key_bits, void *keys) {
+    if (n == 0) return cudaSuccess;
+    const int grid = encode_grid(n, ENC_BLOCK, 8);
+    if (key_bits <= 32)
+        k_encode_origin<uint32_t><<<grid, ENC_BLOCK, 0, s>>>(org, n, lo[0], lo[1], lo[2], ext[0], ext[1], ext[2],
+                                                             key_bits, (uint32_t *)keys);
+    else
+        k_encode_origin<uint64_t><<<grid, ENC_BLOCK, 0, s>>>(org, n, lo[0], lo[1], lo[2], ext[0], ext[1], ext[2],
+                                                             key_bits, (uint64_t *)keys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encode_origin_dir(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n,
+                                     const float lo[3], const float ext[3], uint32_t key_bits, void *keys) {
+    if (n == 0) return cudaSuccess;
+    const int grid = encode_grid(n, ENC_BLOCK, 8);
+    if (key_bits <= 32)
+        k_encode_origin_dir<uint32_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, lo[0], lo[1], lo[2], ext[0], ext[1],
+                                                                 ext[2], key_bits, (uint32_t *)keys);
+    else
+        k_encode_origin_dir<uint64_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, lo[0], lo[1], lo[2], ext[0], ext[1],
+                                                                 ext[2], key_bits, (uint64_t *)keys);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_encode_hcc(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n,
                               const float4 *cut_boxes, uint32_t used, uint32_t key_bits, void *keys) {

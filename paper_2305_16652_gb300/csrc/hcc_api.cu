@@ -572,10 +572,11 @@ hcc_status hcc_encode(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const
     hcc_status st = check_rays(ctx, rays, "rays");
     if (st != HCC_OK) return st;
     if (key_bits < 1 || key_bits > 64) return fail(ctx, HCC_ERR_INVALID_ARG, "key_bits must be 1..64");
-    if (method != HCC_METHOD_HCC && method != HCC_METHOD_TWOPOINT)
-        return fail(ctx, HCC_ERR_INVALID_ARG, "hcc_encode needs HCC or TWOPOINT");
+    if (method != HCC_METHOD_HCC && method != HCC_METHOD_TWOPOINT && method != HCC_METHOD_ORIGIN &&
+        method != HCC_METHOD_ORIGIN_DIR)
+        return fail(ctx, HCC_ERR_INVALID_ARG, "hcc_encode needs HCC, TWOPOINT, ORIGIN or ORIGIN_DIR");
     if (method == HCC_METHOD_HCC && !cut) return fail(ctx, HCC_ERR_INVALID_ARG, "HCC needs a cut");
-    if (method == HCC_METHOD_TWOPOINT && !bvh) return fail(ctx, HCC_ERR_INVALID_ARG, "TWOPOINT needs the BVH");
+    if (method != HCC_METHOD_HCC && !bvh) return fail(ctx, HCC_ERR_INVALID_ARG, "this key needs the BVH");
     if (rays->n == 0) return HCC_OK;
     if (!keys || !aligned(keys, key_bits > 32 ? 8 : 4))
         return fail(ctx, HCC_ERR_INVALID_ARG, "keys NULL or misaligned");
@@ -592,10 +593,44 @@ hcc_status hcc_encode(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const
             lo[a] = bvh->lo[a];
             ext[a] = bvh->hi[a] - bvh->lo[a];
         }
-        const float L = 0.25f * std::max(ext[0], std::max(ext[1], ext[2]));
-        e = launch_encode_twopoint(ctx->stream, o, d, rays->n, lo, ext, L, key_bits, keys);
+        if (method == HCC_METHOD_TWOPOINT) {
+            const float L = 0.25f * std::max(ext[0], std::max(ext[1], ext[2]));
+            e = launch_encode_twopoint(ctx->stream, o, d, rays->n, lo, ext, L, key_bits, keys);
+        } else if (method == HCC_METHOD_ORIGIN) {
+            e = launch_encode_origin(ctx->stream, o, rays->n, lo, ext, key_bits, keys);
+        } else {
+            e = launch_encode_origin_dir(ctx->stream, o, d, rays->n, lo, ext, key_bits, keys);
+        }
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "encode launch");
+    return HCC_OK;
+}
+
+hcc_status hcc_key_stats(hcc_ctx *ctx, const void *keys, uint32_t key_bits, const uint32_t *perm, uint64_t n,
+                         double *anc, uint64_t *distinct) {
+    if (!ctx) return HCC_ERR_INVALID_ARG;
+    if (key_bits < 1 || key_bits > 64) return fail(ctx, HCC_ERR_INVALID_ARG, "key_bits must be 1..64");
+    if (!anc || !distinct) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL output");
+    *anc = 0.0;
+    *distinct = 0;
+    if (n == 0) return HCC_OK;
+    if (!keys || !perm || !aligned(keys, key_bits > 32 ? 8 : 4) || !aligned(perm, 4))
+        return fail(ctx, HCC_ERR_INVALID_ARG, "keys/perm NULL or misaligned");
+    DeviceGuard g(ctx->device);
+    DevBuf tmp;
+    hcc_status st = ensure(ctx, tmp, 256, "key statistics");
+    if (st != HCC_OK) return st;
+    unsigned long long host[2] = {0, 0};
+    cudaError_t e = cudaMemsetAsync(tmp.p, 0, 2 * sizeof(unsigned long long), ctx->stream);
+    if (e == cudaSuccess)
+        e = launch_key_stats(ctx->stream, keys, key_bits, perm, n, static_cast<unsigned long long *>(tmp.p));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, tmp.p, sizeof host, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    release(tmp);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "key statistics");
+    const uint64_t groups = (n + 31) / 32;
+    *anc = (double)(groups + host[1]) / (double)groups;
+    *distinct = 1 + host[0];
     return HCC_OK;
 }
 
@@ -696,21 +731,21 @@ hcc_status hcc_trace_sorted(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *ra
     return HCC_OK;
 }
 
-hcc_status hcc_trace_counts(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *rays, int any_hit,
-                            uint64_t *node_visits, uint64_t *tri_tests) {
+hcc_status hcc_trace_counts(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *rays, const uint32_t *perm,
+                            int any_hit, uint64_t counts[4]) {
     if (!ctx) return HCC_ERR_INVALID_ARG;
     hcc_status st = check_rays(ctx, rays, "rays");
     if (st != HCC_OK) return st;
-    if (!bvh || !node_visits || !tri_tests) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL argument");
-    *node_visits = 0;
-    *tri_tests = 0;
+    if (!bvh || !counts) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL argument");
+    for (int k = 0; k < 4; ++k) counts[k] = 0;
     if (rays->n == 0) return HCC_OK;
+    if (perm && !aligned(perm, 4)) return fail(ctx, HCC_ERR_INVALID_ARG, "perm misaligned");
     DeviceGuard g(ctx->device);
     DevBuf tmp;
     if ((st = ensure(ctx, tmp, rays->n * sizeof(hcc_hit) + 256, "counting trace output")) != HCC_OK) return st;
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(static_cast<char *>(tmp.p) +
                                                                      rays->n * sizeof(hcc_hit));
-    cudaError_t e = cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), ctx->stream);
+    cudaError_t e = cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), ctx->stream);
     TraceArgs a;
     a.nodes = bvh->d_nodes;
     a.layout = bvh->layout;
@@ -719,19 +754,18 @@ hcc_status hcc_trace_counts(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *ra
     a.org = reinterpret_cast<const float4 *>(rays->org_tmin);
     a.dir = reinterpret_cast<const float4 *>(rays->dir_tmax);
     a.n = rays->n;
-    a.gather = nullptr;
-    a.scatter = nullptr;
+    a.gather = perm;
+    a.scatter = perm;
     a.hits = reinterpret_cast<int4 *>(tmp.p);
     a.err = ctx->d_err;
     a.counts = cnt;
     if (e == cudaSuccess) e = launch_trace(ctx->stream, a, any_hit);
-    unsigned long long host[2] = {0, 0};
+    unsigned long long host[4] = {0, 0, 0, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(host, cnt, sizeof host, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     release(tmp);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "counting trace");
-    *node_visits = host[0];
-    *tri_tests = host[1];
+    for (int k = 0; k < 4; ++k) counts[k] = host[k];
     return HCC_OK;
 }
 
@@ -743,7 +777,8 @@ hcc_status hcc_run(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const hc
     hcc_status st = check_rays(ctx, rays, "rays");
     if (st != HCC_OK) return st;
     if (!bvh) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL BVH");
-    if (method != HCC_METHOD_NOSORT && method != HCC_METHOD_HCC && method != HCC_METHOD_TWOPOINT)
+    if (method != HCC_METHOD_NOSORT && method != HCC_METHOD_HCC && method != HCC_METHOD_TWOPOINT &&
+        method != HCC_METHOD_ORIGIN && method != HCC_METHOD_ORIGIN_DIR)
         return fail(ctx, HCC_ERR_INVALID_ARG, "unknown method");
     if (rays->n == 0) return HCC_OK;
     if (method == HCC_METHOD_NOSORT) return hcc_trace(ctx, bvh, rays, any_hit, nullptr, hits);

@@ -46,6 +46,17 @@ cudaError_t launch_encode_hcc(cudaStream_t s, const float4 *org, const float4 *d
 cudaError_t launch_encode_twopoint(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n,
                                    const float lo[3], const float ext[3], float L, uint32_t key_bits, void *keys);
 
+cudaError_t launch_encode_origin(cudaStream_t s, const float4 *org, uint64_t n, const float lo[3], const float ext[3],
+                                 uint32_t key_bits, void *keys);
+
+cudaError_t launch_encode_origin_dir(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n,
+                                     const float lo[3], const float ext[3], uint32_t key_bits, void *keys);
+
+// cnt[0] += key changes between consecutive sorted positions, cnt[1] += those
+// inside groups of 32 positions (cnt zeroed by the caller).
+cudaError_t launch_key_stats(cudaStream_t s, const void *keys, uint32_t key_bits, const uint32_t *perm, uint64_t n,
+                             unsigned long long *cnt);
+
 // Radix sort scratch bytes for n keys of key_bits bits.
 size_t sort_scratch_bytes(uint64_t n, uint32_t key_bits);
 
@@ -67,7 +78,8 @@ struct TraceArgs {
     const uint32_t *scatter;  // its hit goes to hits[scatter[j]] (NULL = j)
     int4 *hits;
     uint32_t *err;
-    unsigned long long *counts;  // diagnostic: node visits, triangle tests (NULL = off)
+    unsigned long long *counts;  // diagnostic (NULL = off): node visits, triangle tests,
+                                 // warp node steps, warp leaf steps
 };
 
 cudaError_t launch_trace(cudaStream_t s, const TraceArgs &a, int any_hit);

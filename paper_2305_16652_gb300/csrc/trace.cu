@@ -142,7 +142,8 @@ __device__ __forceinline__ void fetch_exact(const uint4 *nodes, uint32_t ref, Ch
 template <bool ANY, bool COUNT, int LAYOUT>
 __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
     const uint64_t i = (uint64_t)blockIdx.x * TRACE_BLOCK + threadIdx.x;
-    uint32_t n_nodes = 0, n_tris = 0;
+    uint32_t n_nodes = 0, n_tris = 0, w_nodes = 0, w_leaves = 0;
+    const uint32_t lane = threadIdx.x & 31;
     if (i >= a.n) return;
     uint64_t src = i;
     if (a.gather) {
@@ -194,7 +195,10 @@ __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
                 fetch_quant8(a.nodes, node, c);
             else
                 fetch_exact(a.nodes, node, c);
-            if (COUNT) ++n_nodes;
+            if (COUNT) {
+                ++n_nodes;  // this lane's node visit; the lowest active lane counts the warp's step
+                if (lane == (uint32_t)(__ffs(__activemask()) - 1)) ++w_nodes;
+            }
             float tn0, tf0, tn1, tf1;
             slab(r, c.lo0x, c.lo0y, c.lo0z, c.hi0x, c.hi0y, c.hi0z, tcap, tn0, tf0);
             slab(r, c.lo1x, c.lo1y, c.lo1z, c.hi1x, c.hi1y, c.hi1z, tcap, tn1, tf1);
@@ -225,6 +229,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
         }
         // leaves: the parked one, then any leaf that is next on the stack
         while (leaf != REF_NONE) {
+            if (COUNT && lane == (uint32_t)(__ffs(__activemask()) - 1)) ++w_leaves;
             const uint32_t first = leaf & REF_TRI_MASK, cnt = ((leaf >> 29) & 3u) + 1u;
             bool hit_any = false;
             for (uint32_t k = 0; k < cnt; ++k) {
@@ -272,6 +277,8 @@ __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
     if (COUNT) {
         atomicAdd(a.counts, (unsigned long long)n_nodes);
         atomicAdd(a.counts + 1, (unsigned long long)n_tris);
+        if (w_nodes) atomicAdd(a.counts + 2, (unsigned long long)w_nodes);
+        if (w_leaves) atomicAdd(a.counts + 3, (unsigned long long)w_leaves);
     }
 }
 

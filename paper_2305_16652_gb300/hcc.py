@@ -22,8 +22,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "csrc", "_build", "libhcc.so")
 
-HCC_METHOD_NOSORT, HCC_METHOD_HCC, HCC_METHOD_TWOPOINT = 0, 1, 2
-METHODS = {"nosort": HCC_METHOD_NOSORT, "hcc": HCC_METHOD_HCC, "twopoint": HCC_METHOD_TWOPOINT}
+HCC_METHOD_NOSORT, HCC_METHOD_HCC, HCC_METHOD_TWOPOINT, HCC_METHOD_ORIGIN, HCC_METHOD_ORIGIN_DIR = 0, 1, 2, 3, 4
+METHODS = {"nosort": HCC_METHOD_NOSORT, "hcc": HCC_METHOD_HCC, "twopoint": HCC_METHOD_TWOPOINT,
+           "origin": HCC_METHOD_ORIGIN, "origin_dir": HCC_METHOD_ORIGIN_DIR}
 STATUS = {0: "HCC_OK", 1: "HCC_ERR_INVALID_ARG", 2: "HCC_ERR_OOM", 3: "HCC_ERR_CUDA", 4: "HCC_ERR_UNSUPPORTED",
           5: "HCC_ERR_STACK_OVERFLOW", 6: "HCC_ERR_TIMEOUT"}
 HIT_DTYPE = np.dtype([("prim", np.int32), ("t", np.float32), ("u", np.float32), ("v", np.float32)])
@@ -78,7 +79,8 @@ def load(path: str = LIB_PATH):
         "hcc_trace": [P, P, ctypes.POINTER(_Rays), i32, P, P],
         "hcc_run": [P, i32, P, P, ctypes.POINTER(_Rays), u32, i32, P],
         "hcc_run_host": [P, i32, P, P, P, P, u64, u32, i32, P],
-        "hcc_trace_counts": [P, P, ctypes.POINTER(_Rays), i32, P, P],
+        "hcc_trace_counts": [P, P, ctypes.POINTER(_Rays), P, i32, P],
+        "hcc_key_stats": [P, P, u32, P, u64, P, P],
         "hcc_trace_sorted": [P, P, ctypes.POINTER(_Rays), P, i32, P],
         "hcc_sort_noalloc": [P, u32, u64, P, P, P],
     }
@@ -239,13 +241,21 @@ def hcc_trace_sorted(ctx, bvh, org, dir_, perm, hits, any_hit: bool = False):
     _check(load().hcc_trace_sorted(ctx, bvh, ctypes.byref(r), _ptr(perm), int(any_hit), _ptr(hits)), ctx)
 
 
-def hcc_trace_counts(ctx, bvh, org, dir_, any_hit: bool = False):
-    """Diagnostic: total internal-node visits and triangle tests of a trace."""
+def hcc_trace_counts(ctx, bvh, org, dir_, perm=None, any_hit: bool = False):
+    """Diagnostic trace: node visits, triangle tests and warp-level node / leaf steps."""
     r = _rays(org, dir_)
-    nv, nt = ctypes.c_uint64(), ctypes.c_uint64()
-    _check(load().hcc_trace_counts(ctx, bvh, ctypes.byref(r), int(any_hit), ctypes.byref(nv), ctypes.byref(nt)),
-           ctx)
-    return {"node_visits": int(nv.value), "tri_tests": int(nt.value)}
+    c = (ctypes.c_uint64 * 4)()
+    _check(load().hcc_trace_counts(ctx, bvh, ctypes.byref(r), _ptr(perm), int(any_hit), c), ctx)
+    return {"node_visits": int(c[0]), "tri_tests": int(c[1]), "warp_node_steps": int(c[2]),
+            "warp_leaf_steps": int(c[3])}
+
+
+def hcc_key_stats(ctx, keys, key_bits: int, perm, n: int):
+    """Distinct keys and average distinct codes per warp of keys in sorted order."""
+    anc, distinct = ctypes.c_double(), ctypes.c_uint64()
+    _check(load().hcc_key_stats(ctx, _ptr(keys), key_bits, _ptr(perm), n, ctypes.byref(anc),
+                                ctypes.byref(distinct)), ctx)
+    return {"anc": anc.value, "distinct": int(distinct.value)}
 
 
 def hcc_run(ctx, method, bvh, cut, org, dir_, key_bits: int, hits, any_hit: bool = False):

@@ -169,6 +169,44 @@ def test_encode_twopoint_matches_oracle(ctx, room, k):
     assert np.array_equal(g, o)
 
 
+@pytest.mark.parametrize("k", [1, 3, 6, 16, 24, 31, 32, 33, 48, 64])
+def test_encode_origin_keys_match_oracle(ctx, room, k):
+    lo, hi = room.w.bvh.lo[0], room.w.bvh.hi[0]
+    g = gpu_encode(ctx, room, "origin", k)
+    assert np.array_equal(g, oracle.encode_origin(room.w.rays.org, lo, hi, k))
+    g = gpu_encode(ctx, room, "origin_dir", k)
+    assert np.array_equal(g, oracle.encode_origin_dir(room.w.rays.org, room.w.rays.dir, lo, hi, k))
+
+
+@pytest.mark.parametrize("method,k", [("hcc", 16), ("hcc", 32), ("hcc", 64), ("twopoint", 32), ("origin_dir", 24)])
+def test_key_stats_match_oracle(ctx, room, method, k):
+    cut = hcc.hcc_select_cut(ctx, room.bvh, max(k, 32), 0.125) if method == "hcc" else None
+    keys = _keys_tensor(room.n, k)
+    perm = torch.zeros(room.n, dtype=torch.int32, device=DEV)
+    try:
+        hcc.hcc_encode(ctx, method, room.bvh, cut, room.org, room.dir, k, keys)
+        hcc.hcc_sort(ctx, keys, k, room.n, perm)
+        st = hcc.hcc_key_stats(ctx, keys, k, perm, room.n)
+    finally:
+        if cut is not None:
+            hcc.hcc_cut_destroy(cut)
+    ku, pu = _u64(keys, k), perm.cpu().numpy().view(np.uint32)
+    assert st["distinct"] == len(np.unique(ku))
+    assert abs(st["anc"] - oracle.anc(ku, pu)) < 1e-12
+
+
+def test_trace_counts_are_consistent(ctx, room):
+    """Visits depend on the warp a ray shares (a lane holding a parked leaf keeps descending),
+    so the two orders may differ in work, never in the counts' internal consistency."""
+    rng = np.random.default_rng(8)
+    perm = torch.from_numpy(rng.permutation(room.n).astype(np.int32)).to(DEV)
+    for c in (hcc.hcc_trace_counts(ctx, room.bvh_exact, room.org, room.dir),
+              hcc.hcc_trace_counts(ctx, room.bvh_exact, room.org, room.dir, perm=perm)):
+        assert c["node_visits"] > 0 and c["tri_tests"] > 0
+        assert c["warp_node_steps"] <= c["node_visits"] <= 32 * c["warp_node_steps"]
+        assert c["warp_leaf_steps"] > 0
+
+
 def test_encode_special_rays(ctx, tiny):
     """Zero direction components, origins on box faces, NaN and Inf inputs."""
     cut = hcc.hcc_select_cut(ctx, tiny.bvh, 32, 0.125)
@@ -193,6 +231,9 @@ def test_encode_special_rays(ctx, tiny):
             assert np.array_equal(g, oracle.encode_hcc(org, dir_, lo, hi, k))
         g = gpu_encode(ctx, tiny, "twopoint", 32, org=o_t, dir_=d_t)
         assert np.array_equal(g, oracle.encode_twopoint(org, dir_, tiny.w.bvh.lo[0], tiny.w.bvh.hi[0], 32))
+        for k in (24, 64):
+            g = gpu_encode(ctx, tiny, "origin_dir", k, org=o_t, dir_=d_t)
+            assert np.array_equal(g, oracle.encode_origin_dir(org, dir_, tiny.w.bvh.lo[0], tiny.w.bvh.hi[0], k))
     finally:
         hcc.hcc_cut_destroy(cut)
 
@@ -352,7 +393,7 @@ def test_pipeline_methods_agree_bit_for_bit(ctx, which, request):
     sc = request.getfixturevalue(which)
     base = run_pipeline(ctx, sc, "nosort")
     for method, k, C in (("hcc", 32, 32), ("hcc", 32, 256), ("hcc", 64, 64), ("hcc", 16, 4096), ("twopoint", 32, 0),
-                         ("twopoint", 64, 0)):
+                         ("twopoint", 64, 0), ("origin", 30, 0), ("origin_dir", 48, 0)):
         assert run_pipeline(ctx, sc, method, k, C).tobytes() == base.tobytes(), (method, k, C)
     compare_hits(base, oracle.trace_bvh(sc.w.bvh, sc.w.rays.org, sc.w.rays.dir))
 
