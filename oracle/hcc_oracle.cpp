@@ -24,6 +24,9 @@
 //                         origin Morton code in the high bits, a Morton code
 //                         of the octahedral parametrisation of the direction
 //                         in the low bits
+//   oracle_spawn          next-bounce diffuse rays (wavefront path tracing,
+//                         Sec. 5 pipeline; the definition is the one stated
+//                         for hcc_batch_spawn, restated here independently)
 //   oracle_stable_sort    sort keys as natural numbers (Sec. 4.2.3 "Sorting",
 //                         Sec. 5: sort of ray indices)
 //   oracle_gather         rays fetched through the sorted indices (Sec. 5)
@@ -346,6 +349,84 @@ double oracle_anc(uint64_t n, const uint64_t *keys, const uint32_t *perm) {
         ++groups;
     }
     return (double)distinct / (double)groups;
+}
+
+static uint64_t splitmix(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Uniform number j of ray i: the top 24 bits of SplitMix64(SplitMix64(seed)
+// ^ (64 i + j)) scaled by 2^-24.
+static float uniform24(uint64_t seed_mixed, uint64_t i, uint32_t j) {
+    uint64_t z = splitmix(seed_mixed ^ (i * 64u + j));
+    return (float)(uint32_t)(z >> 40) * 5.9604644775390625e-08f;
+}
+
+// Next bounce: a ray that hit triangle p at distance t spawns a diffuse ray
+// from o + t d, cosine-weighted about the triangle's unit normal turned
+// toward the incoming ray (a point of the unit disk by rejection, lifted to
+// the hemisphere, in the orthonormal basis of Duff et al. 2017); a miss
+// becomes the empty ray [1, 0] at the old origin.  tris: the scene's
+// triangles (v0, v1, v2); hits: records {prim, t, u, v}.
+void oracle_spawn(uint64_t n, const float *org, const float *dir, const void *hits_in, const float *tris,
+                  uint32_t ntris, uint64_t seed, float tmin, float *out_org, float *out_dir) {
+    const Hit *hits = (const Hit *)hits_in;
+    const uint64_t sm = splitmix(seed);
+    for (uint64_t i = 0; i < n; ++i) {
+        const float *o = org + 4 * i, *d = dir + 4 * i;
+        const Hit h = hits[i];
+        if (h.prim < 0 || (uint32_t)h.prim >= ntris) {
+            out_org[4 * i] = o[0];
+            out_org[4 * i + 1] = o[1];
+            out_org[4 * i + 2] = o[2];
+            out_org[4 * i + 3] = 1.0f;
+            out_dir[4 * i] = d[0];
+            out_dir[4 * i + 1] = d[1];
+            out_dir[4 * i + 2] = d[2];
+            out_dir[4 * i + 3] = 0.0f;
+            continue;
+        }
+        const float *T = tris + 9 * (uint64_t)h.prim;
+        V3 v0{T[0], T[1], T[2]}, v1{T[3], T[4], T[5]}, v2{T[6], T[7], T[8]};
+        V3 nrm = cross(sub(v1, v0), sub(v2, v0));
+        float len = std::sqrt(dot(nrm, nrm));
+        if (len > 0.0f)
+            nrm = {nrm.x / len, nrm.y / len, nrm.z / len};
+        else
+            nrm = {0.0f, 0.0f, 1.0f};
+        V3 dv{d[0], d[1], d[2]};
+        if (dot(nrm, dv) > 0.0f) nrm = {-nrm.x, -nrm.y, -nrm.z};
+        float x = 0.0f, y = 0.0f, r2 = 0.0f;
+        for (uint32_t a = 0; a < 16; ++a) {
+            float cx = 2.0f * uniform24(sm, i, 2 * a) - 1.0f;
+            float cy = 2.0f * uniform24(sm, i, 2 * a + 1) - 1.0f;
+            float c2 = std::fma(cy, cy, cx * cx);
+            if (c2 <= 1.0f) {
+                x = cx;
+                y = cy;
+                r2 = c2;
+                break;
+            }
+        }
+        float z = std::sqrt(std::fmax(0.0f, 1.0f - r2));
+        float sign = std::copysign(1.0f, nrm.z);
+        float aa = -1.0f / (sign + nrm.z);
+        float bb = (nrm.x * nrm.y) * aa;
+        V3 b1{1.0f + ((sign * nrm.x) * nrm.x) * aa, sign * bb, -(sign * nrm.x)};
+        V3 b2{bb, sign + (nrm.y * nrm.y) * aa, -nrm.y};
+        float t = h.t;
+        out_org[4 * i] = std::fma(t, d[0], o[0]);
+        out_org[4 * i + 1] = std::fma(t, d[1], o[1]);
+        out_org[4 * i + 2] = std::fma(t, d[2], o[2]);
+        out_org[4 * i + 3] = tmin;
+        out_dir[4 * i] = std::fma(z, nrm.x, std::fma(y, b2.x, x * b1.x));
+        out_dir[4 * i + 1] = std::fma(z, nrm.y, std::fma(y, b2.y, x * b1.y));
+        out_dir[4 * i + 2] = std::fma(z, nrm.z, std::fma(y, b2.z, x * b1.z));
+        out_dir[4 * i + 3] = INFINITY;
+    }
 }
 
 // Rays sorted by key as natural numbers (Sec. 4.2.3), realised as a stable

@@ -538,3 +538,30 @@ def test_anc_closed_forms():
     assert oracle.anc(np.arange(64, dtype=np.uint64), perm) == 32.0
     keys = np.repeat(np.arange(8, dtype=np.uint64), 8)  # each warp of 32 holds 4 codes
     assert oracle.anc(keys, perm) == 4.0
+
+
+# ------------------------------------------------------------- next bounce
+
+def test_spawn_rays_are_cosine_distributed_on_the_visible_side():
+    """Spawned directions are unit, on the side facing the incoming ray, and
+    cosine-distributed: E[cos] = 2/3 and E[cos^2] = 1/2 about the normal."""
+    tri = np.array([[0, 0, 0, 1, 0, 0, 0, 1, 0]], np.float32)  # normal +z
+    n = 20000
+    org = np.tile(np.array([[0.25, 0.25, 1.0, 1e-4]], np.float32), (n, 1))
+    dir_ = np.tile(np.array([[0, 0, -1, np.inf]], np.float32), (n, 1))
+    hits = np.zeros(n, oracle.HIT_DTYPE)
+    hits["prim"], hits["t"] = 0, 1.0
+    oo, od = oracle.spawn(org, dir_, hits, tri, seed=7, tmin=1e-4)
+    assert np.allclose(oo[:, :3], [0.25, 0.25, 0.0]) and np.all(oo[:, 3] == np.float32(1e-4))
+    c = od[:, 2].astype(np.float64)
+    assert np.all(c >= 0) and np.allclose(np.linalg.norm(od[:, :3], axis=1), 1, atol=1e-5)
+    assert abs(c.mean() - 2 / 3) < 0.01 and abs((c ** 2).mean() - 0.5) < 0.01
+    # incoming from below: the normal flips, directions go to -z
+    _, od2 = oracle.spawn(org * [1, 1, -1, 1], -dir_ * [1, 1, 1, -1], hits, tri, seed=7, tmin=1e-4)
+    assert np.all(od2[:, 2] <= 0)
+    # misses become empty rays, and the draw depends on the seed
+    hits["prim"][::2] = -1
+    oo3, od3 = oracle.spawn(org, dir_, hits, tri, seed=7, tmin=1e-4)
+    assert np.all(oo3[::2, 3] == 1) and np.all(od3[::2, 3] == 0)
+    _, od4 = oracle.spawn(org, dir_, hits, tri, seed=8, tmin=1e-4)
+    assert not np.array_equal(od3[1::2], od4[1::2])
