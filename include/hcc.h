@@ -331,6 +331,69 @@ hcc_status hcc_trace_sorted(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *ra
 hcc_status hcc_trace_counts(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *rays, const uint32_t *perm,
                             int any_hit, uint64_t counts[4]);
 
+/* ---------------------------------------------- batches of wavefronts */
+
+/*
+ * A batch: the wavefronts of several scenes traced together.  Scene s owns
+ * rays [offsets[s], offsets[s+1]) of the batch's combined ray buffers; its
+ * BVH is bvhs[s] and, for HCC keys, its cut is cuts[s] (cuts may be NULL for
+ * other methods).  All BVHs must use the same node layout.  offsets (host,
+ * num_scenes + 1 entries, offsets[0] = 0, non-decreasing) and the scene table
+ * are copied to the device; the handles must outlive the batch.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+typedef struct hcc_batch hcc_batch;
+hcc_status hcc_batch_create(hcc_ctx *ctx, uint32_t num_scenes, const hcc_bvh *const *bvhs, const hcc_cut *const *cuts,
+                            const uint64_t *offsets, hcc_batch **out);
+hcc_status hcc_batch_destroy(hcc_batch *batch);
+
+/*
+ * One bounce of every wavefront of the batch with one launch per stage:
+ * one encode over all rays (each against its own scene's cut or box, the
+ * scene index placed above the key_bits key), one sort of the combined keys
+ * (rays grouped by scene, then by key), one trace that fetches each ray
+ * through the permutation and traverses its own scene's BVH.  NOSORT traces
+ * in input order.  hits[i] is the record of ray i in its scene (triangle ids
+ * of that scene).  key_bits plus ceil(log2(num_scenes)) must be <= 64.
+ * rays->n must equal offsets[num_scenes].  Asynchronous; no host
+ * synchronisation inside (scratch is grown first if needed, see
+ * hcc_reserve).  Errors: as hcc_run.
+ */
+hcc_status hcc_batch_run(hcc_ctx *ctx, const hcc_batch *batch, hcc_method method, const hcc_rays *rays,
+                         uint32_t key_bits, int any_hit, hcc_hit *hits);
+
+/*
+ * The next bounce of a batch (ray generation between bounces, not part of
+ * the reordering method): for every ray i with hits[i].prim >= 0, a diffuse
+ * ray leaving its hit point o + t d, cosine-weighted about the hit
+ * triangle's normal turned toward the incoming ray, interval [tmin, +inf);
+ * a ray that missed becomes the empty ray (interval [1, 0]) at its old
+ * origin.  Random numbers: the top 24 bits of SplitMix64(SplitMix64(seed) ^
+ * (64 i + j)); the direction is the first point of the unit disk found by
+ * rejection among 16 tries (else the centre) lifted to the hemisphere, in
+ * the orthonormal basis of Duff et al. 2017; every step is a correctly
+ * rounded FP32 operation so the rays are reproducible.  in and out must be
+ * different buffers with n = offsets[num_scenes].
+ * Errors: INVALID_ARG, CUDA; INVALID_ARG at hcc_sync for a hit whose
+ * triangle id is outside its scene (that ray becomes empty).
+ */
+hcc_status hcc_batch_spawn(hcc_ctx *ctx, const hcc_batch *batch, const hcc_rays *in, const hcc_hit *hits,
+                           uint64_t seed, float tmin, const hcc_rays *out);
+
+/*
+ * CUDA graph of one batch bounce: reserves the scratch hcc_batch_run needs,
+ * captures hcc_batch_run(ctx, batch, method, rays, key_bits, any_hit, hits)
+ * on the context's stream (which must not be the legacy default stream) and
+ * instantiates it.  hcc_graph_launch replays it on the context's stream with
+ * the same buffers; the rays may be rewritten between launches.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+typedef struct hcc_graph hcc_graph;
+hcc_status hcc_graph_capture_batch(hcc_ctx *ctx, const hcc_batch *batch, hcc_method method, const hcc_rays *rays,
+                                   uint32_t key_bits, int any_hit, hcc_hit *hits, hcc_graph **out);
+hcc_status hcc_graph_launch(hcc_ctx *ctx, const hcc_graph *graph);
+hcc_status hcc_graph_destroy(hcc_graph *graph);
+
 /* ------------------------------------------------------- whole pipeline */
 
 /*

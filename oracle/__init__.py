@@ -60,7 +60,7 @@ def _load():
     lib.oracle_octahedral.restype = None
     lib.oracle_anc.argtypes = [u64, P, P]
     lib.oracle_anc.restype = f64
-    lib.oracle_spawn.argtypes = [u64, P, P, P, P, u32, u64, f32, P, P]
+    lib.oracle_spawn.argtypes = [u64, P, P, P, P, u32, u64, f32, u64, P, P]
     lib.oracle_spawn.restype = None
     lib.oracle_stable_sort.argtypes = [u64, P, P]
     lib.oracle_stable_sort.restype = None
@@ -167,14 +167,16 @@ def anc(keys, perm) -> float:
     return float(_load().oracle_anc(keys.shape[0], _p(keys), _p(perm)))
 
 
-def spawn(org, dir, hits, tris, seed: int, tmin: float):
-    """Next-bounce rays from hit records (structured HIT_DTYPE array)."""
+def spawn(org, dir, hits, tris, seed: int, tmin: float, first_index: int = 0):
+    """Next-bounce rays from hit records (structured HIT_DTYPE array); ray k is
+    ray first_index + k of its batch."""
     org, dir, tris = _c(org, np.float32), _c(dir, np.float32), _c(tris, np.float32)
     hits = np.ascontiguousarray(hits, dtype=HIT_DTYPE)
     n = org.shape[0]
     oo = np.zeros((n, 4), np.float32)
     od = np.zeros((n, 4), np.float32)
-    _load().oracle_spawn(n, _p(org), _p(dir), _p(hits), _p(tris), tris.shape[0], seed, tmin, _p(oo), _p(od))
+    _load().oracle_spawn(n, _p(org), _p(dir), _p(hits), _p(tris), tris.shape[0], seed, tmin, first_index, _p(oo),
+                         _p(od))
     return oo, od
 
 

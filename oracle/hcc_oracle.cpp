@@ -370,9 +370,10 @@ static float uniform24(uint64_t seed_mixed, uint64_t i, uint32_t j) {
 // toward the incoming ray (a point of the unit disk by rejection, lifted to
 // the hemisphere, in the orthonormal basis of Duff et al. 2017); a miss
 // becomes the empty ray [1, 0] at the old origin.  tris: the scene's
-// triangles (v0, v1, v2); hits: records {prim, t, u, v}.
+// triangles (v0, v1, v2); hits: records {prim, t, u, v}.  Ray k of the call
+// is ray first_index + k of its batch (the index keys its random numbers).
 void oracle_spawn(uint64_t n, const float *org, const float *dir, const void *hits_in, const float *tris,
-                  uint32_t ntris, uint64_t seed, float tmin, float *out_org, float *out_dir) {
+                  uint32_t ntris, uint64_t seed, float tmin, uint64_t first_index, float *out_org, float *out_dir) {
     const Hit *hits = (const Hit *)hits_in;
     const uint64_t sm = splitmix(seed);
     for (uint64_t i = 0; i < n; ++i) {
@@ -401,8 +402,8 @@ void oracle_spawn(uint64_t n, const float *org, const float *dir, const void *hi
         if (dot(nrm, dv) > 0.0f) nrm = {-nrm.x, -nrm.y, -nrm.z};
         float x = 0.0f, y = 0.0f, r2 = 0.0f;
         for (uint32_t a = 0; a < 16; ++a) {
-            float cx = 2.0f * uniform24(sm, i, 2 * a) - 1.0f;
-            float cy = 2.0f * uniform24(sm, i, 2 * a + 1) - 1.0f;
+            float cx = 2.0f * uniform24(sm, first_index + i, 2 * a) - 1.0f;
+            float cy = 2.0f * uniform24(sm, first_index + i, 2 * a + 1) - 1.0f;
             float c2 = std::fma(cy, cy, cx * cx);
             if (c2 <= 1.0f) {
                 x = cx;

@@ -22,11 +22,22 @@ int encode_grid(uint64_t n, int block, int per_sm) {
     return (int)(want < cap ? (want ? want : 1) : cap);
 }
 
+// Slab test of one ray against one box: t = (bound - o) * (1/d) per axis,
+// tnear = max over axes and tmin, tfar = min over axes and tmax, met when
+// tnear <= tfar (fminf/fmaxf ignore the NaN of 0 * inf).
+__device__ __forceinline__ bool meets(const float4 &o, const float4 &d, float ix, float iy, float iz, const float4 &lo,
+                                      const float4 &hi) {
+    const float ax = __fmul_rn(__fsub_rn(lo.x, o.x), ix), bx = __fmul_rn(__fsub_rn(hi.x, o.x), ix);
+    const float ay = __fmul_rn(__fsub_rn(lo.y, o.y), iy), by = __fmul_rn(__fsub_rn(hi.y, o.y), iy);
+    const float az = __fmul_rn(__fsub_rn(lo.z, o.z), iz), bz = __fmul_rn(__fsub_rn(hi.z, o.z), iz);
+    const float tnear = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), o.w));
+    const float tfar = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), d.w));
+    return tnear <= tfar;
+}
+
 // Algorithm 1: the cut nodes are staged in shared memory once per block
 // (line 1); every ray is tested against every cut node and each result sets
-// one key bit.  Cut node r drives bit (key_bits - 1 - r).  Slab test per
-// axis: t = (bound - o) * (1/d), tn = min, tf = max; tnear = max over axes
-// and tmin, tfar = min over axes and tmax; the node is met when tnear <= tfar.
+// one key bit.  Cut node r drives bit (key_bits - 1 - r).
 template <typename K>
 __global__ void __launch_bounds__(ENC_BLOCK) k_encode_hcc(const float4 *__restrict__ org,
                                                           const float4 *__restrict__ dir, uint64_t n,
@@ -45,15 +56,8 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_hcc(const float4 *__restri
         const float ix = __frcp_rn(d.x), iy = __frcp_rn(d.y), iz = __frcp_rn(d.z);
         K key = 0;
         K bit = (K)1 << (key_bits - 1);
-        for (uint32_t r = 0; r < used; ++r, bit >>= 1) {
-            const float4 lo = s_lo[r], hi = s_hi[r];
-            const float ax = __fmul_rn(__fsub_rn(lo.x, o.x), ix), bx = __fmul_rn(__fsub_rn(hi.x, o.x), ix);
-            const float ay = __fmul_rn(__fsub_rn(lo.y, o.y), iy), by = __fmul_rn(__fsub_rn(hi.y, o.y), iy);
-            const float az = __fmul_rn(__fsub_rn(lo.z, o.z), iz), bz = __fmul_rn(__fsub_rn(hi.z, o.z), iz);
-            const float tnear = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), o.w));
-            const float tfar = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), d.w));
-            if (tnear <= tfar) key |= bit;
-        }
+        for (uint32_t r = 0; r < used; ++r, bit >>= 1)
+            if (meets(o, d, ix, iy, iz, s_lo[r], s_hi[r])) key |= bit;
         __stcs(keys + i, key);
     }
 }
@@ -117,6 +121,24 @@ __device__ __forceinline__ K interleave(const uint32_t (&q)[M], uint32_t b) {
     return key;
 }
 
+// Octahedral map of a direction: L1-normalise, fold the lower hemisphere
+// (z < 0) over the diagonals, map [-1, 1]^2 to [0, 1]^2; zero -> centre.
+__device__ __forceinline__ void octahedral(const float4 &d, float &u, float &v) {
+    u = 0.5f;
+    v = 0.5f;
+    const float s = __fadd_rn(__fadd_rn(fabsf(d.x), fabsf(d.y)), fabsf(d.z));
+    if (s > 0.0f) {
+        const float nx = __fdiv_rn(d.x, s), ny = __fdiv_rn(d.y, s), nz = __fdiv_rn(d.z, s);
+        float x = nx, y = ny;
+        if (nz < 0.0f) {
+            x = __fmul_rn(__fsub_rn(1.0f, fabsf(ny)), nx >= 0.0f ? 1.0f : -1.0f);
+            y = __fmul_rn(__fsub_rn(1.0f, fabsf(nx)), ny >= 0.0f ? 1.0f : -1.0f);
+        }
+        u = __fadd_rn(__fmul_rn(x, 0.5f), 0.5f);
+        v = __fadd_rn(__fmul_rn(y, 0.5f), 0.5f);
+    }
+}
+
 // Origin key: 3D Morton code of the origin, floor(k/3) bits per axis,
 // left-justified in k bits.
 template <typename K>
@@ -149,19 +171,8 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_origin_dir(const float4 *_
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const float4 o = __ldcs(org + i);
         const float4 d = __ldcs(dir + i);
-        // octahedral map: L1-normalise, fold the lower hemisphere, map to [0, 1]^2
-        float u = 0.5f, v = 0.5f;
-        const float s = __fadd_rn(__fadd_rn(fabsf(d.x), fabsf(d.y)), fabsf(d.z));
-        if (s > 0.0f) {
-            const float nx = __fdiv_rn(d.x, s), ny = __fdiv_rn(d.y, s), nz = __fdiv_rn(d.z, s);
-            float x = nx, y = ny;
-            if (nz < 0.0f) {
-                x = __fmul_rn(__fsub_rn(1.0f, fabsf(ny)), nx >= 0.0f ? 1.0f : -1.0f);
-                y = __fmul_rn(__fsub_rn(1.0f, fabsf(nx)), ny >= 0.0f ? 1.0f : -1.0f);
-            }
-            u = __fadd_rn(__fmul_rn(x, 0.5f), 0.5f);
-            v = __fadd_rn(__fmul_rn(y, 0.5f), 0.5f);
-        }
+        float u, v;
+        octahedral(d, u, v);
         const uint32_t qo[3] = {quantise(o.x, lox, ex, bo), quantise(o.y, loy, ey, bo), quantise(o.z, loz, ez, bo)};
         const uint32_t qd[2] = {quantise(u, 0.0f, 1.0f, bd), quantise(v, 0.0f, 1.0f, bd)};
         K key = (interleave<K, 3>(qo, bo) << (2 * bd)) | interleave<K, 2>(qd, bd);
@@ -189,7 +200,102 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_key_stats(const K *__restrict__ k
     if (inner) atomicAdd(cnt + 1, inner);
 }
 
+// TwoPoint / Origin / Origin-Direction keys of one ray (the formulas of the
+// single-scene kernels above, as functions of the scene box).
+template <typename K>
+__device__ __forceinline__ K twopoint_key(const float4 &o, const float4 &d, const SceneDesc &sc, uint32_t key_bits) {
+    const uint32_t b = key_bits / 6, pad = key_bits - 6 * b;
+    const float p[6] = {o.x, o.y, o.z, __fmaf_rn(sc.L, d.x, o.x), __fmaf_rn(sc.L, d.y, o.y),
+                        __fmaf_rn(sc.L, d.z, o.z)};
+    uint32_t q[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) q[c] = quantise(p[c], sc.lo[c % 3], sc.ext[c % 3], b);
+    K key = interleave<K, 6>(q, b);
+    return pad ? (K)(key << pad) : key;
+}
+
+template <typename K>
+__device__ __forceinline__ K origin_key(const float4 &o, const SceneDesc &sc, uint32_t key_bits) {
+    const uint32_t b = key_bits / 3, pad = key_bits - 3 * b;
+    const uint32_t q[3] = {quantise(o.x, sc.lo[0], sc.ext[0], b), quantise(o.y, sc.lo[1], sc.ext[1], b),
+                           quantise(o.z, sc.lo[2], sc.ext[2], b)};
+    K key = interleave<K, 3>(q, b);
+    return pad ? (K)(key << pad) : key;
+}
+
+template <typename K>
+__device__ __forceinline__ K origin_dir_key(const float4 &o, const float4 &d, const SceneDesc &sc, uint32_t key_bits) {
+    const uint32_t bd = key_bits / 6, bo = (key_bits - 2 * bd) / 3, pad = key_bits - (3 * bo + 2 * bd);
+    float u, v;
+    octahedral(d, u, v);
+    const uint32_t qo[3] = {quantise(o.x, sc.lo[0], sc.ext[0], bo), quantise(o.y, sc.lo[1], sc.ext[1], bo),
+                            quantise(o.z, sc.lo[2], sc.ext[2], bo)};
+    const uint32_t qd[2] = {quantise(u, 0.0f, 1.0f, bd), quantise(v, 0.0f, 1.0f, bd)};
+    K key = (interleave<K, 3>(qo, bo) << (2 * bd)) | interleave<K, 2>(qd, bd);
+    return pad ? (K)(key << pad) : key;
+}
+
+// Batch of wavefronts: one launch encodes the rays of every scene against
+// that scene's cut or box; the scene index sits above the key so that one
+// sort groups rays by scene, then by key.
+template <typename K, int METHOD>
+__global__ void __launch_bounds__(ENC_BLOCK) k_encode_multi(const float4 *__restrict__ org,
+                                                            const float4 *__restrict__ dir, uint64_t n,
+                                                            const SceneDesc *__restrict__ scenes,
+                                                            const uint64_t *__restrict__ offsets, uint32_t num_scenes,
+                                                            uint32_t key_bits, K *__restrict__ keys) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t s = scene_of(offsets, num_scenes, i);
+        const SceneDesc &sc = scenes[s];
+        const float4 o = __ldcs(org + i);
+        const float4 d = __ldcs(dir + i);
+        K key = 0;
+        if (METHOD == HCC_METHOD_HCC) {
+            const float ix = __frcp_rn(d.x), iy = __frcp_rn(d.y), iz = __frcp_rn(d.z);
+            K bit = (K)1 << (key_bits - 1);
+            for (uint32_t r = 0; r < sc.used; ++r, bit >>= 1)
+                if (meets(o, d, ix, iy, iz, __ldg(sc.cut + 2 * r), __ldg(sc.cut + 2 * r + 1))) key |= bit;
+        } else if (METHOD == HCC_METHOD_TWOPOINT) {
+            key = twopoint_key<K>(o, d, sc, key_bits);
+        } else if (METHOD == HCC_METHOD_ORIGIN) {
+            key = origin_key<K>(o, sc, key_bits);
+        } else {
+            key = origin_dir_key<K>(o, d, sc, key_bits);
+        }
+        if (key_bits < 8 * sizeof(K)) key |= (K)s << key_bits;
+        __stcs(keys + i, key);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_encode_multi(cudaStream_t s, int method, const float4 *org, const float4 *dir, uint64_t n,
+                                const SceneDesc *scenes, const uint64_t *offsets, uint32_t num_scenes,
+                                uint32_t key_bits, uint32_t total_bits, void *keys) {
+    if (n == 0) return cudaSuccess;
+    const int grid = encode_grid(n, ENC_BLOCK, 8);
+#define HCC_ENC_MULTI(K, M) \
+    k_encode_multi<K, M><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, scenes, offsets, num_scenes, key_bits, (K *)keys)
+#define HCC_ENC_MULTI_K(K)                                                      \
+    do {                                                                        \
+        if (method == HCC_METHOD_HCC)                                           \
+            HCC_ENC_MULTI(K, HCC_METHOD_HCC);                                   \
+        else if (method == HCC_METHOD_TWOPOINT)                                 \
+            HCC_ENC_MULTI(K, HCC_METHOD_TWOPOINT);                              \
+        else if (method == HCC_METHOD_ORIGIN)                                   \
+            HCC_ENC_MULTI(K, HCC_METHOD_ORIGIN);                                \
+        else                                                                    \
+            HCC_ENC_MULTI(K, HCC_METHOD_ORIGIN_DIR);                            \
+    } while (0)
+    if (total_bits <= 32)
+        HCC_ENC_MULTI_K(uint32_t);
+    else
+        HCC_ENC_MULTI_K(uint64_t);
+#undef HCC_ENC_MULTI_K
+#undef HCC_ENC_MULTI
+    return cudaGetLastError();
+}
 
 cudaError_t launch_key_stats(cudaStream_t s, const void *keys, uint32_t key_bits, const uint32_t *perm, uint64_t n,
                              unsigned long long *cnt) {

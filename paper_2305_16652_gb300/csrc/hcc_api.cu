@@ -37,6 +37,7 @@ struct hcc_bvh {
     int layout = HCC_BVH_QUANTISED;
     uint4 *d_nodes = nullptr;
     float4 *d_tris = nullptr;
+    uint32_t *d_prim_rec = nullptr;  // triangle id -> record index
     uint32_t num_nodes = 0, num_internal = 0, num_tris = 0, depth = 0;
     uint32_t root_ref = 0;
     // exact tree kept on the host for cut selection
@@ -52,9 +53,26 @@ struct hcc_cut {
     uint32_t on_device = 0;
 };
 
+struct hcc_batch {
+    int device = 0;
+    int layout = 0;
+    uint32_t num_scenes = 0;
+    uint32_t scene_bits = 0;  // bits above the key that hold the scene index
+    std::vector<uint64_t> offsets;
+    hcc::SceneDesc *d_scenes = nullptr;
+    uint64_t *d_offsets = nullptr;
+};
+
+struct hcc_graph {
+    int device = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
 namespace {
 
 constexpr uint32_t MAX_KEY_NODES = 64;
+constexpr uint32_t MAX_BATCH_SCENES = 1024;
 
 hcc_status fail(hcc_ctx *ctx, hcc_status st, const char *fmt, ...) {
     if (ctx) {
@@ -459,10 +477,14 @@ hcc_status hcc_bvh_upload_layout(hcc_ctx *ctx, const hcc_bvh_desc *d, hcc_bvh_la
     b->right.assign(d->right, d->right + N);
     b->count.assign(d->count, d->count + N);
     DeviceGuard g(ctx->device);
+    std::vector<uint32_t> prim_rec(T, 0u);
+    for (uint32_t k = 0; k < T; ++k) prim_rec[d->order[k]] = k;
     cudaError_t e = cudaMalloc(&b->d_nodes, words.size() * 4);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tris, tri.size() * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_prim_rec, (size_t)T * 4);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_nodes, words.data(), words.size() * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_tris, tri.data(), tri.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_prim_rec, prim_rec.data(), (size_t)T * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaGetLastError();
         hcc_bvh_destroy(b);
@@ -491,6 +513,7 @@ hcc_status hcc_bvh_destroy(hcc_bvh *b) {
         DeviceGuard g(b->device);
         if (b->d_nodes) cudaFree(b->d_nodes);
         if (b->d_tris) cudaFree(b->d_tris);
+        if (b->d_prim_rec) cudaFree(b->d_prim_rec);
     }
     delete b;
     return HCC_OK;
@@ -698,6 +721,9 @@ hcc_status hcc_trace(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *rays, int
     a.hits = reinterpret_cast<int4 *>(hits);
     a.err = ctx->d_err;
     a.counts = nullptr;
+    a.scenes = nullptr;
+    a.offsets = nullptr;
+    a.num_scenes = 0;
     cudaError_t e = launch_trace(ctx->stream, a, any_hit);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "trace launch");
     return HCC_OK;
@@ -726,6 +752,9 @@ hcc_status hcc_trace_sorted(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *ra
     a.hits = reinterpret_cast<int4 *>(hits);
     a.err = ctx->d_err;
     a.counts = nullptr;
+    a.scenes = nullptr;
+    a.offsets = nullptr;
+    a.num_scenes = 0;
     cudaError_t e = launch_trace(ctx->stream, a, any_hit);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "trace launch");
     return HCC_OK;
@@ -759,6 +788,9 @@ hcc_status hcc_trace_counts(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *ra
     a.hits = reinterpret_cast<int4 *>(tmp.p);
     a.err = ctx->d_err;
     a.counts = cnt;
+    a.scenes = nullptr;
+    a.offsets = nullptr;
+    a.num_scenes = 0;
     if (e == cudaSuccess) e = launch_trace(ctx->stream, a, any_hit);
     unsigned long long host[4] = {0, 0, 0, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(host, cnt, sizeof host, cudaMemcpyDeviceToHost, ctx->stream);
@@ -766,6 +798,206 @@ hcc_status hcc_trace_counts(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *ra
     release(tmp);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "counting trace");
     for (int k = 0; k < 4; ++k) counts[k] = host[k];
+    return HCC_OK;
+}
+
+// ----------------------------------------------------------------- batch
+
+hcc_status hcc_batch_create(hcc_ctx *ctx, uint32_t num_scenes, const hcc_bvh *const *bvhs, const hcc_cut *const *cuts,
+                            const uint64_t *offsets, hcc_batch **out) {
+    if (!ctx || !bvhs || !offsets || !out) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (num_scenes == 0 || num_scenes > MAX_BATCH_SCENES)
+        return fail(ctx, HCC_ERR_INVALID_ARG, "a batch holds 1..%u scenes", MAX_BATCH_SCENES);
+    if (offsets[0] != 0) return fail(ctx, HCC_ERR_INVALID_ARG, "offsets[0] must be 0");
+    for (uint32_t s = 0; s < num_scenes; ++s) {
+        if (!bvhs[s]) return fail(ctx, HCC_ERR_INVALID_ARG, "scene %u has no BVH", s);
+        if (bvhs[s]->layout != bvhs[0]->layout)
+            return fail(ctx, HCC_ERR_INVALID_ARG, "all BVHs of a batch need the same node layout");
+        if (offsets[s + 1] < offsets[s]) return fail(ctx, HCC_ERR_INVALID_ARG, "offsets must not decrease");
+    }
+    if (offsets[num_scenes] > HCC_MAX_SORT_N) return fail(ctx, HCC_ERR_INVALID_ARG, "batch above HCC_MAX_SORT_N rays");
+    std::vector<hcc::SceneDesc> sd(num_scenes);
+    for (uint32_t s = 0; s < num_scenes; ++s) {
+        const hcc_bvh *b = bvhs[s];
+        hcc::SceneDesc &d = sd[s];
+        std::memset(&d, 0, sizeof d);
+        d.nodes = b->d_nodes;
+        d.tris = b->d_tris;
+        d.prim_rec = b->d_prim_rec;
+        d.root_ref = b->root_ref;
+        d.num_tris = b->num_tris;
+        const hcc_cut *c = cuts ? cuts[s] : nullptr;
+        d.cut = c ? c->d_boxes : nullptr;
+        d.used = c ? c->on_device : 0;
+        for (int a = 0; a < 3; ++a) {
+            d.lo[a] = b->lo[a];
+            d.ext[a] = b->hi[a] - b->lo[a];
+        }
+        d.L = 0.25f * std::max(d.ext[0], std::max(d.ext[1], d.ext[2]));
+    }
+    hcc_batch *bt = new (std::nothrow) hcc_batch;
+    if (!bt) return fail(ctx, HCC_ERR_OOM, "host allocation");
+    bt->device = ctx->device;
+    bt->layout = bvhs[0]->layout;
+    bt->num_scenes = num_scenes;
+    while ((1u << bt->scene_bits) < num_scenes) ++bt->scene_bits;
+    bt->offsets.assign(offsets, offsets + num_scenes + 1);
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaMalloc(&bt->d_scenes, sizeof(hcc::SceneDesc) * num_scenes);
+    if (e == cudaSuccess) e = cudaMalloc(&bt->d_offsets, sizeof(uint64_t) * (num_scenes + 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(bt->d_scenes, sd.data(), sizeof(hcc::SceneDesc) * num_scenes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(bt->d_offsets, offsets, sizeof(uint64_t) * (num_scenes + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        hcc_batch_destroy(bt);
+        return cuda_fail(ctx, e, "batch upload");
+    }
+    *out = bt;
+    return HCC_OK;
+}
+
+hcc_status hcc_batch_destroy(hcc_batch *b) {
+    if (!b) return HCC_ERR_INVALID_ARG;
+    {
+        DeviceGuard g(b->device);
+        if (b->d_scenes) cudaFree(b->d_scenes);
+        if (b->d_offsets) cudaFree(b->d_offsets);
+    }
+    delete b;
+    return HCC_OK;
+}
+
+hcc_status hcc_batch_run(hcc_ctx *ctx, const hcc_batch *b, hcc_method method, const hcc_rays *rays, uint32_t key_bits,
+                         int any_hit, hcc_hit *hits) {
+    if (!ctx || !b) return HCC_ERR_INVALID_ARG;
+    hcc_status st = check_rays(ctx, rays, "rays");
+    if (st != HCC_OK) return st;
+    const uint64_t n = b->offsets[b->num_scenes];
+    if (rays->n != n) return fail(ctx, HCC_ERR_INVALID_ARG, "rays->n must equal the batch's last offset");
+    if (method != HCC_METHOD_NOSORT && method != HCC_METHOD_HCC && method != HCC_METHOD_TWOPOINT &&
+        method != HCC_METHOD_ORIGIN && method != HCC_METHOD_ORIGIN_DIR)
+        return fail(ctx, HCC_ERR_INVALID_ARG, "unknown method");
+    if (n == 0) return HCC_OK;
+    if (!hits || !aligned(hits, 16)) return fail(ctx, HCC_ERR_INVALID_ARG, "hits NULL or not 16-byte aligned");
+    const uint32_t total_bits = key_bits + b->scene_bits;
+    if (method != HCC_METHOD_NOSORT && (key_bits < 1 || total_bits > 64))
+        return fail(ctx, HCC_ERR_INVALID_ARG, "key_bits plus %u scene bits must fit 64 bits", b->scene_bits);
+    DeviceGuard g(ctx->device);
+    TraceArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.layout = b->layout;
+    a.org = reinterpret_cast<const float4 *>(rays->org_tmin);
+    a.dir = reinterpret_cast<const float4 *>(rays->dir_tmax);
+    a.n = n;
+    a.hits = reinterpret_cast<int4 *>(hits);
+    a.err = ctx->d_err;
+    a.scenes = b->d_scenes;
+    a.offsets = b->d_offsets;
+    a.num_scenes = b->num_scenes;
+    cudaError_t e;
+    if (method != HCC_METHOD_NOSORT) {
+        const size_t ksz = total_bits > 32 ? 8 : 4;
+        if ((st = ensure(ctx, ctx->keys, n * ksz, "keys")) != HCC_OK) return st;
+        if ((st = ensure(ctx, ctx->perm, n * 4, "perm")) != HCC_OK) return st;
+        e = launch_encode_multi(ctx->stream, (int)method, a.org, a.dir, n, b->d_scenes, b->d_offsets, b->num_scenes,
+                                key_bits, total_bits, ctx->keys.p);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "batch encode launch");
+        uint32_t *perm = static_cast<uint32_t *>(ctx->perm.p);
+        if ((st = hcc_sort(ctx, ctx->keys.p, total_bits, n, perm)) != HCC_OK) return st;
+        a.gather = perm;
+        a.scatter = perm;
+    }
+    e = launch_trace(ctx->stream, a, any_hit);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch trace launch");
+    return HCC_OK;
+}
+
+hcc_status hcc_batch_spawn(hcc_ctx *ctx, const hcc_batch *b, const hcc_rays *in, const hcc_hit *hits, uint64_t seed,
+                           float tmin, const hcc_rays *out) {
+    if (!ctx || !b) return HCC_ERR_INVALID_ARG;
+    hcc_status st;
+    if ((st = check_rays(ctx, in, "in")) != HCC_OK) return st;
+    if ((st = check_rays(ctx, out, "out")) != HCC_OK) return st;
+    const uint64_t n = b->offsets[b->num_scenes];
+    if (in->n != n || out->n != n) return fail(ctx, HCC_ERR_INVALID_ARG, "ray counts must equal the batch's");
+    if (n == 0) return HCC_OK;
+    if (!hits || !aligned(hits, 16)) return fail(ctx, HCC_ERR_INVALID_ARG, "hits NULL or misaligned");
+    if (in->org_tmin == out->org_tmin || in->dir_tmax == out->dir_tmax)
+        return fail(ctx, HCC_ERR_INVALID_ARG, "in and out must be different buffers");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = launch_spawn(ctx->stream, reinterpret_cast<const float4 *>(in->org_tmin),
+                                 reinterpret_cast<const float4 *>(in->dir_tmax), reinterpret_cast<const int4 *>(hits),
+                                 n, b->d_scenes, b->d_offsets, b->num_scenes, seed, tmin,
+                                 reinterpret_cast<float4 *>(out->org_tmin), reinterpret_cast<float4 *>(out->dir_tmax),
+                                 ctx->d_err);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "spawn launch");
+    return HCC_OK;
+}
+
+// --------------------------------------------------------- graph capture
+
+hcc_status hcc_graph_capture_batch(hcc_ctx *ctx, const hcc_batch *b, hcc_method method, const hcc_rays *rays,
+                                   uint32_t key_bits, int any_hit, hcc_hit *hits, hcc_graph **out) {
+    if (!ctx || !b || !out) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (!ctx->stream) return fail(ctx, HCC_ERR_INVALID_ARG, "graph capture needs a non-default stream");
+    // everything the bounce needs must exist before capture: no allocation inside it
+    const uint64_t n = b->offsets[b->num_scenes];
+    if (method != HCC_METHOD_NOSORT) {
+        const uint32_t total_bits = key_bits + b->scene_bits;
+        if (key_bits < 1 || total_bits > 64) return fail(ctx, HCC_ERR_INVALID_ARG, "key bits do not fit");
+        hcc_status st = hcc_reserve(ctx, n, total_bits);
+        if (st != HCC_OK) return st;
+    }
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "begin capture");
+    hcc_status st = hcc_batch_run(ctx, b, method, rays, key_bits, any_hit, hits);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (st != HCC_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(ctx, e, "graph instantiate");
+    }
+    hcc_graph *gr = new (std::nothrow) hcc_graph;
+    if (!gr) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return fail(ctx, HCC_ERR_OOM, "host allocation");
+    }
+    gr->device = ctx->device;
+    gr->graph = graph;
+    gr->exec = exec;
+    *out = gr;
+    return HCC_OK;
+}
+
+hcc_status hcc_graph_launch(hcc_ctx *ctx, const hcc_graph *gr) {
+    if (!ctx || !gr) return HCC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaGraphLaunch(gr->exec, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+    return HCC_OK;
+}
+
+hcc_status hcc_graph_destroy(hcc_graph *gr) {
+    if (!gr) return HCC_ERR_INVALID_ARG;
+    {
+        DeviceGuard g(gr->device);
+        if (gr->exec) cudaGraphExecDestroy(gr->exec);
+        if (gr->graph) cudaGraphDestroy(gr->graph);
+    }
+    delete gr;
     return HCC_OK;
 }
 

@@ -37,6 +37,33 @@ constexpr uint32_t REF_TRI_MASK = 0x1FFFFFFFu;
 // Triangle record = three float4: (v0.xyz, id bits), (e1.xyz, 0), (e2.xyz, 0)
 // with e1 = v1 - v0, e2 = v2 - v0 rounded to float.
 
+// One scene of a batch of wavefronts (device table, read by the fused
+// multi-scene kernels): its BVH, its cut (HCC), its key normalisation box and
+// the rays [begin, end) of the batch that belong to it.
+struct SceneDesc {
+    const uint4 *nodes;
+    const float4 *tris;
+    const float4 *cut;  // (lo, hi) pairs in key order
+    const uint32_t *prim_rec;  // triangle id -> triangle record
+    uint32_t root_ref;
+    uint32_t used;      // cut nodes that drive key bits
+    float lo[3], ext[3], L;
+    uint32_t num_tris;
+};
+
+// Scene of ray src in a batch: the last s with offsets[s] <= src.
+__device__ __forceinline__ uint32_t scene_of(const uint64_t *__restrict__ offsets, uint32_t num_scenes, uint64_t src) {
+    uint32_t lo = 0, hi = num_scenes;  // offsets[lo] <= src < offsets[hi]
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(offsets + mid) <= src)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
 // ------------------------------------------------------------------ launchers
 // All return the launch error (cudaSuccess when queued).
 
@@ -51,6 +78,16 @@ cudaError_t launch_encode_origin(cudaStream_t s, const float4 *org, uint64_t n, 
 
 cudaError_t launch_encode_origin_dir(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n,
                                      const float lo[3], const float ext[3], uint32_t key_bits, void *keys);
+
+// Batch of scenes: key of ray i = (scene << key_bits) | its key in its scene.
+cudaError_t launch_encode_multi(cudaStream_t s, int method, const float4 *org, const float4 *dir, uint64_t n,
+                                const SceneDesc *scenes, const uint64_t *offsets, uint32_t num_scenes,
+                                uint32_t key_bits, uint32_t total_bits, void *keys);
+
+// Next bounce of a batch: diffuse rays from the hit points (see spawn.cu).
+cudaError_t launch_spawn(cudaStream_t s, const float4 *in_org, const float4 *in_dir, const int4 *hits, uint64_t n,
+                         const SceneDesc *scenes, const uint64_t *offsets, uint32_t num_scenes, uint64_t seed,
+                         float tmin, float4 *out_org, float4 *out_dir, uint32_t *err);
 
 // cnt[0] += key changes between consecutive sorted positions, cnt[1] += those
 // inside groups of 32 positions (cnt zeroed by the caller).
@@ -80,6 +117,9 @@ struct TraceArgs {
     uint32_t *err;
     unsigned long long *counts;  // diagnostic (NULL = off): node visits, triangle tests,
                                  // warp node steps, warp leaf steps
+    const SceneDesc *scenes;     // batch mode (NULL = single BVH above)
+    const uint64_t *offsets;     // scene s owns rays [offsets[s], offsets[s+1])
+    uint32_t num_scenes;
 };
 
 cudaError_t launch_trace(cudaStream_t s, const TraceArgs &a, int any_hit);

@@ -15,6 +15,8 @@
 //   k_ident  perm = identity when no pass is active (all keys equal, n <= 1)
 // Tiles take their position from an atomic counter in launch order, so a tile
 // only ever waits for tiles that are already running.
+#include <atomic>
+
 #include "hcc_internal.cuh"
 
 namespace hcc {
@@ -426,8 +428,14 @@ cudaError_t run_sort(cudaStream_t s, const K *keys, uint32_t key_bits, uint64_t 
     a.num_tiles = tiles;
     a.err = err;
     const size_t dyn = (sizeof(K) + sizeof(uint32_t)) * SORT_TILE;
-    e = cudaFuncSetAttribute(k_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    if (e != cudaSuccess) return e;
+    // the shared-memory opt-in is set once per device (so that a sort can be
+    // captured in a CUDA graph without any non-stream call)
+    static std::atomic<uint64_t> opted{0};
+    if (dev >= 0 && dev < 64 && !(opted.load() & (1ull << dev))) {
+        e = cudaFuncSetAttribute(k_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+        opted.fetch_or(1ull << dev);
+    }
     for (int p = 0; p < passes; ++p) k_pass<K><<<tiles, SORT_BLOCK, dyn, s>>>(a, p);
     uint64_t iblocks = (n + 255) / 256;
     if (iblocks > 4096) iblocks = 4096;

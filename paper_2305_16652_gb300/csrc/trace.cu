@@ -132,28 +132,23 @@ __device__ __forceinline__ void fetch_exact(const uint4 *nodes, uint32_t ref, Ch
     c.ref1 = n3.y;
 }
 
+// Diagnostic counters of one ray (the COUNT variants only).
+struct Counters {
+    uint32_t nodes = 0, tris = 0, warp_nodes = 0, warp_leaves = 0;
+};
+
 // Traversal loop ("while-while" with postponed leaves, Aila & Laine 2009):
 // a lane that reaches a leaf parks it and keeps descending until every lane
 // of the warp holds a leaf, so triangle tests run with full warps; the
 // nearer child is visited first and the farther one is pushed with its
 // entry distance, which lets a pop skip subtrees beyond the best hit.
-// COUNT = true is a diagnostic variant that also adds up internal-node
-// visits and triangle tests into a.counts[0..1] (never the timed kernel).
+// Returns the hit record {prim, t, u, v} (prim -1 and t = +inf on a miss);
+// sets overflow if the ray needed more than STACK entries.
 template <bool ANY, bool COUNT, int LAYOUT>
-__global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
-    const uint64_t i = (uint64_t)blockIdx.x * TRACE_BLOCK + threadIdx.x;
-    uint32_t n_nodes = 0, n_tris = 0, w_nodes = 0, w_leaves = 0;
+__device__ __forceinline__ int4 trace_ray(const uint4 *__restrict__ nodes, const float4 *__restrict__ tris,
+                                          uint32_t root_ref, const float4 o4, const float4 d4, Counters &cn,
+                                          bool &overflow) {
     const uint32_t lane = threadIdx.x & 31;
-    if (i >= a.n) return;
-    uint64_t src = i;
-    if (a.gather) {
-        src = a.gather[i];
-        if (src >= a.n) {  // invalid permutation entry: report, never read out of bounds
-            atomicOr(a.err, ERR_INDEX);
-            return;
-        }
-    }
-    const float4 o4 = __ldcs(a.org + src), d4 = __ldcs(a.dir + src);
     Ray r;
     r.ox = o4.x;
     r.oy = o4.y;
@@ -173,7 +168,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
     uint32_t st_ref[STACK];
     float st_t[STACK];
     int sp = 0;
-    bool overflow = false;
+    overflow = false;
     // next pending subtree that can still hold a closer hit, or REF_NONE
     auto pop = [&]() -> uint32_t {
         while (sp > 0) {
@@ -182,7 +177,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
         }
         return REF_NONE;
     };
-    uint32_t node = a.root_ref, leaf = REF_NONE;
+    uint32_t node = root_ref, leaf = REF_NONE;
     if (node & REF_LEAF) {
         leaf = node;
         node = REF_NONE;
@@ -192,12 +187,12 @@ __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
         while (node != REF_NONE && !(node & REF_LEAF)) {
             ChildBoxes c;
             if (LAYOUT == 0)
-                fetch_quant8(a.nodes, node, c);
+                fetch_quant8(nodes, node, c);
             else
-                fetch_exact(a.nodes, node, c);
+                fetch_exact(nodes, node, c);
             if (COUNT) {
-                ++n_nodes;  // this lane's node visit; the lowest active lane counts the warp's step
-                if (lane == (uint32_t)(__ffs(__activemask()) - 1)) ++w_nodes;
+                ++cn.nodes;  // this lane's node visit; the lowest active lane counts the warp's step
+                if (lane == (uint32_t)(__ffs(__activemask()) - 1)) ++cn.warp_nodes;
             }
             float tn0, tf0, tn1, tf1;
             slab(r, c.lo0x, c.lo0y, c.lo0z, c.hi0x, c.hi0y, c.hi0z, tcap, tn0, tf0);
@@ -229,13 +224,13 @@ __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
         }
         // leaves: the parked one, then any leaf that is next on the stack
         while (leaf != REF_NONE) {
-            if (COUNT && lane == (uint32_t)(__ffs(__activemask()) - 1)) ++w_leaves;
+            if (COUNT && lane == (uint32_t)(__ffs(__activemask()) - 1)) ++cn.warp_leaves;
             const uint32_t first = leaf & REF_TRI_MASK, cnt = ((leaf >> 29) & 3u) + 1u;
             bool hit_any = false;
             for (uint32_t k = 0; k < cnt; ++k) {
-                const float4 *rec = a.tris + 3 * (size_t)(first + k);
+                const float4 *rec = tris + 3 * (size_t)(first + k);
                 const float4 A = __ldg(rec), E1 = __ldg(rec + 1), E2 = __ldg(rec + 2);
-                if (COUNT) ++n_tris;
+                if (COUNT) ++cn.tris;
                 float t, u, v;
                 if (!intersect(r, A, E1, E2, t, u, v)) continue;
                 const int32_t prim = __float_as_int(A.w);
@@ -260,25 +255,55 @@ __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
             }
         }
     }
-    if (overflow) {
-        atomicOr(a.err, ERR_STACK);
-        best_prim = -1;
-    }
+    if (overflow) best_prim = -1;
     int4 out;
     out.x = best_prim;
     out.y = __float_as_int(best_prim < 0 ? __int_as_float(0x7F800000) : best_t);
     out.z = __float_as_int(best_prim < 0 ? 0.0f : best_u);
     out.w = __float_as_int(best_prim < 0 ? 0.0f : best_v);
+    return out;
+}
+
+// One thread per ray slot i: the ray is org/dir[gather[i]] (or i), its record
+// goes to hits[scatter[i]] (or i).  MULTI: the ray's BVH is that of its scene
+// in a batch (a.scenes, ray ranges a.offsets).  COUNT = true is a diagnostic
+// variant that also adds up work counters into a.counts (never timed).
+template <bool ANY, bool COUNT, int LAYOUT, bool MULTI>
+__global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
+    const uint64_t i = (uint64_t)blockIdx.x * TRACE_BLOCK + threadIdx.x;
+    if (i >= a.n) return;
+    uint64_t src = i;
+    if (a.gather) {
+        src = a.gather[i];
+        if (src >= a.n) {  // invalid permutation entry: report, never read out of bounds
+            atomicOr(a.err, ERR_INDEX);
+            return;
+        }
+    }
+    const float4 o4 = __ldcs(a.org + src), d4 = __ldcs(a.dir + src);
+    const uint4 *nodes = a.nodes;
+    const float4 *tris = a.tris;
+    uint32_t root = a.root_ref;
+    if (MULTI) {
+        const SceneDesc &sc = a.scenes[scene_of(a.offsets, a.num_scenes, src)];
+        nodes = sc.nodes;
+        tris = sc.tris;
+        root = sc.root_ref;
+    }
+    Counters cn;
+    bool overflow;
+    const int4 out = trace_ray<ANY, COUNT, LAYOUT>(nodes, tris, root, o4, d4, cn, overflow);
+    if (overflow) atomicOr(a.err, ERR_STACK);
     const uint64_t dst = a.scatter ? (uint64_t)a.scatter[i] : i;
     if (dst < a.n)
-        a.hits[dst] = out;
+        __stcs(a.hits + dst, out);
     else  // invalid scatter entry: report, never write out of bounds
         atomicOr(a.err, ERR_INDEX);
     if (COUNT) {
-        atomicAdd(a.counts, (unsigned long long)n_nodes);
-        atomicAdd(a.counts + 1, (unsigned long long)n_tris);
-        if (w_nodes) atomicAdd(a.counts + 2, (unsigned long long)w_nodes);
-        if (w_leaves) atomicAdd(a.counts + 3, (unsigned long long)w_leaves);
+        atomicAdd(a.counts, (unsigned long long)cn.nodes);
+        atomicAdd(a.counts + 1, (unsigned long long)cn.tris);
+        if (cn.warp_nodes) atomicAdd(a.counts + 2, (unsigned long long)cn.warp_nodes);
+        if (cn.warp_leaves) atomicAdd(a.counts + 3, (unsigned long long)cn.warp_leaves);
     }
 }
 
@@ -287,13 +312,20 @@ __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
 cudaError_t launch_trace(cudaStream_t s, const TraceArgs &a, int any_hit) {
     if (a.n == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((a.n + TRACE_BLOCK - 1) / TRACE_BLOCK);
-    const bool count = a.counts != nullptr;
+    const bool count = a.counts != nullptr, multi = a.scenes != nullptr;
 #define HCC_TRACE_LAUNCH(ANY, CNT)                                                  \
     do {                                                                            \
-        if (a.layout == 0)                                                          \
-            k_trace<ANY, CNT, 0><<<blocks, TRACE_BLOCK, 0, s>>>(a);                 \
-        else                                                                        \
-            k_trace<ANY, CNT, 1><<<blocks, TRACE_BLOCK, 0, s>>>(a);                 \
+        if (multi) {                                                                \
+            if (a.layout == 0)                                                      \
+                k_trace<ANY, CNT, 0, true><<<blocks, TRACE_BLOCK, 0, s>>>(a);       \
+            else                                                                    \
+                k_trace<ANY, CNT, 1, true><<<blocks, TRACE_BLOCK, 0, s>>>(a);       \
+        } else {                                                                    \
+            if (a.layout == 0)                                                      \
+                k_trace<ANY, CNT, 0, false><<<blocks, TRACE_BLOCK, 0, s>>>(a);      \
+            else                                                                    \
+                k_trace<ANY, CNT, 1, false><<<blocks, TRACE_BLOCK, 0, s>>>(a);      \
+        }                                                                           \
     } while (0)
     if (any_hit && count)
         HCC_TRACE_LAUNCH(true, true);

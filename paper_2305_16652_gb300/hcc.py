@@ -83,6 +83,13 @@ def load(path: str = LIB_PATH):
         "hcc_key_stats": [P, P, u32, P, u64, P, P],
         "hcc_trace_sorted": [P, P, ctypes.POINTER(_Rays), P, i32, P],
         "hcc_sort_noalloc": [P, u32, u64, P, P, P],
+        "hcc_batch_create": [P, u32, P, P, P, PP],
+        "hcc_batch_destroy": [P],
+        "hcc_batch_run": [P, P, i32, ctypes.POINTER(_Rays), u32, i32, P],
+        "hcc_batch_spawn": [P, P, ctypes.POINTER(_Rays), P, u64, ctypes.c_float, ctypes.POINTER(_Rays)],
+        "hcc_graph_capture_batch": [P, P, i32, ctypes.POINTER(_Rays), u32, i32, P, PP],
+        "hcc_graph_launch": [P, P],
+        "hcc_graph_destroy": [P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -175,6 +182,10 @@ def hcc_bvh_upload(ctx, bvh, layout=None):
     return h
 
 
+def hcc_bvh_upload_layout(ctx, bvh, layout):
+    return hcc_bvh_upload(ctx, bvh, layout=layout)
+
+
 def hcc_bvh_info(bvh):
     nn, nt, dep = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
     lo, hi = (ctypes.c_float * 3)(), (ctypes.c_float * 3)()
@@ -256,6 +267,53 @@ def hcc_key_stats(ctx, keys, key_bits: int, perm, n: int):
     _check(load().hcc_key_stats(ctx, _ptr(keys), key_bits, _ptr(perm), n, ctypes.byref(anc),
                                 ctypes.byref(distinct)), ctx)
     return {"anc": anc.value, "distinct": int(distinct.value)}
+
+
+# ------------------------------------------------------------------ batches
+
+def hcc_batch_create(ctx, bvhs, cuts, offsets):
+    """bvhs / cuts: lists of handles (cuts may be None or hold None); offsets: S + 1 ints."""
+    S = len(bvhs)
+    arr_b = (ctypes.c_void_p * S)(*[b.value if hasattr(b, "value") else b for b in bvhs])
+    arr_c = None
+    if cuts is not None:
+        arr_c = (ctypes.c_void_p * S)(*[(c.value if hasattr(c, "value") else c) if c is not None else None
+                                        for c in cuts])
+    off = np.ascontiguousarray(offsets, np.uint64)
+    h = ctypes.c_void_p()
+    _check(load().hcc_batch_create(ctx, S, arr_b, arr_c, _ptr(off), ctypes.byref(h)), ctx)
+    return h
+
+
+def hcc_batch_destroy(batch):
+    _check(load().hcc_batch_destroy(batch))
+
+
+def hcc_batch_run(ctx, batch, method, org, dir_, key_bits: int, hits, any_hit: bool = False):
+    r = _rays(org, dir_)
+    _check(load().hcc_batch_run(ctx, batch, METHODS.get(method, method), ctypes.byref(r), key_bits, int(any_hit),
+                                _ptr(hits)), ctx)
+
+
+def hcc_batch_spawn(ctx, batch, in_org, in_dir, hits, seed: int, tmin: float, out_org, out_dir):
+    ri, ro = _rays(in_org, in_dir), _rays(out_org, out_dir)
+    _check(load().hcc_batch_spawn(ctx, batch, ctypes.byref(ri), _ptr(hits), seed, tmin, ctypes.byref(ro)), ctx)
+
+
+def hcc_graph_capture_batch(ctx, batch, method, org, dir_, key_bits: int, hits, any_hit: bool = False):
+    r = _rays(org, dir_)
+    h = ctypes.c_void_p()
+    _check(load().hcc_graph_capture_batch(ctx, batch, METHODS.get(method, method), ctypes.byref(r), key_bits,
+                                          int(any_hit), _ptr(hits), ctypes.byref(h)), ctx)
+    return h
+
+
+def hcc_graph_launch(ctx, graph):
+    _check(load().hcc_graph_launch(ctx, graph), ctx)
+
+
+def hcc_graph_destroy(graph):
+    _check(load().hcc_graph_destroy(graph))
 
 
 def hcc_run(ctx, method, bvh, cut, org, dir_, key_bits: int, hits, any_hit: bool = False):

@@ -48,3 +48,11 @@ def test_product_path_never_touches_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", text, flags=re.M), f
                 assert "hcc_oracle" not in text and "libhcc_oracle" not in text, f
+
+
+def test_binding_declares_every_entry_point(lib):
+    """Every function of the header has an explicit ctypes signature in the binding."""
+    from paper_2305_16652_gb300 import hcc
+    for f in declared_functions():
+        assert getattr(lib, f).argtypes is not None or f in ("hcc_last_error", "hcc_status_string"), f
+        assert hasattr(hcc, f) or f in ("hcc_last_error", "hcc_status_string"), f
