@@ -491,6 +491,100 @@ def run_keylen_sweep(args):
     print(json.dumps(out), flush=True)
 
 
+def run_batch_sweep(args):
+    """Batched wavefronts: 16 rooms (seeds 2-17, 50k-2M triangles) with log-uniform
+    wavefronts of 64k-8M rays, two bounces, each bounce one captured CUDA graph
+    (fused multi-scene encode, one sort, one fused trace; bounce 2 starts with the
+    spawn kernel), autotuned per-scene cut size and shared key length."""
+    import torch
+    from paper_2305_16652_gb300 import build, gen, hcc, tune
+    build()
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    ws = gen.batch_workloads(scale=0.125 if args.quick else 1.0)
+    gen_s = time.perf_counter() - t0
+    S = len(ws)
+    stream = torch.cuda.Stream()
+    ctx = hcc.hcc_create(0, stream)
+    bvhs = [hcc.hcc_bvh_upload(ctx, w.bvh, layout=args.layout) for w in ws]
+    offsets = np.concatenate([[0], np.cumsum([w.rays.n for w in ws])]).astype(np.uint64)
+    n = int(offsets[-1])
+    with torch.cuda.stream(stream):
+        org1 = torch.from_numpy(np.concatenate([w.rays.org for w in ws])).to(dev)
+        dir1 = torch.from_numpy(np.concatenate([w.rays.dir for w in ws])).to(dev)
+        org2, dir2 = torch.empty_like(org1), torch.empty_like(dir1)
+        hits1 = torch.empty((n, 4), dtype=torch.int32, device=dev)
+        hits2 = torch.empty_like(hits1)
+    stream.synchronize()
+    per_scene = [(org1[int(offsets[s]):int(offsets[s + 1])], dir1[int(offsets[s]):int(offsets[s + 1])])
+                 for s in range(S)]
+    t0 = time.perf_counter()
+    tuned = tune.tune_batch(ctx, stream, bvhs, per_scene)
+    tune_s = time.perf_counter() - t0
+    cuts = [hcc.hcc_select_cut(ctx, b, C, 0.125) for b, C in zip(bvhs, tuned["cut_sizes"])]
+    batch = hcc.hcc_batch_create(ctx, bvhs, cuts, offsets)
+    hcc.hcc_reserve(ctx, n, 64)
+    results = {}
+    for name, method, k in (("nosort", "nosort", 32), ("twopoint", "twopoint", 30),
+                            ("hcc_tuned", "hcc", tuned["key_bits"]), ("hcc_32", "hcc", 32)):
+        if name == "hcc_32":
+            for c in cuts:
+                hcc.hcc_cut_destroy(c)
+            cuts = [hcc.hcc_select_cut(ctx, b, 32, 0.125) for b in bvhs]
+            hcc.hcc_batch_destroy(batch)
+            batch = hcc.hcc_batch_create(ctx, bvhs, cuts, offsets)
+        hcc.hcc_graph_begin(ctx)
+        hcc.hcc_batch_run(ctx, batch, method, org1, dir1, k, hits1)
+        g1 = hcc.hcc_graph_end(ctx)
+        hcc.hcc_graph_begin(ctx)
+        hcc.hcc_batch_spawn(ctx, batch, org1, dir1, hits1, 1234, 1e-4, org2, dir2)
+        hcc.hcc_batch_run(ctx, batch, method, org2, dir2, k, hits2)
+        g2 = hcc.hcc_graph_end(ctx)
+        times = {}
+        for label, g in (("bounce1", g1), ("bounce2_with_spawn", g2)):
+            for _ in range(args.warmup):
+                hcc.hcc_graph_launch(ctx, g)
+            hcc.hcc_sync(ctx)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+            for a, b in evs:
+                a.record(stream)
+                hcc.hcc_graph_launch(ctx, g)
+                b.record(stream)
+            hcc.hcc_sync(ctx)
+            times[label] = statistics.median([a.elapsed_time(b) for a, b in evs])
+        # the same bounce issued call by call (no graph), for the launch overhead
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+        for a, b in evs:
+            a.record(stream)
+            hcc.hcc_batch_run(ctx, batch, method, org1, dir1, k, hits1)
+            b.record(stream)
+        hcc.hcc_sync(ctx)
+        times["bounce1_eager"] = statistics.median([a.elapsed_time(b) for a, b in evs])
+        hcc.hcc_graph_destroy(g1)
+        hcc.hcc_graph_destroy(g2)
+        results[name] = {"key_bits": k, **{f"{kk}_ms": round(v, 4) for kk, v in times.items()},
+                         "bounce1_mrays_s": round(n / (times["bounce1"] * 1e3), 1),
+                         "two_bounces_mrays_s": round(2 * n / ((times["bounce1"] + times["bounce2_with_spawn"]) * 1e3),
+                                                      1)}
+    out = {"metric": "batched wavefronts: secondary Mrays/s over 2 bounces, one CUDA graph per bounce",
+           "unit": "Mrays/s",
+           "config": {"workload": f"{S} rooms (seeds 2-17), {sum(w.tris.shape[0] for w in ws)} triangles, "
+                                  f"{n} rays per bounce", "bvh_layout": args.layout,
+                      "scenes": [{"tris": int(w.tris.shape[0]), "rays": int(w.rays.n)} for w in ws]},
+           "autotune": {"key_bits": tuned["key_bits"], "cut_sizes": tuned["cut_sizes"],
+                        "totals_ms": {str(k): round(v, 3) for k, v in tuned["totals_ms"].items()},
+                        "seconds": round(tune_s, 1)},
+           "generation_s": round(gen_s, 1), "methods": results}
+    for c in cuts:
+        hcc.hcc_cut_destroy(c)
+    hcc.hcc_batch_destroy(batch)
+    for b in bvhs:
+        hcc.hcc_bvh_destroy(b)
+    hcc.hcc_destroy(ctx)
+    print(json.dumps(out), flush=True)
+
+
 def profile_case(name: str):
     """Small, fixed workloads for ncu captures (not a benchmark: nothing is timed).
 
@@ -543,12 +637,14 @@ def main(argv=None):
     ap.add_argument("--ref-sample", type=int, default=300_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", choices=["trace-small", "sort-16m"], help="run a small profiling case and exit")
-    ap.add_argument("--sweep", choices=["keylen"], help="run a study instead of the headline benchmark")
+    ap.add_argument("--sweep", choices=["keylen", "batch"], help="run a study instead of the headline benchmark")
     args = ap.parse_args(argv)
     if args.case:
         return profile_case(args.case)
     if args.sweep == "keylen":
         return run_keylen_sweep(args)
+    if args.sweep == "batch":
+        return run_batch_sweep(args)
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = dist_env()
     if world > 1:

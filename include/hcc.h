@@ -391,6 +391,12 @@ hcc_status hcc_batch_spawn(hcc_ctx *ctx, const hcc_batch *batch, const hcc_rays 
 typedef struct hcc_graph hcc_graph;
 hcc_status hcc_graph_capture_batch(hcc_ctx *ctx, const hcc_batch *batch, hcc_method method, const hcc_rays *rays,
                                    uint32_t key_bits, int any_hit, hcc_hit *hits, hcc_graph **out);
+/* General capture: every hcc call issued on ctx between hcc_graph_begin and
+ * hcc_graph_end is recorded (not run) into the graph.  Reserve scratch first
+ * (hcc_reserve): a call that would allocate fails inside a capture.  The
+ * context's stream must not be the legacy default stream. */
+hcc_status hcc_graph_begin(hcc_ctx *ctx);
+hcc_status hcc_graph_end(hcc_ctx *ctx, hcc_graph **out);
 hcc_status hcc_graph_launch(hcc_ctx *ctx, const hcc_graph *graph);
 hcc_status hcc_graph_destroy(hcc_graph *graph);
 

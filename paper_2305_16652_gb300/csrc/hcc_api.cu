@@ -982,6 +982,41 @@ hcc_status hcc_graph_capture_batch(hcc_ctx *ctx, const hcc_batch *b, hcc_method 
     return HCC_OK;
 }
 
+hcc_status hcc_graph_begin(hcc_ctx *ctx) {
+    if (!ctx) return HCC_ERR_INVALID_ARG;
+    if (!ctx->stream) return fail(ctx, HCC_ERR_INVALID_ARG, "graph capture needs a non-default stream");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "begin capture");
+    return HCC_OK;
+}
+
+hcc_status hcc_graph_end(hcc_ctx *ctx, hcc_graph **out) {
+    if (!ctx || !out) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    DeviceGuard g(ctx->device);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(ctx, e, "graph instantiate");
+    }
+    hcc_graph *gr = new (std::nothrow) hcc_graph;
+    if (!gr) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return fail(ctx, HCC_ERR_OOM, "host allocation");
+    }
+    gr->device = ctx->device;
+    gr->graph = graph;
+    gr->exec = exec;
+    *out = gr;
+    return HCC_OK;
+}
+
 hcc_status hcc_graph_launch(hcc_ctx *ctx, const hcc_graph *gr) {
     if (!ctx || !gr) return HCC_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);

@@ -199,6 +199,31 @@ def tiny_workload(seed: int = 0, ntris: int = 10_000, nrays: int = 4096) -> Work
 
 
 ROOM_LIGHTS = ((2.5, 2.95, 2.0), (7.5, 2.95, 2.0), (2.5, 2.95, 6.0), (7.5, 2.95, 6.0))
+P_BATCH_TRIS, P_BATCH_RAYS = 100, 101
+
+
+def _log_uniform(seed: int, purpose: int, lo: float, hi: float) -> int:
+    u = (rng_u64(seed, purpose, 0) >> 11) * (1.0 / 9007199254740992.0)
+    return int(round(float(np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo))))))
+
+
+def batch_workloads(seeds=range(2, 18), tris_range=(50_000, 2_000_000), rays_range=(65_536, 8_388_608),
+                    scale: float = 1.0):
+    """One furnished room per seed with a log-uniform triangle count and a
+    log-uniform wavefront size (8 spp, 16:9 image, every sample hits).
+    scale < 1 shrinks both ranges (quick runs)."""
+    out = []
+    for seed in seeds:
+        nt = max(2_000, int(_log_uniform(seed, P_BATCH_TRIS, *tris_range) * scale))
+        nr = max(1_024, int(_log_uniform(seed, P_BATCH_RAYS, *rays_range) * scale))
+        H = int(np.ceil(np.sqrt(nr / 8 * 9 / 16)))
+        W = int(np.ceil(H * 16 / 9))
+        tris = room_tris(seed, nt, clusters=40)
+        bvh = build_bvh(tris)
+        sec, _, prim = camera_rays(tris, (5.0, 1.6, 0.4), (5.0, 1.2, 8.0), 60.0, W, H, 8, seed, sample_major=False,
+                                   max_rays=nr)
+        out.append(Workload(f"room-seed{seed}-{tris.shape[0]}-tris-{sec.n}-rays", tris, bvh, sec, None, prim))
+    return out
 
 
 def room_workload(seed: int = 1, target_tris: int = 1_000_000, W: int = 1920, H: int = 1080, spp: int = 8,

@@ -90,6 +90,8 @@ def load(path: str = LIB_PATH):
         "hcc_graph_capture_batch": [P, P, i32, ctypes.POINTER(_Rays), u32, i32, P, PP],
         "hcc_graph_launch": [P, P],
         "hcc_graph_destroy": [P],
+        "hcc_graph_begin": [P],
+        "hcc_graph_end": [P, PP],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -305,6 +307,16 @@ def hcc_graph_capture_batch(ctx, batch, method, org, dir_, key_bits: int, hits, 
     h = ctypes.c_void_p()
     _check(load().hcc_graph_capture_batch(ctx, batch, METHODS.get(method, method), ctypes.byref(r), key_bits,
                                           int(any_hit), _ptr(hits), ctypes.byref(h)), ctx)
+    return h
+
+
+def hcc_graph_begin(ctx):
+    _check(load().hcc_graph_begin(ctx), ctx)
+
+
+def hcc_graph_end(ctx):
+    h = ctypes.c_void_p()
+    _check(load().hcc_graph_end(ctx, ctypes.byref(h)), ctx)
     return h
 
 
