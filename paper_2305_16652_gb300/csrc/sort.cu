@@ -15,6 +15,7 @@
 //   k_ident  perm = identity when no pass is active (all keys equal, n <= 1)
 // Tiles take their position from an atomic counter in launch order, so a tile
 // only ever waits for tiles that are already running.
+#include <algorithm>
 #include <atomic>
 
 #include "hcc_internal.cuh"
@@ -224,171 +225,231 @@ struct PassArgs {
     uint32_t *err;
 };
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Copy count elements of T from global src to shared dst with asynchronous
+// copies: 16-byte chunks when the whole tile is present and src is 16-byte
+// aligned, element by element otherwise.  Only elements below count are read.
+template <typename T>
+__device__ __forceinline__ void load_tile_async(T *dst, const T *src, uint32_t count) {
+    if (count == SORT_TILE && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+        constexpr uint32_t per = 16 / sizeof(T), chunks = SORT_TILE / per;
+        for (uint32_t c = threadIdx.x; c < chunks; c += SORT_BLOCK) cp_async16(dst + c * per, src + c * per);
+    } else {
+        for (uint32_t p = threadIdx.x; p < count; p += SORT_BLOCK) {
+            if (sizeof(T) == 8)
+                cp_async8(dst + p, src + p);
+            else
+                cp_async4(dst + p, src + p);
+        }
+    }
+}
+
+// One digit pass.  Persistent blocks (two per SM) take tiles of 4096 keys in
+// launch order from an atomic counter; while a tile is ranked and written,
+// the next tile's keys and values stream into the other shared-memory
+// buffer (cp.async), so the DRAM latency of a tile overlaps the work on the
+// previous one.  Per tile: warp-level stable ranking (ballot bit-split, the
+// group leader's atomic returns the group's base), the tile's digit counts
+// published at once to the decoupled look-back chain, the tile reordered by
+// digit in shared memory, the look-back for the global offsets (bounded
+// waits with back-off), and runs of equal digits written out coalesced.
+// A block handles its tiles in increasing order, so the lowest unfinished
+// tile is always being worked on and every wait ends.
 template <typename K>
-__global__ void __launch_bounds__(SORT_BLOCK, 4) k_pass(PassArgs<K> a, int pass) {
+__global__ void __launch_bounds__(SORT_BLOCK) k_pass(PassArgs<K> a, int pass) {
     const PassPlan pl = a.h->plan[pass];
     if (!pl.active) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    K *s_keys = reinterpret_cast<K *>(smem_raw);
-    uint32_t *s_vals = reinterpret_cast<uint32_t *>(smem_raw + sizeof(K) * SORT_TILE);
+    K *in_keys = reinterpret_cast<K *>(smem_raw);                                  // [2][TILE]
+    uint32_t *in_vals = reinterpret_cast<uint32_t *>(in_keys + 2 * SORT_TILE);     // [2][TILE]
+    K *out_keys = reinterpret_cast<K *>(in_vals + 2 * SORT_TILE);                  // [TILE]
+    uint32_t *out_vals = reinterpret_cast<uint32_t *>(out_keys + SORT_TILE);       // [TILE]
     __shared__ uint32_t s_whist[SORT_WARPS][RADIX];
     __shared__ uint32_t s_local[RADIX];
     __shared__ uint32_t s_base[RADIX];
     __shared__ uint32_t s_wsum[SORT_WARPS];
-    __shared__ uint32_t s_tile, s_abort;
+    __shared__ uint32_t s_next, s_abort;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        s_tile = atomicAdd(&a.h->tile_counter[pass], 1u);
-        s_abort = 0;
-    }
-    for (int i = tid; i < SORT_WARPS * RADIX; i += SORT_BLOCK) (&s_whist[0][0])[i] = 0;
-    __syncthreads();
-    const uint32_t tile = s_tile;
-    const uint64_t base = (uint64_t)tile * SORT_TILE;
     const uint32_t shift = 8u * (uint32_t)pass;
     const K mask = key_mask<K>(a.key_bits);
+    const uint32_t dbits = a.key_bits - shift < 8u ? a.key_bits - shift : 8u;
     const K *kin = pl.src_keys == KB_USER ? a.user_keys : (pl.src_keys == KB_A ? a.ka : a.kb);
     const uint32_t *vin = pl.src_vals == VB_A ? a.va : a.perm;
-
-    // Load: warp w owns the contiguous run [w*ITEMS*32, (w+1)*ITEMS*32) of the
-    // tile; item i of a lane sits at i*32 + lane, so each load is coalesced
-    // and the (item, lane) order is the input order within the warp.
-    K key[SORT_ITEMS];
-    uint32_t val[SORT_ITEMS], rank[SORT_ITEMS];
-    const uint32_t tile_n = (uint32_t)((a.n - base) < (uint64_t)SORT_TILE ? (a.n - base) : SORT_TILE);
-    const uint32_t wfirst = (uint32_t)warp * (SORT_ITEMS * 32) + lane;  // tile position of item 0
-#pragma unroll
-    for (int i = 0; i < SORT_ITEMS; ++i) {
-        const uint32_t pos = wfirst + (uint32_t)i * 32;
-        const bool valid = pos < tile_n;
-        const uint64_t idx = base + pos;
-        key[i] = valid ? (__ldcs(kin + idx) & mask) : (K)0;
-        val[i] = valid ? (pl.src_vals == VB_SYNTH ? (uint32_t)idx : __ldcs(vin + idx)) : 0u;
-    }
-    // Warp-level stable ranking: the lanes holding the same digit are found
-    // with one ballot per digit bit; the lowest of them adds their number to
-    // the warp's counter of that digit and the old value, broadcast to the
-    // group, is the rank of the group's first item.  The warp issues its
-    // atomics in item order, so ranks follow the input order (stable), and
-    // nothing waits between items.
-    const uint32_t lt = lanemask_lt();
-    const uint32_t dbits = a.key_bits - shift < 8u ? a.key_bits - shift : 8u;
-    uint32_t *wh = s_whist[warp];
-#pragma unroll
-    for (int i = 0; i < SORT_ITEMS; ++i) {
-        const bool valid = wfirst + (uint32_t)i * 32 < tile_n;
-        const uint32_t d = (uint32_t)(key[i] >> shift) & 255u;
-        const uint32_t peers = digit_peers(d, dbits, __ballot_sync(0xFFFFFFFFu, valid));
-        const uint32_t leader = __ffs(peers) - 1;
-        uint32_t prior = 0;
-        if (valid && (uint32_t)lane == leader) prior = atomicAdd(&wh[d], (uint32_t)__popc(peers));
-        prior = __shfl_sync(0xFFFFFFFFu, prior, valid ? leader : lane);
-        rank[i] = prior + __popc(peers & lt);
-    }
-    __syncthreads();
-
-    // Thread tid now owns digit tid: offsets of each warp within the tile.
-    uint32_t total = 0;
-#pragma unroll
-    for (int w = 0; w < SORT_WARPS; ++w) {
-        const uint32_t c = s_whist[w][tid];
-        s_whist[w][tid] = total;
-        total += c;
-    }
-    // Publish this tile's count of digit tid at once (tile 0 knows its prefix).
-    uint32_t *st = a.status + ((size_t)pass * a.num_tiles + tile) * RADIX;
-    if (tile == 0)
-        st_relaxed(st + tid, ST_INC | ((a.h->start[pass][tid] + total) & ST_VALUE));
-    else
-        st_relaxed(st + tid, ST_AGG | total);
-    // Exclusive scan of the tile's digit counts (positions in shared memory).
-    uint32_t incl = total;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, off);
-        if (lane >= off) incl += v;
-    }
-    if (lane == 31) s_wsum[warp] = incl;
-    __syncthreads();
-    uint32_t wpre = 0;
-    for (int w = 0; w < warp; ++w) wpre += s_wsum[w];
-    s_local[tid] = wpre + incl - total;
-    __syncthreads();
-    // Reorder the tile by digit in shared memory (stable) while the
-    // predecessors finish; this needs no global offsets yet.
-#pragma unroll
-    for (int i = 0; i < SORT_ITEMS; ++i) {
-        if (wfirst + (uint32_t)i * 32 < tile_n) {
-            const uint32_t d = (uint32_t)(key[i] >> shift) & 255u;
-            const uint32_t pos = s_local[d] + wh[d] + rank[i];
-            s_keys[pos] = key[i];
-            s_vals[pos] = val[i];
-        }
-    }
-    // Decoupled look-back for digit tid: read LOOKBACK predecessors per round
-    // (independent loads), consume them newest first until an inclusive
-    // prefix is found; back off with a short sleep while one is not ready.
-    uint32_t excl;
-    if (tile == 0) {
-        excl = a.h->start[pass][tid];
-    } else {
-        excl = 0;
-        int64_t j = (int64_t)tile - 1;
-        uint32_t spins = 0;
-        bool timed_out = false, done = false;
-        const uint32_t *col = a.status + (size_t)pass * a.num_tiles * RADIX + tid;
-        while (!done) {
-            uint32_t sv[LOOKBACK];
-#pragma unroll
-            for (int w = 0; w < LOOKBACK; ++w)
-                sv[w] = (j - w >= 0) ? ld_relaxed(col + (size_t)(j - w) * RADIX) : ST_INC;
-            int used = 0;
-            bool stalled = false;
-#pragma unroll
-            for (int w = 0; w < LOOKBACK; ++w) {
-                if (done || stalled) continue;
-                const uint32_t flag = sv[w] & ~ST_VALUE;
-                if (flag == 0) {
-                    stalled = true;
-                    continue;
-                }
-                if (j - w >= 0) excl += sv[w] & ST_VALUE;
-                ++used;
-                if (flag == ST_INC) done = true;
-            }
-            j -= used;
-            if (done) break;
-            if (stalled) {
-                if (++spins > SPIN_LIMIT / LOOKBACK || ((spins & 63u) == 0 && ld_relaxed(&a.h->abort))) {
-                    timed_out = true;
-                    break;
-                }
-                __nanosleep(spins < 8 ? 32u * spins : 256u);
-            }
-        }
-        if (timed_out) {
-            atomicOr(a.err, ERR_TIMEOUT);
-            atomicExch(&a.h->abort, 1u);
-            s_abort = 1;
-        }
-        st_relaxed(st + tid, ST_INC | ((excl + total) & ST_VALUE));
-    }
-    s_base[tid] = excl;
-    __syncthreads();
-    if (s_abort) return;
-
-    // Write runs of equal digits to their global positions.
+    const bool synth = pl.src_vals == VB_SYNTH;
     K *kout = pl.dst_keys == KB_A ? a.ka : (pl.dst_keys == KB_B ? a.kb : nullptr);
     uint32_t *vout = pl.dst_vals == VB_A ? a.va : a.perm;
-#pragma unroll 4
-    for (uint32_t p = tid; p < tile_n; p += SORT_BLOCK) {
-        const K k = s_keys[p];
-        const uint32_t d = (uint32_t)(k >> shift) & 255u;
-        const uint32_t g = s_base[d] + (p - s_local[d]);
-        if (kout) __stcs(kout + g, k);
-        __stcs(vout + g, s_vals[p]);
+    const uint32_t lt = lanemask_lt();
+    const uint32_t wfirst = (uint32_t)warp * (SORT_ITEMS * 32) + lane;  // tile position of this lane's item 0
+
+    auto tile_count = [&](uint32_t t) -> uint32_t {
+        const uint64_t b = (uint64_t)t * SORT_TILE;
+        return (uint32_t)((a.n - b) < (uint64_t)SORT_TILE ? (a.n - b) : SORT_TILE);
+    };
+    auto issue = [&](uint32_t t, int buf) {
+        if (t < a.num_tiles) {
+            const uint64_t b = (uint64_t)t * SORT_TILE;
+            const uint32_t cnt = tile_count(t);
+            load_tile_async(in_keys + buf * SORT_TILE, kin + b, cnt);
+            if (!synth) load_tile_async(in_vals + buf * SORT_TILE, vin + b, cnt);
+        }
+        cp_async_commit();  // possibly empty group: keeps one group per tile
+    };
+
+    if (tid == 0) {
+        s_next = atomicAdd(&a.h->tile_counter[pass], 1u);
+        s_abort = 0;
     }
+    __syncthreads();
+    uint32_t cur = s_next;
+    int buf = 0;
+    issue(cur, buf);
+    while (cur < a.num_tiles) {
+        __syncthreads();  // everyone is done with the previous tile and has read s_next
+        if (tid == 0) s_next = atomicAdd(&a.h->tile_counter[pass], 1u);
+        for (int i = tid; i < SORT_WARPS * RADIX; i += SORT_BLOCK) (&s_whist[0][0])[i] = 0;
+        __syncthreads();
+        const uint32_t nxt = s_next;
+        issue(nxt, buf ^ 1);
+        cp_async_wait_prev();  // this thread's copies of the current tile have landed
+        __syncthreads();       // ... and everyone's
+
+        const uint32_t tile = cur;
+        const uint64_t base = (uint64_t)tile * SORT_TILE;
+        const uint32_t tile_n = tile_count(tile);
+        const K *tk = in_keys + buf * SORT_TILE;
+        const uint32_t *tv = in_vals + buf * SORT_TILE;
+
+        // warp-level stable ranking
+        uint32_t rank[SORT_ITEMS];
+        uint32_t *wh = s_whist[warp];
+#pragma unroll
+        for (int i = 0; i < SORT_ITEMS; ++i) {
+            const uint32_t pos = wfirst + (uint32_t)i * 32;
+            const bool valid = pos < tile_n;
+            const uint32_t d = valid ? (uint32_t)((tk[pos] & mask) >> shift) & 255u : 0u;
+            const uint32_t peers = digit_peers(d, dbits, __ballot_sync(0xFFFFFFFFu, valid));
+            const uint32_t leader = __ffs(peers) - 1;
+            uint32_t prior = 0;
+            if (valid && (uint32_t)lane == leader) prior = atomicAdd(&wh[d], (uint32_t)__popc(peers));
+            prior = __shfl_sync(0xFFFFFFFFu, prior, valid ? leader : lane);
+            rank[i] = prior + __popc(peers & lt);
+        }
+        __syncthreads();
+        // thread tid owns digit tid: warp offsets, tile count, publication
+        uint32_t total = 0;
+#pragma unroll
+        for (int w = 0; w < SORT_WARPS; ++w) {
+            const uint32_t c = s_whist[w][tid];
+            s_whist[w][tid] = total;
+            total += c;
+        }
+        uint32_t *st = a.status + ((size_t)pass * a.num_tiles + tile) * RADIX;
+        if (tile == 0)
+            st_relaxed(st + tid, ST_INC | ((a.h->start[pass][tid] + total) & ST_VALUE));
+        else
+            st_relaxed(st + tid, ST_AGG | total);
+        uint32_t incl = total;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        uint32_t wpre = 0;
+        for (int w = 0; w < warp; ++w) wpre += s_wsum[w];
+        s_local[tid] = wpre + incl - total;
+        __syncthreads();
+        // reorder the tile by digit in shared memory (stable)
+#pragma unroll
+        for (int i = 0; i < SORT_ITEMS; ++i) {
+            const uint32_t pos = wfirst + (uint32_t)i * 32;
+            if (pos < tile_n) {
+                const K k = tk[pos] & mask;
+                const uint32_t d = (uint32_t)(k >> shift) & 255u;
+                const uint32_t o = s_local[d] + wh[d] + rank[i];
+                out_keys[o] = k;
+                out_vals[o] = synth ? (uint32_t)(base + pos) : tv[pos];
+            }
+        }
+        // decoupled look-back for digit tid
+        uint32_t excl;
+        if (tile == 0) {
+            excl = a.h->start[pass][tid];
+        } else {
+            excl = 0;
+            int64_t j = (int64_t)tile - 1;
+            uint32_t spins = 0;
+            bool timed_out = false, done = false;
+            const uint32_t *col = a.status + (size_t)pass * a.num_tiles * RADIX + tid;
+            while (!done) {
+                uint32_t sv[LOOKBACK];
+#pragma unroll
+                for (int w = 0; w < LOOKBACK; ++w)
+                    sv[w] = (j - w >= 0) ? ld_relaxed(col + (size_t)(j - w) * RADIX) : ST_INC;
+                int used = 0;
+                bool stalled = false;
+#pragma unroll
+                for (int w = 0; w < LOOKBACK; ++w) {
+                    if (done || stalled) continue;
+                    const uint32_t flag = sv[w] & ~ST_VALUE;
+                    if (flag == 0) {
+                        stalled = true;
+                        continue;
+                    }
+                    if (j - w >= 0) excl += sv[w] & ST_VALUE;
+                    ++used;
+                    if (flag == ST_INC) done = true;
+                }
+                j -= used;
+                if (done) break;
+                if (stalled) {
+                    if (++spins > SPIN_LIMIT / LOOKBACK || ((spins & 63u) == 0 && ld_relaxed(&a.h->abort))) {
+                        timed_out = true;
+                        break;
+                    }
+                    __nanosleep(spins < 8 ? 32u * spins : 256u);
+                }
+            }
+            if (timed_out) {
+                atomicOr(a.err, ERR_TIMEOUT);
+                atomicExch(&a.h->abort, 1u);
+                s_abort = 1;
+            }
+            st_relaxed(st + tid, ST_INC | ((excl + total) & ST_VALUE));
+        }
+        s_base[tid] = excl;
+        __syncthreads();
+        if (s_abort) break;
+        // runs of equal digits to their global positions
+#pragma unroll 4
+        for (uint32_t p = tid; p < tile_n; p += SORT_BLOCK) {
+            const K k = out_keys[p];
+            const uint32_t d = (uint32_t)(k >> shift) & 255u;
+            const uint32_t g = s_base[d] + (p - s_local[d]);
+            if (kout) __stcs(kout + g, k);
+            __stcs(vout + g, out_vals[p]);
+        }
+        cur = nxt;
+        buf ^= 1;
+    }
+    cp_async_wait_all();
 }
 
 __global__ void k_ident(const SortHeader *h, uint32_t *perm, uint64_t n) {
@@ -427,7 +488,7 @@ cudaError_t run_sort(cudaStream_t s, const K *keys, uint32_t key_bits, uint64_t 
     a.key_bits = key_bits;
     a.num_tiles = tiles;
     a.err = err;
-    const size_t dyn = (sizeof(K) + sizeof(uint32_t)) * SORT_TILE;
+    const size_t dyn = 3 * (sizeof(K) + sizeof(uint32_t)) * SORT_TILE;  // 2 input buffers + 1 staging
     // the shared-memory opt-in is set once per device (so that a sort can be
     // captured in a CUDA graph without any non-stream call)
     static std::atomic<uint64_t> opted{0};
@@ -436,7 +497,9 @@ cudaError_t run_sort(cudaStream_t s, const K *keys, uint32_t key_bits, uint64_t 
         if (e != cudaSuccess) return e;
         opted.fetch_or(1ull << dev);
     }
-    for (int p = 0; p < passes; ++p) k_pass<K><<<tiles, SORT_BLOCK, dyn, s>>>(a, p);
+    const uint32_t per_sm = sizeof(K) == 4 ? 2u : 1u;  // blocks that fit the shared memory
+    const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)(sms > 0 ? sms : 1) * per_sm);
+    for (int p = 0; p < passes; ++p) k_pass<K><<<grid, SORT_BLOCK, dyn, s>>>(a, p);
     uint64_t iblocks = (n + 255) / 256;
     if (iblocks > 4096) iblocks = 4096;
     k_ident<<<(unsigned)iblocks, 256, 0, s>>>(h, perm, n);
