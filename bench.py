@@ -585,6 +585,185 @@ def run_batch_sweep(args):
     print(json.dumps(out), flush=True)
 
 
+class _HitRing:
+    """Page-locked hit records handed out to in-flight requests in a ring.
+
+    A region is reused only after every request writing into it has finished:
+    take() first collects finished requests and then waits for any unfinished
+    one that overlaps the new region (counted as a stall)."""
+
+    def __init__(self, torch, size: int):
+        self.buf = torch.empty((size, 4), dtype=torch.int32).pin_memory()
+        self.size, self.head = size, 0
+        self.live = []  # [ticket, start, end, submit_time]
+        self.stalls = 0
+
+    def take(self, n: int, server, done):
+        from paper_2305_16652_gb300 import hcc
+        if self.head + n > self.size:
+            self.head = 0
+        a, b = self.head, self.head + n
+        self.collect(server, done)
+        keep = []
+        for item in self.live:
+            if item[1] < b and a < item[2]:
+                self.stalls += 1
+                done.append((item[3], hcc.hcc_server_wait(server, item[0]), item[2] - item[1]))
+            else:
+                keep.append(item)
+        self.live = keep
+        self.head = b
+        return a, self.buf[a:b]
+
+    def collect(self, server, done, block: bool = False):
+        from paper_2305_16652_gb300 import hcc
+        keep = []
+        for item in self.live:
+            if block or hcc.hcc_server_query(server, item[0]):
+                done.append((item[3], hcc.hcc_server_wait(server, item[0]), item[2] - item[1]))
+            else:
+                keep.append(item)
+        self.live = keep
+
+
+def _serve_run(server, ring, pools, reqs, count, rate=None, outstanding=None):
+    """Submit requests 0..count-1 of the stream: open loop with Poisson arrivals
+    at `rate` requests/s, or closed loop keeping `outstanding` requests queued.
+    Returns (completed Mrays/s over the makespan, latencies in ms, stats)."""
+    from paper_2305_16652_gb300 import hcc
+    done = []
+    ring.stalls = 0
+    t0 = time.perf_counter()
+    arrive = t0 + np.cumsum(reqs["gap"][:count]) / rate if rate else None
+    for i in range(count):
+        s, n, off = int(reqs["scene"][i]), int(reqs["n"][i]), int(reqs["offset"][i])
+        if rate:
+            polled = 0.0
+            while True:
+                now = time.perf_counter()
+                if now >= arrive[i]:
+                    break
+                if now - polled > 2e-4:  # collect finished requests without contending for the server's lock
+                    ring.collect(server, done)
+                    polled = now
+        else:
+            while len(ring.live) >= outstanding:
+                oldest = ring.live.pop(0)
+                done.append((oldest[3], hcc.hcc_server_wait(server, oldest[0]), oldest[2] - oldest[1]))
+        a, hits = ring.take(n, server, done)
+        org, dir_ = pools[s]
+        t = time.perf_counter()
+        ticket = hcc.hcc_server_submit(server, s, org[off:off + n], dir_[off:off + n], hits)
+        ring.live.append([ticket, a, a + n, t])
+    ring.collect(server, done, block=True)
+    first = min(d[0] for d in done)
+    last = max(d[0] + d[1] / 1e3 for d in done)
+    rays = sum(d[2] for d in done)
+    lat = np.array([d[1] for d in done])
+    return rays / (last - first) / 1e6, lat, hcc.hcc_server_stats_get(server)
+
+
+def run_serve_sweep(args):
+    """Serving loop: Poisson arrivals of ray queries (64k-4M rays, log-uniform)
+    against 8 resident rooms of 0.2-4M triangles; per-request HCC encode, sort
+    and trace with host buffers; throughput and p50/p99 latency of the
+    continuous-admission server against the unbatched per-request path (one
+    request on the GPU at a time) at 25/50/90% of the server's saturation."""
+    import torch
+    from paper_2305_16652_gb300 import build, gen, hcc
+    build()
+    scale = 0.125 if args.quick else 1.0
+    t0 = time.perf_counter()
+    ws = gen.serve_scenes(scale=scale)
+    gen_s = time.perf_counter() - t0
+    rr = (65_536, 4_194_304) if not args.quick else (8_192, 524_288)
+    count = args.serve_requests
+    reqs = gen.serve_requests(1, count, [w.rays.n for w in ws], rays_range=rr)
+    ctx = hcc.hcc_create(0)
+    bvhs = [hcc.hcc_bvh_upload(ctx, w.bvh, layout=args.layout) for w in ws]
+    cuts = [hcc.hcc_select_cut(ctx, b, args.cut_size, 0.125) for b in bvhs]
+    pools = [(torch.from_numpy(w.rays.org).pin_memory(), torch.from_numpy(w.rays.dir).pin_memory()) for w in ws]
+    ring = _HitRing(torch, 64 << 20 if not args.quick else 8 << 20)
+    key_bits = args.key_bits
+
+    def server(slots):
+        srv = hcc.hcc_server_create(0, bvhs, cuts, slots=slots, method="hcc", key_bits=key_bits)
+        _serve_run(srv, ring, pools, reqs, min(24, count), outstanding=2 * slots)  # warm the pool
+        return srv
+
+    def summary(mrays, lat, st):
+        return {"mrays_s": round(mrays, 1), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                "p99_ms": round(float(np.percentile(lat, 99)), 3), "mean_ms": round(float(lat.mean()), 3),
+                "max_in_flight": st["max_in_flight"], "ring_stalls": ring.stalls}
+
+    out = {"metric": "serving: ray-query Mrays/s and p50/p99 latency under Poisson load, continuous admission "
+                     "vs the unbatched per-request path", "unit": "Mrays/s",
+           "config": {"workload": f"{len(ws)} rooms (seeds 30-37), {sum(w.tris.shape[0] for w in ws)} triangles; "
+                                  f"{count} requests of {rr[0]}-{rr[1]} rays (log-uniform, mean "
+                                  f"{int(reqs['n'].mean())}), host buffers (page-locked)",
+                      "scenes": [{"tris": int(w.tris.shape[0]), "ray_pool": int(w.rays.n)} for w in ws],
+                      "method": "hcc", "cut_size": args.cut_size, "key_bits": key_bits, "bvh_layout": args.layout,
+                      "slots": args.slots},
+           "generation_s": round(gen_s, 1)}
+    with ClockSampler(0) as clk:
+        # saturation: closed loop, 2 x slots requests outstanding
+        sweep = {}
+        sat = {}
+        for slots in sorted({1, 2, 3, 4, 6, 8, 16, args.slots}):
+            srv = server(slots)
+            try:
+                m, lat, st = _serve_run(srv, ring, pools, reqs, count, outstanding=max(2, 2 * slots))
+            finally:
+                hcc.hcc_server_destroy(srv)
+            sweep[str(slots)] = summary(m, lat, st)
+            sat[slots] = m
+        out["saturation_by_slots"] = sweep
+        mean_rays = float(reqs["n"][:count].mean())
+        sat_req_s = sat[args.slots] * 1e6 / mean_rays
+        out["saturation"] = {"continuous_mrays_s": round(sat[args.slots], 1), "unbatched_mrays_s": round(sat[1], 1),
+                             "continuous_req_s": round(sat_req_s, 1)}
+        loads = []
+        for load in (0.25, 0.5, 0.9):
+            row = {"load": load, "offered_req_s": round(load * sat_req_s, 1),
+                   "offered_mrays_s": round(load * sat[args.slots], 1)}
+            for name, slots in (("continuous", args.slots), ("unbatched", 1)):
+                srv = server(slots)
+                try:
+                    m, lat, st = _serve_run(srv, ring, pools, reqs, count, rate=load * sat_req_s)
+                finally:
+                    hcc.hcc_server_destroy(srv)
+                row[name] = summary(m, lat, st)
+            loads.append(row)
+        out["loads"] = loads
+    out["clocks"] = clk.summary()
+    # each result the same alone and in the mix (GPU vs GPU, full-size requests)
+    srv = hcc.hcc_server_create(0, bvhs, cuts, slots=args.slots, method="hcc", key_bits=key_bits)
+    k = min(12, count)
+    mix = [torch.empty((int(reqs["n"][i]), 4), dtype=torch.int32).pin_memory() for i in range(k)]
+    tickets = []
+    for i in range(k):
+        s, n, off = int(reqs["scene"][i]), int(reqs["n"][i]), int(reqs["offset"][i])
+        tickets.append(hcc.hcc_server_submit(srv, s, pools[s][0][off:off + n], pools[s][1][off:off + n], mix[i]))
+    for t in tickets:
+        hcc.hcc_server_wait(srv, t)
+    st = hcc.hcc_server_stats_get(srv)
+    hcc.hcc_server_destroy(srv)
+    same = True
+    for i in range(k):
+        s, n, off = int(reqs["scene"][i]), int(reqs["n"][i]), int(reqs["offset"][i])
+        alone = torch.empty((n, 4), dtype=torch.int32).pin_memory()
+        hcc.hcc_run_host(ctx, "hcc", bvhs[s], cuts[s], pools[s][0][off:off + n], pools[s][1][off:off + n],
+                         key_bits, alone)
+        same &= bool(torch.equal(alone, mix[i]))
+    out["mix_equals_alone"] = {"requests": k, "max_in_flight": st["max_in_flight"], "identical": same}
+    for c in cuts:
+        hcc.hcc_cut_destroy(c)
+    for b in bvhs:
+        hcc.hcc_bvh_destroy(b)
+    hcc.hcc_destroy(ctx)
+    print(json.dumps(out), flush=True)
+
+
 def profile_case(name: str):
     """Small, fixed workloads for ncu captures (not a benchmark: nothing is timed).
 
@@ -637,7 +816,10 @@ def main(argv=None):
     ap.add_argument("--ref-sample", type=int, default=300_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", choices=["trace-small", "sort-16m"], help="run a small profiling case and exit")
-    ap.add_argument("--sweep", choices=["keylen", "batch"], help="run a study instead of the headline benchmark")
+    ap.add_argument("--sweep", choices=["keylen", "batch", "serve"],
+                    help="run a study instead of the headline benchmark")
+    ap.add_argument("--slots", type=int, default=4, help="serving: requests on the GPU at once")
+    ap.add_argument("--serve-requests", type=int, default=1000, help="serving: requests per run")
     args = ap.parse_args(argv)
     if args.case:
         return profile_case(args.case)
@@ -645,6 +827,8 @@ def main(argv=None):
         return run_keylen_sweep(args)
     if args.sweep == "batch":
         return run_batch_sweep(args)
+    if args.sweep == "serve":
+        return run_serve_sweep(args)
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = dist_env()
     if world > 1:

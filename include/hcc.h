@@ -426,6 +426,96 @@ hcc_status hcc_run_host(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, con
                         const float *org_tmin, const float *dir_tmax, uint64_t n, uint32_t key_bits, int any_hit,
                         hcc_hit *hits);
 
+/* ------------------------------------------------------------ serving loop */
+
+/*
+ * A ray-query server over resident scenes.  The paper traces one wavefront
+ * at a time (Sec. 5) and has no serving layer; this loop runs the same
+ * per-request pipeline as hcc_run_host (encode against the scene's cut, sort,
+ * trace through the permutation) for many clients at once.
+ *
+ * Requests are admitted in arrival order by a dispatcher thread that the
+ * server owns, as soon as one of `slots` execution slots is free and the
+ * request's device memory fits the budget; each admitted request runs on its
+ * slot's own stream, so requests that arrive while others are on the GPU
+ * start at once and their kernels and copies overlap.  Request buffers come
+ * from a stream-ordered pool that keeps released memory, so steady-state
+ * requests allocate nothing from the driver.  slots = 1 is the unbatched
+ * per-request path: one request on the GPU at a time.
+ *
+ * A request's result does not depend on which requests share the GPU with
+ * it: its kernels read only its own buffers and the read-only scene data,
+ * and its hits equal hcc_run_host's for the same rays bit for bit.
+ *
+ * The BVH and cut handles given to hcc_server_create must stay alive until
+ * hcc_server_destroy.  Host ray and hit buffers should be page-locked:
+ * pageable buffers work, but their copies are staged synchronously and
+ * serialise the dispatcher.
+ */
+typedef struct hcc_server hcc_server;
+
+typedef struct hcc_server_config {
+    uint32_t slots;       /* requests on the GPU at once, 1..64 */
+    hcc_method method;    /* NOSORT, HCC, TWOPOINT, ORIGIN or ORIGIN_DIR */
+    uint32_t key_bits;    /* 1..64 (ignored for NOSORT) */
+    uint64_t hbm_budget;  /* device bytes for request buffers; 0 = 90% of free memory at creation */
+} hcc_server_config;
+
+typedef struct hcc_server_stats {
+    uint64_t completed;     /* requests finished with HCC_OK */
+    uint64_t failed;        /* requests finished with an error */
+    uint64_t rays;          /* rays of the completed requests */
+    uint32_t max_in_flight; /* most requests on the GPU at one time */
+    uint32_t queued;        /* requests waiting for admission now */
+    uint64_t budget;        /* the admission budget in bytes */
+    uint64_t peak_bytes;    /* most budget bytes held by admitted requests */
+} hcc_server_stats;
+
+/*
+ * Creates a server for num_scenes resident scenes (scene s = bvhs[s] and, for
+ * HCC, cuts[s]); all BVHs must share one node layout and live on `device`.
+ * Starts the dispatcher thread.  Errors: INVALID_ARG (bad config or handles),
+ * CUDA (streams, events, the memory pool), OOM (host).
+ */
+hcc_status hcc_server_create(int device, uint32_t num_scenes, const hcc_bvh *const *bvhs, const hcc_cut *const *cuts,
+                             const hcc_server_config *cfg, hcc_server **out);
+
+/*
+ * Queues a request of n rays (host float4 arrays org_tmin and dir_tmax, as
+ * hcc_rays) against scene `scene`; the n hit records go to host memory
+ * `hits`, valid once hcc_server_wait returns HCC_OK for *ticket.  The caller
+ * keeps the three buffers alive and unchanged until then.  Thread-safe.
+ * Errors: INVALID_ARG (scene index, NULL buffer, n = 0 or above
+ * HCC_MAX_SORT_N, server stopping), OOM (the request alone exceeds the
+ * budget; it would never be admitted).
+ */
+hcc_status hcc_server_submit(hcc_server *s, uint32_t scene, const float *org_tmin, const float *dir_tmax, uint64_t n,
+                             int any_hit, hcc_hit *hits, uint64_t *ticket);
+
+/* *done = 1 once the request has finished (successfully or not). */
+hcc_status hcc_server_query(hcc_server *s, uint64_t ticket, int *done);
+
+/*
+ * Blocks until the request finishes, releases its ticket and returns its
+ * status: OK, STACK_OVERFLOW (a ray's traversal needed more than
+ * HCC_TRACE_STACK entries; its record is incomplete), TIMEOUT (a bounded
+ * wait in the sort gave up), OOM (the pool could not grow), CUDA.  A failed
+ * request does not affect any other.  *latency_ms (may be NULL) = time from
+ * submission until the dispatcher saw the request's last copy complete.
+ * INVALID_ARG for an unknown ticket.
+ */
+hcc_status hcc_server_wait(hcc_server *s, uint64_t ticket, double *latency_ms);
+
+hcc_status hcc_server_stats_get(hcc_server *s, hcc_server_stats *out);
+
+/* *bytes = the device memory a request of n rays is charged against the
+ * budget (its ray, hit, key, permutation and sort-scratch buffers). */
+hcc_status hcc_server_request_bytes(const hcc_server *s, uint64_t n, uint64_t *bytes);
+
+/* Finishes every queued and running request, stops the thread, frees the
+ * server (tickets not yet waited for are dropped). */
+hcc_status hcc_server_destroy(hcc_server *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(CSRC, "_build")
 INCLUDE = os.path.join(REPO, "include")
 LIB = os.path.join(BUILD, "libhcc.so")
-SOURCES = ["hcc_api.cu", "encode.cu", "sort.cu", "gather.cu", "trace.cu", "spawn.cu", "sort_noalloc.cu"]
+SOURCES = ["hcc_api.cu", "encode.cu", "sort.cu", "gather.cu", "trace.cu", "spawn.cu", "sort_noalloc.cu", "serve.cu"]
 HEADERS = [os.path.join(CSRC, "hcc_internal.cuh"), os.path.join(INCLUDE, "hcc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC,-ffp-contract=off,-fno-fast-math",

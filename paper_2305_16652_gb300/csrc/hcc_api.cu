@@ -277,6 +277,33 @@ struct HadHeap {
 
 }  // namespace
 
+namespace hcc {
+
+// Device views of the handles for the serving loop (serve.cu).
+void bvh_view(const hcc_bvh *b, SceneDesc *out, int *layout, int *device) {
+    std::memset(out, 0, sizeof *out);
+    out->nodes = b->d_nodes;
+    out->tris = b->d_tris;
+    out->prim_rec = b->d_prim_rec;
+    out->root_ref = b->root_ref;
+    out->num_tris = b->num_tris;
+    for (int a = 0; a < 3; ++a) {
+        out->lo[a] = b->lo[a];
+        out->ext[a] = b->hi[a] - b->lo[a];
+    }
+    out->L = 0.25f * std::max(out->ext[0], std::max(out->ext[1], out->ext[2]));
+    *layout = b->layout;
+    *device = b->device;
+}
+
+void cut_view(const hcc_cut *c, const float4 **boxes, uint32_t *on_device, int *device) {
+    *boxes = c->d_boxes;
+    *on_device = c->on_device;
+    *device = c->device;
+}
+
+}  // namespace hcc
+
 // ================================================================== C ABI
 
 extern "C" {

@@ -200,10 +200,16 @@ def tiny_workload(seed: int = 0, ntris: int = 10_000, nrays: int = 4096) -> Work
 
 ROOM_LIGHTS = ((2.5, 2.95, 2.0), (7.5, 2.95, 2.0), (2.5, 2.95, 6.0), (7.5, 2.95, 6.0))
 P_BATCH_TRIS, P_BATCH_RAYS = 100, 101
+P_SERVE_SCENE, P_SERVE_SIZE, P_SERVE_OFFSET, P_SERVE_GAP = 102, 103, 104, 105
 
 
-def _log_uniform(seed: int, purpose: int, lo: float, hi: float) -> int:
-    u = (rng_u64(seed, purpose, 0) >> 11) * (1.0 / 9007199254740992.0)
+def _unit(seed: int, purpose: int, index: int) -> float:
+    """Uniform double in [0, 1) from the counter-based generator."""
+    return (rng_u64(seed, purpose, index) >> 11) * (1.0 / 9007199254740992.0)
+
+
+def _log_uniform(seed: int, purpose: int, lo: float, hi: float, index: int = 0) -> int:
+    u = _unit(seed, purpose, index)
     return int(round(float(np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo))))))
 
 
@@ -224,6 +230,43 @@ def batch_workloads(seeds=range(2, 18), tris_range=(50_000, 2_000_000), rays_ran
                                    max_rays=nr)
         out.append(Workload(f"room-seed{seed}-{tris.shape[0]}-tris-{sec.n}-rays", tris, bvh, sec, None, prim))
     return out
+
+
+def serve_scenes(seeds=range(30, 38), tris_range=(200_000, 4_000_000), W: int = 1920, H: int = 1080, spp: int = 2,
+                 scale: float = 1.0):
+    """Resident scenes of a ray-query server: one furnished room per seed with a
+    log-uniform triangle count and a pool of W x H x spp diffuse secondary rays
+    (pixel-major) from which requests take contiguous windows.  scale < 1
+    shrinks the triangle counts and the image (quick runs)."""
+    out = []
+    for seed in seeds:
+        nt = max(2_000, int(_log_uniform(seed, P_BATCH_TRIS, *tris_range) * scale))
+        w, h = max(16, int(W * np.sqrt(scale))), max(9, int(H * np.sqrt(scale)))
+        tris = room_tris(seed, nt, clusters=40)
+        bvh = build_bvh(tris)
+        sec, _, prim = camera_rays(tris, (5.0, 1.6, 0.4), (5.0, 1.2, 8.0), 60.0, w, h, spp, seed, sample_major=False)
+        out.append(Workload(f"room-seed{seed}-{tris.shape[0]}-tris-{sec.n}-ray-pool", tris, bvh, sec, None, prim))
+    return out
+
+
+def serve_requests(seed: int, count: int, pool_sizes, rays_range=(65_536, 4_194_304)):
+    """A request stream: request i goes to a uniformly drawn scene, asks for a
+    log-uniform number of rays in rays_range (capped by the scene's pool) taken
+    as a window at a uniform offset of the pool, and arrives a unit-mean
+    exponential gap after request i-1 (Poisson arrivals at rate 1; scale the
+    gaps by 1/rate).  Returns arrays scene, n, offset, gap."""
+    S = len(pool_sizes)
+    scene = np.empty(count, np.int64)
+    n = np.empty(count, np.int64)
+    off = np.empty(count, np.int64)
+    gap = np.empty(count, np.float64)
+    for i in range(count):
+        s = min(int(_unit(seed, P_SERVE_SCENE, i) * S), S - 1)
+        k = min(_log_uniform(seed, P_SERVE_SIZE, *rays_range, index=i), int(pool_sizes[s]))
+        scene[i], n[i] = s, k
+        off[i] = min(int(_unit(seed, P_SERVE_OFFSET, i) * (pool_sizes[s] - k + 1)), pool_sizes[s] - k)
+        gap[i] = -np.log1p(-_unit(seed, P_SERVE_GAP, i))
+    return {"scene": scene, "n": n, "offset": off, "gap": gap}
 
 
 def room_workload(seed: int = 1, target_tris: int = 1_000_000, W: int = 1920, H: int = 1080, spp: int = 8,

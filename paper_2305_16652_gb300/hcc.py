@@ -40,6 +40,17 @@ class _Rays(ctypes.Structure):
     _fields_ = [("org_tmin", ctypes.c_void_p), ("dir_tmax", ctypes.c_void_p), ("n", ctypes.c_uint64)]
 
 
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_uint32), ("method", ctypes.c_int), ("key_bits", ctypes.c_uint32),
+                ("hbm_budget", ctypes.c_uint64)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64), ("rays", ctypes.c_uint64),
+                ("max_in_flight", ctypes.c_uint32), ("queued", ctypes.c_uint32), ("budget", ctypes.c_uint64),
+                ("peak_bytes", ctypes.c_uint64)]
+
+
 class _BvhDesc(ctypes.Structure):
     _fields_ = [("num_nodes", ctypes.c_uint32), ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p),
                 ("left", ctypes.c_void_p), ("right", ctypes.c_void_p), ("first", ctypes.c_void_p),
@@ -92,6 +103,13 @@ def load(path: str = LIB_PATH):
         "hcc_graph_destroy": [P],
         "hcc_graph_begin": [P],
         "hcc_graph_end": [P, PP],
+        "hcc_server_create": [i32, u32, P, P, ctypes.POINTER(_ServerConfig), PP],
+        "hcc_server_submit": [P, u32, P, P, u64, i32, P, ctypes.POINTER(u64)],
+        "hcc_server_query": [P, u64, ctypes.POINTER(i32)],
+        "hcc_server_wait": [P, u64, ctypes.POINTER(f64)],
+        "hcc_server_stats_get": [P, ctypes.POINTER(_ServerStats)],
+        "hcc_server_destroy": [P],
+        "hcc_server_request_bytes": [P, u64, ctypes.POINTER(u64)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -340,6 +358,62 @@ def hcc_run_host(ctx, method, bvh, cut, org: np.ndarray, dir_: np.ndarray, key_b
     n = int(org.shape[0])
     _check(load().hcc_run_host(ctx, METHODS.get(method, method), bvh, cut, _ptr(org), _ptr(dir_), n, key_bits,
                                int(any_hit), _ptr(hits)), ctx)
+
+
+# ------------------------------------------------------------- serving loop
+
+def hcc_server_create(device: int, bvhs, cuts, slots: int, method="hcc", key_bits: int = 32,
+                      hbm_budget: int = 0):
+    """A ray-query server over resident scenes (bvhs[s], cuts[s] for HCC)."""
+    arr_b = (ctypes.c_void_p * len(bvhs))(*[b.value if isinstance(b, ctypes.c_void_p) else b for b in bvhs])
+    arr_c = None
+    if cuts is not None:
+        arr_c = (ctypes.c_void_p * len(cuts))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in cuts])
+    cfg = _ServerConfig(slots, METHODS.get(method, method), key_bits, hbm_budget)
+    h = ctypes.c_void_p()
+    _check(load().hcc_server_create(device, len(bvhs), arr_b, arr_c, ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def hcc_server_submit(server, scene: int, org, dir_, hits, any_hit: bool = False) -> int:
+    """Queue a request; org/dir/hits are host arrays (page-locked for overlap)
+    that must stay alive until hcc_server_wait returns."""
+    n = int(org.shape[0])
+    if dir_.shape[0] != n or hits.shape[0] != n:
+        raise ValueError("org_tmin, dir_tmax and hits differ in length")
+    t = ctypes.c_uint64()
+    _check(load().hcc_server_submit(server, scene, _ptr(org), _ptr(dir_), n, int(any_hit), _ptr(hits),
+                                    ctypes.byref(t)))
+    return t.value
+
+
+def hcc_server_query(server, ticket: int) -> bool:
+    d = ctypes.c_int()
+    _check(load().hcc_server_query(server, ticket, ctypes.byref(d)))
+    return bool(d.value)
+
+
+def hcc_server_wait(server, ticket: int) -> float:
+    """Wait for a request; returns its latency in ms, raises HccError if it failed."""
+    ms = ctypes.c_double()
+    _check(load().hcc_server_wait(server, ticket, ctypes.byref(ms)))
+    return ms.value
+
+
+def hcc_server_stats_get(server) -> dict:
+    st = _ServerStats()
+    _check(load().hcc_server_stats_get(server, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in _ServerStats._fields_}
+
+
+def hcc_server_request_bytes(server, n: int) -> int:
+    b = ctypes.c_uint64()
+    _check(load().hcc_server_request_bytes(server, n, ctypes.byref(b)))
+    return b.value
+
+
+def hcc_server_destroy(server):
+    _check(load().hcc_server_destroy(server))
 
 
 def hits_to_numpy(hits_tensor) -> np.ndarray:

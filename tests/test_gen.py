@@ -79,3 +79,19 @@ def test_room_workload_small_image():
     assert np.all(w.shadow.dir[:, 3] > 0) and np.all(np.isfinite(w.shadow.dir[:, 3]))
     o = w.rays.org[:, :3]
     assert np.all(o > -1e-3) and np.all(o[:, 0] < 10.001) and np.all(o[:, 1] < 3.001) and np.all(o[:, 2] < 8.001)
+
+
+def test_serve_request_stream():
+    pools = [4_147_200, 3_000_000, 500_000]
+    r = gen.serve_requests(1, 4000, pools)
+    assert np.all((r["n"] >= 65_536) & (r["n"] <= 4_194_304))
+    caps = np.array(pools)[r["scene"]]
+    assert np.all(r["n"] <= caps) and np.all(r["offset"] >= 0) and np.all(r["offset"] + r["n"] <= caps)
+    assert set(np.unique(r["scene"])) == {0, 1, 2}
+    # log-uniform sizes: log n uniform on [log 64k, log 4M] where the pool does not cap it
+    ln = np.log(r["n"][r["scene"] == 0])
+    assert abs(ln.mean() - (np.log(65_536) + np.log(4_194_304)) / 2) < 0.1
+    # Poisson arrivals at rate 1: exponential gaps with mean 1 and variance 1
+    assert abs(r["gap"].mean() - 1) < 0.06 and abs(r["gap"].var() - 1) < 0.15 and np.all(r["gap"] >= 0)
+    r2 = gen.serve_requests(1, 4000, pools)
+    assert all(np.array_equal(r[k], r2[k]) for k in r)
