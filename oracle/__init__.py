@@ -50,6 +50,14 @@ def _load():
     lib.oracle_encode_hcc.restype = None
     lib.oracle_key_margin.argtypes = [u64, P, P, u32, P, P, u32, P]
     lib.oracle_key_margin.restype = None
+    lib.oracle_select_cut_ml.argtypes = [u32, P, P, P, P, P, u32, u32, f64, P, P]
+    lib.oracle_select_cut_ml.restype = u32
+    lib.oracle_encode_mlhcc.argtypes = [u64, P, P, u32, u32, P, P, u32, P, P, u32, P]
+    lib.oracle_encode_mlhcc.restype = None
+    lib.oracle_grid_cells.argtypes = [P, P, u32, P, P, P]
+    lib.oracle_grid_cells.restype = u32
+    lib.oracle_encode_ppc.argtypes = [u64, P, P, u32, P, P, P, P, u32, P]
+    lib.oracle_encode_ppc.restype = None
     lib.oracle_encode_twopoint.argtypes = [u64, P, P, P, P, u32, P]
     lib.oracle_encode_twopoint.restype = None
     lib.oracle_encode_origin.argtypes = [u64, P, P, P, u32, P]
@@ -126,6 +134,53 @@ def key_margin(org, dir, cut_lo, cut_hi, key_bits: int) -> np.ndarray:
     out = np.zeros(n, np.float64)
     _load().oracle_key_margin(n, _p(org), _p(dir), cut_lo.shape[0], _p(cut_lo), _p(cut_hi), key_bits, _p(out))
     return out
+
+
+def select_cut_ml(bvh, top_size: int, low_size: int, lam: float = 0.125):
+    """Two-level MLHCC cut: (top ids in HAD order, low ids of shape (ntop, low_size))."""
+    lo, hi, left, right, count = _tree(bvh)
+    top = np.zeros(max(top_size, 1), np.int32)
+    low = np.zeros(max(top_size * low_size, 1), np.int32)
+    m = _load().oracle_select_cut_ml(lo.shape[0], _p(lo), _p(hi), _p(left), _p(right), _p(count), top_size,
+                                     low_size, lam, _p(top), _p(low))
+    return top[:m].copy(), low[:m * low_size].reshape(m, low_size).copy()
+
+
+def encode_mlhcc(org, dir, top_field: int, top_lo, top_hi, low_lo, low_hi, key_bits: int) -> np.ndarray:
+    """low_lo/low_hi: (ntop, low_field, 3) boxes of each top node's low cut."""
+    org, dir = _c(org, np.float32), _c(dir, np.float32)
+    top_lo, top_hi = _c(top_lo, np.float32).reshape(-1, 3), _c(top_hi, np.float32).reshape(-1, 3)
+    low_lo, low_hi = _c(low_lo, np.float32), _c(low_hi, np.float32)
+    ntop = top_lo.shape[0]
+    low_field = low_lo.shape[1] if low_lo.ndim == 3 else 0
+    n = org.shape[0]
+    keys = np.zeros(n, np.uint64)
+    _load().oracle_encode_mlhcc(n, _p(org), _p(dir), top_field, ntop, _p(top_lo), _p(top_hi), low_field,
+                                _p(low_lo), _p(low_hi), key_bits, _p(keys))
+    return keys
+
+
+def grid_cells(scene_lo, scene_hi, max_cells: int):
+    """Regular-grid cells: (lo (m, 3), hi (m, 3), dims (3,))."""
+    slo, shi = _c(scene_lo, np.float32), _c(scene_hi, np.float32)
+    cap = 1
+    while cap * 2 <= max(max_cells, 1):
+        cap *= 2
+    lo = np.zeros((cap, 3), np.float32)
+    hi = np.zeros((cap, 3), np.float32)
+    dims = np.zeros(3, np.uint32)
+    m = _load().oracle_grid_cells(_p(slo), _p(shi), max_cells, _p(lo), _p(hi), _p(dims))
+    return lo[:m].copy(), hi[:m].copy(), dims
+
+
+def encode_ppc(org, dir, bvh, key_bits: int) -> np.ndarray:
+    lo, hi, left, right, _ = _tree(bvh)
+    org, dir = _c(org, np.float32), _c(dir, np.float32)
+    n = org.shape[0]
+    keys = np.zeros(n, np.uint64)
+    _load().oracle_encode_ppc(n, _p(org), _p(dir), lo.shape[0], _p(lo), _p(hi), _p(left), _p(right), key_bits,
+                              _p(keys))
+    return keys
 
 
 def encode_twopoint(org, dir, scene_lo, scene_hi, key_bits: int) -> np.ndarray:

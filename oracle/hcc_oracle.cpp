@@ -17,6 +17,11 @@
 //   oracle_encode_hcc     hierarchy cut code, Algorithm 1 (Sec. 4.2.1); bit
 //                         order as in the worked example of the SpaceAnchor figure
 //   oracle_key_margin     distance of a ray from flipping any HCC bit
+//   oracle_select_cut_ml  two-level cut of the multi-level HCC, Algorithm 3 (Sec. 4.3)
+//   oracle_encode_mlhcc   multi-level hierarchy cut code (Sec. 4.3)
+//   oracle_grid_cells     regular grid encoding's cells (Sec. 5; encoded by
+//                         oracle_encode_hcc with the cells as the cut)
+//   oracle_encode_ppc     prefix path code (Sec. 4.1)
 //   oracle_encode_twopoint  TwoPoint key (Sec. 3.2 "Two Point", Sec. 5:
 //                         fixed-length termination estimate 0.25 x largest extent)
 //   oracle_encode_origin  Origin key: 3D Morton code of the ray origin (Sec. 3.2 "Origin")
@@ -254,6 +259,223 @@ void oracle_encode_twopoint(uint64_t n, const float *org, const float *dir, cons
         for (int j = (int)b - 1; j >= 0; --j)
             for (int c = 0; c < 6; ++c) key = (key << 1) | ((q[c] >> j) & 1u);
         if (key_bits > 6 * b) key <<= (key_bits - 6 * b);
+        keys[i] = key;
+    }
+}
+
+// ------------------------------------------------ method variants (Sec. 4.1, 4.3, 5)
+
+// Number of leaves under node n.
+static uint32_t leaves_under(int32_t n, const int32_t *left, const int32_t *right) {
+    if (left[n] < 0) return 1;
+    return leaves_under(left[n], left, right) + leaves_under(right[n], left, right);
+}
+
+// Algorithm 2 run on the subtree of `start` (the low-level cut of one top
+// node of MLHCC): the same queue discipline as oracle_select_cut, result in
+// HAD order.
+static std::vector<int32_t> cut_of_subtree(int32_t start, uint32_t size, const std::vector<double> &had,
+                                           const int32_t *left, const int32_t *right) {
+    auto lower_priority = [&](int32_t a, int32_t b) {
+        if (had[a] != had[b]) return had[a] < had[b];
+        return a > b;
+    };
+    std::priority_queue<int32_t, std::vector<int32_t>, decltype(lower_priority)> pq(lower_priority);
+    std::vector<int32_t> cut;
+    uint32_t max_queue = size;
+    pq.push(start);
+    while (!pq.empty() && pq.size() < max_queue) {
+        int32_t node = pq.top();
+        pq.pop();
+        if (left[node] < 0) {
+            cut.push_back(node);
+            max_queue -= 1;
+        } else {
+            pq.push(left[node]);
+            pq.push(right[node]);
+        }
+    }
+    while (!pq.empty()) {
+        cut.push_back(pq.top());
+        pq.pop();
+    }
+    std::sort(cut.begin(), cut.end(), [&](int32_t a, int32_t b) {
+        if (had[a] != had[b]) return had[a] > had[b];
+        return a < b;
+    });
+    return cut;
+}
+
+// Two-level cut of the multi-level hierarchy cut code (Sec. 4.3, Algorithm 3).
+// A node may be a top-level cut node only if its subtree can supply low_size
+// low-level nodes, i.e. it holds at least low_size leaves; Algorithm 3
+// discards the others.  Reading: the top level is Algorithm 2 on the tree of
+// such eligible nodes -- pop the largest-HAD node, push its eligible children
+// (an ineligible child and its subtree are discarded), and a node with no
+// eligible child goes to the cut list as a leaf does in Algorithm 2 -- until
+// the queue plus the list hold top_size nodes.  Every top node t then gets
+// the cut of its own subtree by Algorithm 2 with low_size nodes.  Outputs:
+// top_out[r] (HAD order, r < returned count) and low_out[r * low_size + j]
+// (node j of top node r's low cut, HAD order).  Returns the number of top
+// nodes (0 when the root itself has fewer than low_size leaves).
+uint32_t oracle_select_cut_ml(uint32_t num_nodes, const float *lo, const float *hi, const int32_t *left,
+                              const int32_t *right, const uint32_t *count, uint32_t top_size, uint32_t low_size,
+                              double lambda, int32_t *top_out, int32_t *low_out) {
+    if (num_nodes == 0 || top_size == 0 || low_size == 0) return 0;
+    std::vector<double> had(num_nodes);
+    oracle_had(num_nodes, lo, hi, left, right, count, lambda, had.data());
+    auto eligible = [&](int32_t n) { return leaves_under(n, left, right) >= low_size; };
+    auto lower_priority = [&](int32_t a, int32_t b) {
+        if (had[a] != had[b]) return had[a] < had[b];
+        return a > b;
+    };
+    std::priority_queue<int32_t, std::vector<int32_t>, decltype(lower_priority)> pq(lower_priority);
+    std::vector<int32_t> top;
+    uint32_t max_queue = top_size;
+    if (eligible(0)) pq.push(0);
+    while (!pq.empty() && pq.size() < max_queue) {
+        int32_t node = pq.top();
+        pq.pop();
+        std::vector<int32_t> kids;
+        if (left[node] >= 0) {
+            if (eligible(left[node])) kids.push_back(left[node]);
+            if (eligible(right[node])) kids.push_back(right[node]);
+        }
+        if (kids.empty()) {
+            top.push_back(node);
+            max_queue -= 1;
+        } else {
+            for (int32_t c : kids) pq.push(c);
+        }
+    }
+    while (!pq.empty()) {
+        top.push_back(pq.top());
+        pq.pop();
+    }
+    std::sort(top.begin(), top.end(), [&](int32_t a, int32_t b) {
+        if (had[a] != had[b]) return had[a] > had[b];
+        return a < b;
+    });
+    for (size_t r = 0; r < top.size(); ++r) {
+        top_out[r] = top[r];
+        std::vector<int32_t> low = cut_of_subtree(top[r], low_size, had, left, right);
+        for (uint32_t j = 0; j < low_size; ++j) low_out[r * low_size + j] = low[j];
+    }
+    return (uint32_t)top.size();
+}
+
+// Multi-level hierarchy cut code (Sec. 4.3): the top field (top_field bits,
+// most significant) holds one bit per top node as in Algorithm 1; the
+// representative is the first top node in HAD order that the ray meets
+// (Sec. 4.3: the intersected top node of highest HAD), and the next
+// low_field bits hold the ray's results against that node's low-level cut.
+// A ray that meets no top node has an empty low field.  ntop top boxes,
+// ntop * low_field low boxes (row r = top node r); top_field + low_field <=
+// key_bits, remaining low bits 0.
+void oracle_encode_mlhcc(uint64_t n, const float *org, const float *dir, uint32_t top_field, uint32_t ntop,
+                         const float *top_lo, const float *top_hi, uint32_t low_field, const float *low_lo,
+                         const float *low_hi, uint32_t key_bits, uint64_t *keys) {
+    uint32_t used_top = std::min(ntop, top_field);
+    for (uint64_t i = 0; i < n; ++i) {
+        const float *o = org + 4 * i, *d = dir + 4 * i;
+        float inv[3] = {1.0f / d[0], 1.0f / d[1], 1.0f / d[2]};
+        uint64_t key = 0;
+        int rep = -1;
+        for (uint32_t r = 0; r < used_top; ++r) {
+            float tnear, tfar;
+            slab(o, inv, o[3], d[3], top_lo + 3 * r, top_hi + 3 * r, &tnear, &tfar);
+            if (tnear <= tfar) {
+                key |= (uint64_t)1 << (key_bits - 1 - r);
+                if (rep < 0) rep = (int)r;
+            }
+        }
+        if (rep >= 0) {
+            for (uint32_t j = 0; j < low_field; ++j) {
+                const size_t b = (size_t)rep * low_field + j;
+                float tnear, tfar;
+                slab(o, inv, o[3], d[3], low_lo + 3 * b, low_hi + 3 * b, &tnear, &tfar);
+                if (tnear <= tfar) key |= (uint64_t)1 << (key_bits - 1 - top_field - j);
+            }
+        }
+        keys[i] = key;
+    }
+}
+
+// Regular grid encoding (Sec. 5): the cut boxes of HCC replaced by cells that
+// divide the scene box evenly.  Reading: the cell count is the largest power
+// of two not above max_cells; starting from one cell, the axis whose cells
+// are longest (first axis on ties) is halved until that count is reached.
+// Cell boundary i of g along an axis is ((g - i) lo + i hi) / g evaluated in
+// double and rounded to float, so the outer boundaries are lo and hi exactly
+// and neighbouring cells share their face.  Cell (i, j, l) is number
+// (i gy + j) gz + l and drives key bit (k - 1 - number).  Writes the cell
+// boxes and dims; returns the cell count.
+uint32_t oracle_grid_cells(const float *scene_lo, const float *scene_hi, uint32_t max_cells, float *cell_lo,
+                           float *cell_hi, uint32_t *dims) {
+    if (max_cells == 0) return 0;
+    uint32_t g[3] = {1, 1, 1};
+    uint32_t cells = 1;
+    while (cells * 2 <= max_cells) {
+        int best = 0;
+        double best_len = -1.0;
+        for (int a = 0; a < 3; ++a) {
+            double len = ((double)scene_hi[a] - (double)scene_lo[a]) / g[a];
+            if (len > best_len) {
+                best_len = len;
+                best = a;
+            }
+        }
+        g[best] *= 2;
+        cells *= 2;
+    }
+    auto bound = [&](int a, uint32_t i) {
+        return (float)(((double)(g[a] - i) * (double)scene_lo[a] + (double)i * (double)scene_hi[a]) / (double)g[a]);
+    };
+    uint32_t r = 0;
+    for (uint32_t i = 0; i < g[0]; ++i)
+        for (uint32_t j = 0; j < g[1]; ++j)
+            for (uint32_t l = 0; l < g[2]; ++l, ++r) {
+                const uint32_t c[3] = {i, j, l};
+                for (int a = 0; a < 3; ++a) {
+                    cell_lo[3 * r + a] = bound(a, c[a]);
+                    cell_hi[3 * r + a] = bound(a, c[a] + 1);
+                }
+            }
+    for (int a = 0; a < 3; ++a) dims[a] = g[a];
+    return cells;
+}
+
+// Prefix path code (Sec. 4.1): the results of the first k box tests of a
+// traversal that every ray makes in the same fixed order.  Reading: the order
+// is depth-first pre-order from the root, left child before right; a node
+// whose box the ray meets is followed into its children, a missed node's
+// subtree is skipped, and no test is skipped for a found hit (the path does
+// not depend on hits).  Test number m drives bit (k - 1 - m); a traversal
+// that ends before k tests leaves the remaining bits 0.
+static void ppc_visit(int32_t node, const float *o, const float *inv, float tmin, float tmax, const float *lo,
+                      const float *hi, const int32_t *left, const int32_t *right, uint32_t key_bits, uint32_t *m,
+                      uint64_t *key) {
+    if (*m >= key_bits) return;
+    float tnear, tfar;
+    slab(o, inv, tmin, tmax, lo + 3 * node, hi + 3 * node, &tnear, &tfar);
+    const bool met = tnear <= tfar;
+    if (met) *key |= (uint64_t)1 << (key_bits - 1 - *m);
+    *m += 1;
+    if (met && left[node] >= 0) {
+        ppc_visit(left[node], o, inv, tmin, tmax, lo, hi, left, right, key_bits, m, key);
+        ppc_visit(right[node], o, inv, tmin, tmax, lo, hi, left, right, key_bits, m, key);
+    }
+}
+
+void oracle_encode_ppc(uint64_t n, const float *org, const float *dir, uint32_t num_nodes, const float *lo,
+                       const float *hi, const int32_t *left, const int32_t *right, uint32_t key_bits,
+                       uint64_t *keys) {
+    for (uint64_t i = 0; i < n; ++i) {
+        const float *o = org + 4 * i, *d = dir + 4 * i;
+        float inv[3] = {1.0f / d[0], 1.0f / d[1], 1.0f / d[2]};
+        uint64_t key = 0;
+        uint32_t m = 0;
+        if (num_nodes > 0) ppc_visit(0, o, inv, o[3], d[3], lo, hi, left, right, key_bits, &m, &key);
         keys[i] = key;
     }
 }
