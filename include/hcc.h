@@ -56,7 +56,9 @@ typedef enum hcc_method {
     HCC_METHOD_HCC = 1,       /* hierarchy cut code (Sec. 4.2) */
     HCC_METHOD_TWOPOINT = 2,  /* origin + estimated termination Morton code (Sec. 3.2, Sec. 5) */
     HCC_METHOD_ORIGIN = 3,    /* Morton code of the origin (Sec. 3.2 "Origin", Table 1) */
-    HCC_METHOD_ORIGIN_DIR = 4 /* origin Morton above direction Morton (Sec. 3.2 "Origin-Direction") */
+    HCC_METHOD_ORIGIN_DIR = 4, /* origin Morton above direction Morton (Sec. 3.2 "Origin-Direction") */
+    HCC_METHOD_PPC = 5,        /* prefix path code (Sec. 4.1), an upper bound */
+    HCC_METHOD_MLHCC = 6       /* multi-level hierarchy cut code (Sec. 4.3) */
 } hcc_method;
 
 typedef struct hcc_ctx hcc_ctx; /* device, stream, scratch, device error word */
@@ -193,6 +195,49 @@ hcc_status hcc_cut_info(const hcc_cut *cut, uint32_t *size, int32_t *node_ids);
 
 hcc_status hcc_cut_destroy(hcc_cut *cut);
 
+/*
+ * The two-level cut of the multi-level hierarchy cut code (Sec. 4.3,
+ * Algorithm 3).  A node may be a top-level node only if its subtree holds at
+ * least low_size leaves (Algorithm 3 discards the others, so that no
+ * low-level node is empty).  The top level runs the queue of Algorithm 2 on
+ * such nodes: pop the largest-HAD node, push its children that qualify (a
+ * child that does not is discarded with its subtree); a node with no
+ * qualifying child joins the cut as a leaf does in Algorithm 2; stop at
+ * top_size nodes.  Each top node r then gets the Algorithm 2 cut of its own
+ * subtree with low_size nodes.  Both levels are ordered by HAD, descending.
+ * The result has between 0 and top_size top nodes (0 when the root has fewer
+ * than low_size leaves: every key is then 0), each with exactly low_size
+ * low-level nodes; hcc_cut_info reports the top level.
+ * Errors: INVALID_ARG (a size 0, top_size + low_size > 64, lambda negative
+ * or not finite), OOM, CUDA.
+ */
+hcc_status hcc_select_cut_ml(hcc_ctx *ctx, const hcc_bvh *bvh, uint32_t top_size, uint32_t low_size, double lambda,
+                             hcc_cut **out);
+
+/* Two-level cut sizes: *ntop top nodes, the field widths top_size and
+ * low_size it was made with, and (if low_ids is not NULL, ntop * low_size
+ * entries) the low-level node ids, row r for top node r.  INVALID_ARG for a
+ * one-level cut. */
+hcc_status hcc_cut_ml_info(const hcc_cut *cut, uint32_t *ntop, uint32_t *top_size, uint32_t *low_size,
+                           int32_t *low_ids);
+
+/*
+ * Regular grid encoding (Sec. 5): a "cut" of grid cells that divide the
+ * BVH's root box evenly, for hcc_encode(HCC).  The cell count is the largest
+ * power of two not above max_cells; starting from one cell, the axis whose
+ * cells are longest (the first such axis on ties) is halved until that count
+ * is reached.  Boundary i of g along an axis is ((g - i) lo + i hi) / g in
+ * double, rounded to float, so neighbouring cells share their faces exactly.
+ * Cell (i, j, l) is cut node (i gy + j) gz + l.  hcc_cut_info reports the
+ * cell count and node ids of -1.  Errors: INVALID_ARG (max_cells not in
+ * 1..64), OOM, CUDA.
+ */
+hcc_status hcc_select_grid(hcc_ctx *ctx, const hcc_bvh *bvh, uint32_t max_cells, hcc_cut **out);
+
+/* Host copy of the boxes behind the key bits (the top level of a two-level
+ * cut): lo and hi receive 3 floats per node, min(cut size, 64) nodes. */
+hcc_status hcc_cut_boxes(const hcc_cut *cut, float *lo, float *hi);
+
 /* ---------------------------------------------------------------- encode */
 
 /*
@@ -216,8 +261,20 @@ hcc_status hcc_cut_destroy(hcc_cut *cut);
  *     code (u, v) of the octahedral map of the direction (L1-normalise, fold
  *     z < 0 over the diagonals, map [-1, 1] to [0, 1]) with bd = floor(k/6)
  *     bits per coordinate, left-justified.  Requires bvh.
+ *   MLHCC (Sec. 4.3): with a cut from hcc_select_cut_ml of field widths T
+ *     and L (T + L <= key_bits): bit (key_bits - 1 - r) = the ray meets top
+ *     node r; the representative is the first top node in HAD order that it
+ *     meets, and bit (key_bits - 1 - T - j) = the ray meets low-level node j
+ *     of the representative.  No top node met: the low field is 0.  The
+ *     slab test is HCC's.  Requires a two-level cut.
+ *   PPC (Sec. 4.1): the results of the first key_bits box tests of a
+ *     depth-first, left-child-first traversal that does not depend on the
+ *     ray (a met internal node is entered, a missed node's subtree skipped,
+ *     hits never cut it short); test m drives bit (key_bits - 1 - m), bits
+ *     after the traversal ends are 0.  HCC's slab test on the exact boxes.
+ *     Requires a bvh uploaded with HCC_BVH_EXACT (UNSUPPORTED otherwise).
  *   NOSORT: INVALID_ARG (nothing to encode).
- * Errors: INVALID_ARG, CUDA.
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA.
  */
 hcc_status hcc_encode(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const hcc_cut *cut,
                       const hcc_rays *rays, uint32_t key_bits, void *keys);

@@ -1,5 +1,6 @@
-// Key encoding kernels: hierarchy cut code (Algorithm 1, Sec. 4.2.1) and the
-// TwoPoint baseline (Sec. 3.2, Sec. 5).
+// Key encoding kernels: hierarchy cut code (Algorithm 1, Sec. 4.2.1), its
+// multi-level form (Sec. 4.3), the prefix path code (Sec. 4.1) and the
+// TwoPoint, Origin and Origin-Direction baselines (Sec. 3.2, Sec. 5).
 //
 // Floating point: every rounding step is an explicit round-to-nearest
 // intrinsic and the library is built with --fmad=false, so each key is the
@@ -334,6 +335,145 @@ cudaError_t launch_encode_origin_dir(cudaStream_t s, const float4 *org, const fl
     else
         k_encode_origin_dir<uint64_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, lo[0], lo[1], lo[2], ext[0], ext[1],
                                                                  ext[2], key_bits, (uint64_t *)keys);
+    return cudaGetLastError();
+}
+
+namespace {
+
+// Multi-level HCC (Sec. 4.3): the top field as in Algorithm 1; the first met
+// top node (HAD order) is the representative, and its low-level cut fills the
+// next low_field bits.  All boxes of both levels are staged in shared memory:
+// top pairs first, then the low pairs row by row.
+template <typename K>
+__global__ void __launch_bounds__(ENC_BLOCK) k_encode_mlhcc(const float4 *__restrict__ org,
+                                                            const float4 *__restrict__ dir, uint64_t n,
+                                                            const float4 *__restrict__ top, uint32_t ntop,
+                                                            uint32_t top_field, const float4 *__restrict__ low,
+                                                            uint32_t low_field, uint32_t key_bits,
+                                                            K *__restrict__ keys) {
+    extern __shared__ float4 s_box[];
+    float4 *s_top = s_box, *s_low = s_box + 2 * ntop;
+    for (uint32_t r = threadIdx.x; r < 2 * ntop; r += blockDim.x) s_top[r] = top[r];
+    for (uint32_t r = threadIdx.x; r < 2 * ntop * low_field; r += blockDim.x) s_low[r] = low[r];
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float4 o = __ldcs(org + i);
+        const float4 d = __ldcs(dir + i);
+        const float ix = __frcp_rn(d.x), iy = __frcp_rn(d.y), iz = __frcp_rn(d.z);
+        K key = 0;
+        K bit = (K)1 << (key_bits - 1);
+        uint32_t rep = ntop;
+        for (uint32_t r = 0; r < ntop; ++r, bit >>= 1)
+            if (meets(o, d, ix, iy, iz, s_top[2 * r], s_top[2 * r + 1])) {
+                key |= bit;
+                rep = min(rep, r);
+            }
+        if (rep < ntop) {
+            const float4 *row = s_low + 2 * (size_t)rep * low_field;
+            K lbit = (K)1 << (key_bits - 1 - top_field);
+            for (uint32_t j = 0; j < low_field; ++j, lbit >>= 1)
+                if (meets(o, d, ix, iy, iz, row[2 * j], row[2 * j + 1])) key |= lbit;
+        }
+        __stcs(keys + i, key);
+    }
+}
+
+// Prefix path code (Sec. 4.1): a depth-first, left-child-first walk that
+// every ray takes in the same order; each visited node's box test is one key
+// bit, a met internal node is entered, a missed subtree skipped, and the walk
+// stops after key_bits tests.  The children's exact boxes come from the
+// parent's 64-byte node; a parent whose right child is still due waits on a
+// stack of node indices (each entry follows a test, so key_bits entries
+// suffice).
+template <typename K>
+__global__ void __launch_bounds__(ENC_BLOCK) k_encode_ppc(const float4 *__restrict__ org,
+                                                          const float4 *__restrict__ dir, uint64_t n,
+                                                          const float4 *__restrict__ nodes, uint32_t root_ref,
+                                                          float4 root_lo, float4 root_hi, uint32_t key_bits,
+                                                          K *__restrict__ keys) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float4 o = __ldcs(org + i);
+        const float4 d = __ldcs(dir + i);
+        const float ix = __frcp_rn(d.x), iy = __frcp_rn(d.y), iz = __frcp_rn(d.z);
+        K key = 0;
+        uint32_t m = 0;  // tests made
+        const bool root_met = meets(o, d, ix, iy, iz, root_lo, root_hi);
+        if (root_met) key |= (K)1 << (key_bits - 1);
+        m = 1;
+        uint32_t stack[64];
+        uint32_t sp = 0;
+        uint32_t cur = root_ref;
+        bool right = false;  // which child of cur is visited next
+        bool go = root_met && !(root_ref & REF_LEAF);
+        while (go && m < key_bits) {
+            const float4 *f = nodes + 4 * (size_t)cur;
+            const float4 n0 = __ldg(f), n1 = __ldg(f + 1), n2 = __ldg(f + 2);
+            const uint4 n3 = __ldg(reinterpret_cast<const uint4 *>(f + 3));
+            float4 lo, hi;
+            uint32_t child;
+            if (!right) {
+                lo = make_float4(n0.x, n0.y, n0.z, 0.f);
+                hi = make_float4(n0.w, n1.x, n1.y, 0.f);
+                child = n3.x;
+                stack[sp++] = cur;  // its right child follows the left subtree
+            } else {
+                lo = make_float4(n1.z, n1.w, n2.x, 0.f);
+                hi = make_float4(n2.y, n2.z, n2.w, 0.f);
+                child = n3.y;
+            }
+            const bool met = meets(o, d, ix, iy, iz, lo, hi);
+            if (met) key |= (K)1 << (key_bits - 1 - m);
+            ++m;
+            if (met && !(child & REF_LEAF)) {
+                cur = child;
+                right = false;
+            } else if (sp > 0) {
+                cur = stack[--sp];
+                right = true;
+            } else {
+                go = false;
+            }
+        }
+        __stcs(keys + i, key);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_encode_mlhcc(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n,
+                                const float4 *top, uint32_t ntop, uint32_t top_field, const float4 *low,
+                                uint32_t low_field, uint32_t key_bits, void *keys) {
+    if (n == 0) return cudaSuccess;
+    if (ntop > top_field || top_field + low_field > MAX_CUT_BITS || top_field + low_field > key_bits)
+        return cudaErrorInvalidValue;
+    const size_t smem = sizeof(float4) * 2 * ((size_t)ntop + (size_t)ntop * low_field);
+    const int grid = encode_grid(n, ENC_BLOCK, 8);
+    if (key_bits <= 32)
+        k_encode_mlhcc<uint32_t><<<grid, ENC_BLOCK, smem, s>>>(org, dir, n, top, ntop, top_field, low, low_field,
+                                                              key_bits, (uint32_t *)keys);
+    else
+        k_encode_mlhcc<uint64_t><<<grid, ENC_BLOCK, smem, s>>>(org, dir, n, top, ntop, top_field, low, low_field,
+                                                              key_bits, (uint64_t *)keys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encode_ppc(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n, const uint4 *nodes,
+                              uint32_t root_ref, const float root_lo[3], const float root_hi[3], uint32_t key_bits,
+                              void *keys) {
+    if (n == 0) return cudaSuccess;
+    if (key_bits < 1 || key_bits > MAX_CUT_BITS) return cudaErrorInvalidValue;
+    const float4 lo = make_float4(root_lo[0], root_lo[1], root_lo[2], 0.f);
+    const float4 hi = make_float4(root_hi[0], root_hi[1], root_hi[2], 0.f);
+    const float4 *f = reinterpret_cast<const float4 *>(nodes);
+    const int grid = encode_grid(n, ENC_BLOCK, 8);
+    if (key_bits <= 32)
+        k_encode_ppc<uint32_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, f, root_ref, lo, hi, key_bits,
+                                                          (uint32_t *)keys);
+    else
+        k_encode_ppc<uint64_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, f, root_ref, lo, hi, key_bits,
+                                                          (uint64_t *)keys);
     return cudaGetLastError();
 }
 

@@ -48,9 +48,14 @@ struct hcc_bvh {
 
 struct hcc_cut {
     int device = 0;
-    std::vector<int32_t> ids;
+    std::vector<int32_t> ids;   // cut nodes (the top level of a two-level cut), key order; -1 for grid cells
     float4 *d_boxes = nullptr;  // (lo, hi) pairs in key order, at most 64 nodes
     uint32_t on_device = 0;
+    std::vector<float> lo, hi;  // host copy of the on-device boxes, 3 floats each
+    // two-level cut (MLHCC): field widths, low-level ids and boxes (row r = top node r)
+    uint32_t top_field = 0, low_field = 0;
+    std::vector<int32_t> low_ids;
+    float4 *d_low = nullptr;
 };
 
 struct hcc_batch {
@@ -548,18 +553,16 @@ hcc_status hcc_bvh_destroy(hcc_bvh *b) {
 
 // ------------------------------------------------------------------- cut
 
-hcc_status hcc_select_cut(hcc_ctx *ctx, const hcc_bvh *bvh, uint32_t cut_size, double lambda, hcc_cut **out) {
-    if (!ctx || !bvh || !out) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL argument");
-    *out = nullptr;
-    if (cut_size == 0) return fail(ctx, HCC_ERR_INVALID_ARG, "cut_size must be positive");
-    if (!(lambda >= 0.0) || !std::isfinite(lambda))
-        return fail(ctx, HCC_ERR_INVALID_ARG, "lambda must be finite and non-negative");
-    const std::vector<double> had = compute_had(bvh, lambda);
-    // Algorithm 2
+// Algorithm 2 on the subtree of `start`: pop the largest-HAD node; a leaf
+// joins the cut and lowers the queue limit, an internal node is replaced by
+// its children; stop at cut_size nodes (or when the queue empties).  Result
+// in key order.
+static std::vector<int32_t> cut_of_subtree(const hcc_bvh *bvh, const std::vector<double> &had, int32_t start,
+                                           uint32_t cut_size) {
     HadHeap pq(had);
     std::vector<int32_t> cut;
     uint32_t max_queue = cut_size;
-    pq.push(0);
+    pq.push(start);
     while (!pq.a.empty() && pq.a.size() < max_queue) {
         const int32_t k = pq.pop();
         if (bvh->left[k] < 0) {
@@ -573,27 +576,204 @@ hcc_status hcc_select_cut(hcc_ctx *ctx, const hcc_bvh *bvh, uint32_t cut_size, d
     cut.insert(cut.end(), pq.a.begin(), pq.a.end());
     std::sort(cut.begin(), cut.end(),
               [&](int32_t x, int32_t y) { return had[x] > had[y] || (had[x] == had[y] && x < y); });
+    return cut;
+}
+
+static void push_box(std::vector<float4> &boxes, const float *lo, const float *hi) {
+    boxes.push_back(make_float4(lo[0], lo[1], lo[2], 0.0f));
+    boxes.push_back(make_float4(hi[0], hi[1], hi[2], 0.0f));
+}
+
+// Copies (lo, hi) pairs to a new device array (at least one pair).
+static cudaError_t upload_boxes(std::vector<float4> boxes, float4 **out) {
+    if (boxes.empty()) boxes.resize(2, make_float4(0.f, 0.f, 0.f, 0.f));
+    cudaError_t e = cudaMalloc(out, boxes.size() * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMemcpy(*out, boxes.data(), boxes.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    return e;
+}
+
+// Sets the key-driving boxes of a cut (host copy and device array).
+static cudaError_t set_key_boxes(hcc_cut *c, const std::vector<float> &lo, const std::vector<float> &hi) {
+    const uint32_t m = (uint32_t)std::min<size_t>(lo.size() / 3, MAX_KEY_NODES);
+    c->on_device = m;
+    c->lo.assign(lo.begin(), lo.begin() + 3 * m);
+    c->hi.assign(hi.begin(), hi.begin() + 3 * m);
+    std::vector<float4> boxes;
+    for (uint32_t r = 0; r < m; ++r) push_box(boxes, &c->lo[3 * r], &c->hi[3 * r]);
+    return upload_boxes(boxes, &c->d_boxes);
+}
+
+static hcc_status check_lambda(hcc_ctx *ctx, double lambda) {
+    if (!(lambda >= 0.0) || !std::isfinite(lambda))
+        return fail(ctx, HCC_ERR_INVALID_ARG, "lambda must be finite and non-negative");
+    return HCC_OK;
+}
+
+hcc_status hcc_select_cut(hcc_ctx *ctx, const hcc_bvh *bvh, uint32_t cut_size, double lambda, hcc_cut **out) {
+    if (!ctx || !bvh || !out) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (cut_size == 0) return fail(ctx, HCC_ERR_INVALID_ARG, "cut_size must be positive");
+    hcc_status st = check_lambda(ctx, lambda);
+    if (st != HCC_OK) return st;
+    const std::vector<double> had = compute_had(bvh, lambda);
+    const std::vector<int32_t> cut = cut_of_subtree(bvh, had, 0, cut_size);
     hcc_cut *c = new (std::nothrow) hcc_cut;
     if (!c) return fail(ctx, HCC_ERR_OOM, "host allocation");
     c->device = ctx->device;
     c->ids = cut;
-    c->on_device = (uint32_t)std::min<size_t>(cut.size(), MAX_KEY_NODES);
-    std::vector<float4> boxes(2 * (size_t)std::max<uint32_t>(c->on_device, 1));
-    for (uint32_t r = 0; r < c->on_device; ++r) {
-        const int32_t k = cut[r];
-        boxes[2 * r] = make_float4(bvh->lo[3 * k], bvh->lo[3 * k + 1], bvh->lo[3 * k + 2], 0.0f);
-        boxes[2 * r + 1] = make_float4(bvh->hi[3 * k], bvh->hi[3 * k + 1], bvh->hi[3 * k + 2], 0.0f);
+    std::vector<float> lo, hi;
+    for (int32_t k : cut) {
+        lo.insert(lo.end(), &bvh->lo[3 * k], &bvh->lo[3 * k] + 3);
+        hi.insert(hi.end(), &bvh->hi[3 * k], &bvh->hi[3 * k] + 3);
     }
     DeviceGuard g(ctx->device);
-    cudaError_t e = cudaMalloc(&c->d_boxes, boxes.size() * sizeof(float4));
-    if (e == cudaSuccess)
-        e = cudaMemcpy(c->d_boxes, boxes.data(), boxes.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    cudaError_t e = set_key_boxes(c, lo, hi);
     if (e != cudaSuccess) {
         cudaGetLastError();
         hcc_cut_destroy(c);
         return cuda_fail(ctx, e, "cut upload");
     }
     *out = c;
+    return HCC_OK;
+}
+
+hcc_status hcc_select_cut_ml(hcc_ctx *ctx, const hcc_bvh *bvh, uint32_t top_size, uint32_t low_size, double lambda,
+                             hcc_cut **out) {
+    if (!ctx || !bvh || !out) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (top_size == 0 || low_size == 0 || top_size + low_size > MAX_KEY_NODES)
+        return fail(ctx, HCC_ERR_INVALID_ARG, "top_size and low_size must be positive with a sum of at most 64");
+    hcc_status st = check_lambda(ctx, lambda);
+    if (st != HCC_OK) return st;
+    const std::vector<double> had = compute_had(bvh, lambda);
+    // leaves under every node, children before parents (ids are not assumed ordered)
+    const uint32_t n = bvh->num_nodes;
+    std::vector<uint32_t> leaves(n, 1);
+    {
+        std::vector<int32_t> order, todo{0};
+        while (!todo.empty()) {
+            const int32_t k = todo.back();
+            todo.pop_back();
+            order.push_back(k);
+            if (bvh->left[k] >= 0) {
+                todo.push_back(bvh->left[k]);
+                todo.push_back(bvh->right[k]);
+            }
+        }
+        for (auto it = order.rbegin(); it != order.rend(); ++it)
+            if (bvh->left[*it] >= 0) leaves[*it] = leaves[bvh->left[*it]] + leaves[bvh->right[*it]];
+    }
+    auto qualifies = [&](int32_t k) { return leaves[k] >= low_size; };
+    // Algorithm 3, top level: Algorithm 2 over the nodes that qualify
+    HadHeap pq(had);
+    std::vector<int32_t> top;
+    uint32_t max_queue = top_size;
+    if (qualifies(0)) pq.push(0);
+    while (!pq.a.empty() && pq.a.size() < max_queue) {
+        const int32_t k = pq.pop();
+        const bool l = bvh->left[k] >= 0 && qualifies(bvh->left[k]);
+        const bool r = bvh->left[k] >= 0 && qualifies(bvh->right[k]);
+        if (!l && !r) {
+            top.push_back(k);
+            --max_queue;
+        } else {
+            if (l) pq.push(bvh->left[k]);
+            if (r) pq.push(bvh->right[k]);
+        }
+    }
+    top.insert(top.end(), pq.a.begin(), pq.a.end());
+    std::sort(top.begin(), top.end(),
+              [&](int32_t x, int32_t y) { return had[x] > had[y] || (had[x] == had[y] && x < y); });
+    hcc_cut *c = new (std::nothrow) hcc_cut;
+    if (!c) return fail(ctx, HCC_ERR_OOM, "host allocation");
+    c->device = ctx->device;
+    c->ids = top;
+    c->top_field = top_size;
+    c->low_field = low_size;
+    std::vector<float> lo, hi;
+    std::vector<float4> low_boxes;
+    for (int32_t t : top) {
+        lo.insert(lo.end(), &bvh->lo[3 * t], &bvh->lo[3 * t] + 3);
+        hi.insert(hi.end(), &bvh->hi[3 * t], &bvh->hi[3 * t] + 3);
+        const std::vector<int32_t> low = cut_of_subtree(bvh, had, t, low_size);  // exactly low_size nodes
+        for (int32_t k : low) {
+            c->low_ids.push_back(k);
+            push_box(low_boxes, &bvh->lo[3 * k], &bvh->hi[3 * k]);
+        }
+    }
+    DeviceGuard g(ctx->device);
+    cudaError_t e = set_key_boxes(c, lo, hi);
+    if (e == cudaSuccess) e = upload_boxes(low_boxes, &c->d_low);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        hcc_cut_destroy(c);
+        return cuda_fail(ctx, e, "cut upload");
+    }
+    *out = c;
+    return HCC_OK;
+}
+
+hcc_status hcc_cut_ml_info(const hcc_cut *cut, uint32_t *ntop, uint32_t *top_size, uint32_t *low_size,
+                           int32_t *low_ids) {
+    if (!cut || !ntop || !top_size || !low_size || cut->low_field == 0) return HCC_ERR_INVALID_ARG;
+    *ntop = (uint32_t)cut->ids.size();
+    *top_size = cut->top_field;
+    *low_size = cut->low_field;
+    if (low_ids) std::memcpy(low_ids, cut->low_ids.data(), cut->low_ids.size() * sizeof(int32_t));
+    return HCC_OK;
+}
+
+hcc_status hcc_select_grid(hcc_ctx *ctx, const hcc_bvh *bvh, uint32_t max_cells, hcc_cut **out) {
+    if (!ctx || !bvh || !out) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (max_cells == 0 || max_cells > MAX_KEY_NODES) return fail(ctx, HCC_ERR_INVALID_ARG, "max_cells must be 1..64");
+    const float *blo = &bvh->lo[0], *bhi = &bvh->hi[0];  // the root box
+    uint32_t g[3] = {1, 1, 1}, cells = 1;
+    while (cells * 2 <= max_cells) {
+        int axis = 0;
+        double longest = -1.0;
+        for (int a = 0; a < 3; ++a) {
+            const double len = ((double)bhi[a] - (double)blo[a]) / g[a];
+            if (len > longest) {
+                longest = len;
+                axis = a;
+            }
+        }
+        g[axis] *= 2;
+        cells *= 2;
+    }
+    auto boundary = [&](int a, uint32_t i) {
+        return (float)(((double)(g[a] - i) * (double)blo[a] + (double)i * (double)bhi[a]) / (double)g[a]);
+    };
+    std::vector<float> lo, hi;
+    for (uint32_t i = 0; i < g[0]; ++i)
+        for (uint32_t j = 0; j < g[1]; ++j)
+            for (uint32_t l = 0; l < g[2]; ++l) {
+                const uint32_t idx[3] = {i, j, l};
+                for (int a = 0; a < 3; ++a) {
+                    lo.push_back(boundary(a, idx[a]));
+                    hi.push_back(boundary(a, idx[a] + 1));
+                }
+            }
+    hcc_cut *c = new (std::nothrow) hcc_cut;
+    if (!c) return fail(ctx, HCC_ERR_OOM, "host allocation");
+    c->device = ctx->device;
+    c->ids.assign(cells, -1);
+    DeviceGuard dg(ctx->device);
+    cudaError_t e = set_key_boxes(c, lo, hi);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        hcc_cut_destroy(c);
+        return cuda_fail(ctx, e, "cut upload");
+    }
+    *out = c;
+    return HCC_OK;
+}
+
+hcc_status hcc_cut_boxes(const hcc_cut *cut, float *lo, float *hi) {
+    if (!cut || !lo || !hi) return HCC_ERR_INVALID_ARG;
+    std::memcpy(lo, cut->lo.data(), cut->lo.size() * sizeof(float));
+    std::memcpy(hi, cut->hi.data(), cut->hi.size() * sizeof(float));
     return HCC_OK;
 }
 
@@ -609,6 +789,7 @@ hcc_status hcc_cut_destroy(hcc_cut *cut) {
     {
         DeviceGuard g(cut->device);
         if (cut->d_boxes) cudaFree(cut->d_boxes);
+        if (cut->d_low) cudaFree(cut->d_low);
     }
     delete cut;
     return HCC_OK;
@@ -623,10 +804,19 @@ hcc_status hcc_encode(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const
     if (st != HCC_OK) return st;
     if (key_bits < 1 || key_bits > 64) return fail(ctx, HCC_ERR_INVALID_ARG, "key_bits must be 1..64");
     if (method != HCC_METHOD_HCC && method != HCC_METHOD_TWOPOINT && method != HCC_METHOD_ORIGIN &&
-        method != HCC_METHOD_ORIGIN_DIR)
-        return fail(ctx, HCC_ERR_INVALID_ARG, "hcc_encode needs HCC, TWOPOINT, ORIGIN or ORIGIN_DIR");
-    if (method == HCC_METHOD_HCC && !cut) return fail(ctx, HCC_ERR_INVALID_ARG, "HCC needs a cut");
-    if (method != HCC_METHOD_HCC && !bvh) return fail(ctx, HCC_ERR_INVALID_ARG, "this key needs the BVH");
+        method != HCC_METHOD_ORIGIN_DIR && method != HCC_METHOD_PPC && method != HCC_METHOD_MLHCC)
+        return fail(ctx, HCC_ERR_INVALID_ARG, "hcc_encode needs a method with a key");
+    const bool cut_key = method == HCC_METHOD_HCC || method == HCC_METHOD_MLHCC;
+    if (cut_key && !cut) return fail(ctx, HCC_ERR_INVALID_ARG, "this key needs a cut");
+    if (!cut_key && !bvh) return fail(ctx, HCC_ERR_INVALID_ARG, "this key needs the BVH");
+    if (method == HCC_METHOD_MLHCC) {
+        if (cut->low_field == 0) return fail(ctx, HCC_ERR_INVALID_ARG, "MLHCC needs a two-level cut");
+        if (cut->top_field + cut->low_field > key_bits)
+            return fail(ctx, HCC_ERR_INVALID_ARG, "the cut's two fields need %u key bits",
+                        cut->top_field + cut->low_field);
+    }
+    if (method == HCC_METHOD_PPC && bvh->layout != HCC_BVH_EXACT)
+        return fail(ctx, HCC_ERR_UNSUPPORTED, "the prefix path code needs a BVH with exact node boxes");
     if (rays->n == 0) return HCC_OK;
     if (!keys || !aligned(keys, key_bits > 32 ? 8 : 4))
         return fail(ctx, HCC_ERR_INVALID_ARG, "keys NULL or misaligned");
@@ -637,6 +827,12 @@ hcc_status hcc_encode(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const
     if (method == HCC_METHOD_HCC) {
         const uint32_t used = std::min<uint32_t>(cut->on_device, key_bits);
         e = launch_encode_hcc(ctx->stream, o, d, rays->n, cut->d_boxes, used, key_bits, keys);
+    } else if (method == HCC_METHOD_MLHCC) {
+        e = launch_encode_mlhcc(ctx->stream, o, d, rays->n, cut->d_boxes, cut->on_device, cut->top_field, cut->d_low,
+                                cut->low_field, key_bits, keys);
+    } else if (method == HCC_METHOD_PPC) {
+        e = launch_encode_ppc(ctx->stream, o, d, rays->n, bvh->d_nodes, bvh->root_ref, &bvh->lo[0], &bvh->hi[0],
+                              key_bits, keys);
     } else {
         float lo[3], ext[3];
         for (int a = 0; a < 3; ++a) {
@@ -904,6 +1100,8 @@ hcc_status hcc_batch_run(hcc_ctx *ctx, const hcc_batch *b, hcc_method method, co
     if (st != HCC_OK) return st;
     const uint64_t n = b->offsets[b->num_scenes];
     if (rays->n != n) return fail(ctx, HCC_ERR_INVALID_ARG, "rays->n must equal the batch's last offset");
+    if (method == HCC_METHOD_PPC || method == HCC_METHOD_MLHCC)
+        return fail(ctx, HCC_ERR_UNSUPPORTED, "batches take NOSORT, HCC, TWOPOINT, ORIGIN or ORIGIN_DIR keys");
     if (method != HCC_METHOD_NOSORT && method != HCC_METHOD_HCC && method != HCC_METHOD_TWOPOINT &&
         method != HCC_METHOD_ORIGIN && method != HCC_METHOD_ORIGIN_DIR)
         return fail(ctx, HCC_ERR_INVALID_ARG, "unknown method");
@@ -1072,12 +1270,14 @@ hcc_status hcc_run(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const hc
     if (st != HCC_OK) return st;
     if (!bvh) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL BVH");
     if (method != HCC_METHOD_NOSORT && method != HCC_METHOD_HCC && method != HCC_METHOD_TWOPOINT &&
-        method != HCC_METHOD_ORIGIN && method != HCC_METHOD_ORIGIN_DIR)
+        method != HCC_METHOD_ORIGIN && method != HCC_METHOD_ORIGIN_DIR && method != HCC_METHOD_PPC &&
+        method != HCC_METHOD_MLHCC)
         return fail(ctx, HCC_ERR_INVALID_ARG, "unknown method");
     if (rays->n == 0) return HCC_OK;
     if (method == HCC_METHOD_NOSORT) return hcc_trace(ctx, bvh, rays, any_hit, nullptr, hits);
     if (key_bits < 1 || key_bits > 64) return fail(ctx, HCC_ERR_INVALID_ARG, "key_bits must be 1..64");
-    if (method == HCC_METHOD_HCC && !cut) return fail(ctx, HCC_ERR_INVALID_ARG, "HCC needs a cut");
+    if ((method == HCC_METHOD_HCC || method == HCC_METHOD_MLHCC) && !cut)
+        return fail(ctx, HCC_ERR_INVALID_ARG, "this key needs a cut");
     const uint64_t n = rays->n;
     if (n > HCC_MAX_SORT_N) return fail(ctx, HCC_ERR_INVALID_ARG, "n above HCC_MAX_SORT_N");
     DeviceGuard g(ctx->device);

@@ -79,6 +79,17 @@ cudaError_t launch_encode_origin(cudaStream_t s, const float4 *org, uint64_t n, 
 cudaError_t launch_encode_origin_dir(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n,
                                      const float lo[3], const float ext[3], uint32_t key_bits, void *keys);
 
+// Multi-level HCC: ntop top boxes (at most top_field), ntop * low_field low
+// boxes (row r = top node r), (lo, hi) float4 pairs.
+cudaError_t launch_encode_mlhcc(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n,
+                                const float4 *top, uint32_t ntop, uint32_t top_field, const float4 *low,
+                                uint32_t low_field, uint32_t key_bits, void *keys);
+
+// Prefix path code over the exact-layout nodes; root box given separately.
+cudaError_t launch_encode_ppc(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n, const uint4 *nodes,
+                              uint32_t root_ref, const float root_lo[3], const float root_hi[3], uint32_t key_bits,
+                              void *keys);
+
 // Batch of scenes: key of ray i = (scene << key_bits) | its key in its scene.
 cudaError_t launch_encode_multi(cudaStream_t s, int method, const float4 *org, const float4 *dir, uint64_t n,
                                 const SceneDesc *scenes, const uint64_t *offsets, uint32_t num_scenes,

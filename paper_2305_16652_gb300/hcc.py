@@ -23,8 +23,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "csrc", "_build", "libhcc.so")
 
 HCC_METHOD_NOSORT, HCC_METHOD_HCC, HCC_METHOD_TWOPOINT, HCC_METHOD_ORIGIN, HCC_METHOD_ORIGIN_DIR = 0, 1, 2, 3, 4
+HCC_METHOD_PPC, HCC_METHOD_MLHCC = 5, 6
 METHODS = {"nosort": HCC_METHOD_NOSORT, "hcc": HCC_METHOD_HCC, "twopoint": HCC_METHOD_TWOPOINT,
-           "origin": HCC_METHOD_ORIGIN, "origin_dir": HCC_METHOD_ORIGIN_DIR}
+           "origin": HCC_METHOD_ORIGIN, "origin_dir": HCC_METHOD_ORIGIN_DIR, "ppc": HCC_METHOD_PPC,
+           "mlhcc": HCC_METHOD_MLHCC}
 STATUS = {0: "HCC_OK", 1: "HCC_ERR_INVALID_ARG", 2: "HCC_ERR_OOM", 3: "HCC_ERR_CUDA", 4: "HCC_ERR_UNSUPPORTED",
           5: "HCC_ERR_STACK_OVERFLOW", 6: "HCC_ERR_TIMEOUT"}
 HIT_DTYPE = np.dtype([("prim", np.int32), ("t", np.float32), ("u", np.float32), ("v", np.float32)])
@@ -84,6 +86,10 @@ def load(path: str = LIB_PATH):
         "hcc_select_cut": [P, P, u32, f64, PP],
         "hcc_cut_info": [P, P, P],
         "hcc_cut_destroy": [P],
+        "hcc_select_cut_ml": [P, P, u32, u32, f64, PP],
+        "hcc_cut_ml_info": [P, P, P, P, P],
+        "hcc_select_grid": [P, P, u32, PP],
+        "hcc_cut_boxes": [P, P, P],
         "hcc_encode": [P, i32, P, P, ctypes.POINTER(_Rays), u32, P],
         "hcc_sort": [P, P, u32, u64, P],
         "hcc_gather": [P, ctypes.POINTER(_Rays), P, ctypes.POINTER(_Rays)],
@@ -231,6 +237,38 @@ def hcc_cut_info(cut) -> np.ndarray:
     ids = np.zeros(n.value, np.int32)
     _check(load().hcc_cut_info(cut, ctypes.byref(n), _ptr(ids)))
     return ids
+
+
+def hcc_select_cut_ml(ctx, bvh, top_size: int, low_size: int, lam: float = 0.125):
+    """Two-level MLHCC cut (Algorithm 3)."""
+    h = ctypes.c_void_p()
+    _check(load().hcc_select_cut_ml(ctx, bvh, top_size, low_size, lam, ctypes.byref(h)), ctx)
+    return h
+
+
+def hcc_cut_ml_info(cut):
+    """(top ids, low ids (ntop, low_size), top_size, low_size) of a two-level cut."""
+    ntop, tf, lf = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(load().hcc_cut_ml_info(cut, ctypes.byref(ntop), ctypes.byref(tf), ctypes.byref(lf), None))
+    low = np.zeros(ntop.value * lf.value, np.int32)
+    _check(load().hcc_cut_ml_info(cut, ctypes.byref(ntop), ctypes.byref(tf), ctypes.byref(lf), _ptr(low)))
+    return hcc_cut_info(cut), low.reshape(ntop.value, lf.value), tf.value, lf.value
+
+
+def hcc_select_grid(ctx, bvh, max_cells: int):
+    """Regular-grid cells of the root box as a cut (Sec. 5)."""
+    h = ctypes.c_void_p()
+    _check(load().hcc_select_grid(ctx, bvh, max_cells, ctypes.byref(h)), ctx)
+    return h
+
+
+def hcc_cut_boxes(cut):
+    """Host copy of the key-driving boxes: (lo (m, 3), hi (m, 3))."""
+    m = min(len(hcc_cut_info(cut)), 64)
+    lo = np.zeros((m, 3), np.float32)
+    hi = np.zeros((m, 3), np.float32)
+    _check(load().hcc_cut_boxes(cut, _ptr(lo), _ptr(hi)))
+    return lo, hi
 
 
 def hcc_cut_destroy(cut):
