@@ -155,11 +155,11 @@ class ClockSampler:
 
 # -------------------------------------------------------------- workload
 
-def make_workload(seed: int, quick: bool):
+def make_workload(seed: int, quick: bool, shadow: bool = False):
     from paper_2305_16652_gb300 import gen
     if quick:
-        return gen.room_workload(seed, target_tris=200_000, W=480, H=270, spp=8, shadow=False)
-    return gen.room_workload(seed, target_tris=1_000_000, W=1920, H=1080, spp=8, shadow=False)
+        return gen.room_workload(seed, target_tris=200_000, W=480, H=270, spp=8, shadow=shadow)
+    return gen.room_workload(seed, target_tris=1_000_000, W=1920, H=1080, spp=8, shadow=shadow)
 
 
 def peaks():
@@ -211,9 +211,10 @@ def run_ours(args, rank, world, local_rank):
     hits = torch.empty((n, 4), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(method, ev=None, fused=True, bvh_h=None):
+    def step(method, ev=None, fused=True, bvh_h=None, schedule="auto"):
         """One wavefront through the C ABI; ev = 5 events around encode/sort/gather/trace."""
         b = bvh_h or bvh
+        hcc.hcc_set_trace_schedule(ctx, schedule)
         if ev:
             ev[0].record(stream)
         if method == "nosort":
@@ -266,7 +267,9 @@ def run_ours(args, rank, world, local_rank):
     others = {}
     variants = [("nosort", "nosort", {}), ("twopoint", "twopoint", {}),
                 ("hcc_split_gather", "hcc", {"fused": False}),
-                ("nosort_quantised", "nosort", {"bvh_h": bvh_q}), ("hcc_quantised", "hcc", {"bvh_h": bvh_q})]
+                ("nosort_quantised", "nosort", {"bvh_h": bvh_q}), ("hcc_quantised", "hcc", {"bvh_h": bvh_q}),
+                ("nosort_per_ray", "nosort", {"schedule": "per_ray"}), ("hcc_per_ray", "hcc", {"schedule": "per_ray"}),
+                ("twopoint_per_ray", "twopoint", {"schedule": "per_ray"})]
     for name, method, kw in variants:
         r = timed(method, max(3, args.steps // 2), args.warmup, **kw)
         t_max = reduce_max(r["total_ms"], world)
@@ -344,6 +347,7 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name + f" ({n} secondary rays), HCC cut {C}, {K}-bit keys, {args.layout} BVH nodes",
                    "bvh_layout": args.layout, "gather": "fused into the trace (rays fetched through the sorted ids)",
+                   "trace_schedule": "auto (closest hit: persistent warps with ray replacement)",
                    "rays": n, "triangles": int(w.tris.shape[0]), "cut_size": C, "key_bits": K, "lambda": 0.125,
                    "l2": f"inputs larger than L2 ({n * 32 / 1e6:.0f} MB of rays per step)",
                    "parallelism": f"replica per GPU x{world}"},
@@ -360,7 +364,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": 9 * args.steps,
         "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 2), "unit": "Tops/s",
                      "frac": round(achieved / alu_peak, 3), "traffic": recorded_traffic(),
-                     "kernel": f"k_trace (closest hit, HCC order, {args.layout} nodes)",
+                     "kernel": f"k_trace_pool (closest hit, HCC order, {args.layout} nodes, ray replacement)",
                      "peak_source": f"{SMS} SMs x {LANES_PER_SM} lanes x {clk_mhz:.0f} MHz"},
         "stages": stages,
         "hbm_peak_gbs": hbm, "hbm_peak_source": peak_kind,
@@ -486,6 +490,87 @@ def run_keylen_sweep(args):
            "unit": "Mrays/s", "config": {"workload": w.name + f" ({n} secondary rays)", "bvh_layout": args.layout,
                                          "hcc_cut_size": "= key bits"},
            "nosort": nosort, "points": points}
+    hcc.hcc_bvh_destroy(bvh)
+    hcc.hcc_destroy(ctx)
+    print(json.dumps(out), flush=True)
+
+
+def run_methods_sweep(args):
+    """Method study (Sec. 6, Tables 1, 2 and 4): every ordering on the same 1080p
+    wavefront -- NoSort, TwoPoint, Origin, Origin-Direction, HCC (cut 32), MLHCC16
+    (8 + 8), MLHCC32 (16 + 16), regular grid (32 cells) and PPC (an upper bound) --
+    for the secondary rays (closest hit) and the shadow rays (any hit); per method
+    the encode, sort and trace times, the trace speedup over NoSort, ANC, distinct
+    keys and the trace's warp execution efficiency."""
+    import torch
+    from paper_2305_16652_gb300 import build, hcc
+    build()
+    dev = torch.device("cuda", 0)
+    w = make_workload(1, args.quick, shadow=True)
+    ctx = hcc.hcc_create(0)
+    bvh = hcc.hcc_bvh_upload(ctx, w.bvh, layout=args.layout)
+
+    def tm(f, reps=5):
+        ts = []
+        for _ in range(reps + 2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            f()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts[2:])
+
+    def eff(c):
+        return round(c["node_visits"] / (32.0 * max(1, c["warp_node_steps"])), 4)
+
+    cuts = {"hcc": hcc.hcc_select_cut(ctx, bvh, 32, 0.125),
+            "mlhcc16": hcc.hcc_select_cut_ml(ctx, bvh, 8, 8, 0.125),
+            "mlhcc32": hcc.hcc_select_cut_ml(ctx, bvh, 16, 16, 0.125),
+            "grid": hcc.hcc_select_grid(ctx, bvh, 32)}
+    methods = [("twopoint", "twopoint", 32, None), ("origin", "origin", 32, None),
+               ("origin_dir", "origin_dir", 32, None), ("hcc", "hcc", 32, "hcc"),
+               ("mlhcc16", "mlhcc", 16, "mlhcc16"), ("mlhcc32", "mlhcc", 32, "mlhcc32"),
+               ("regular_grid", "hcc", 32, "grid")]
+    if args.layout == "exact":
+        methods.append(("ppc", "ppc", 32, None))
+    out = {"metric": "method study: Mrays/s, trace speedup over NoSort, ANC and warp efficiency per ordering",
+           "unit": "Mrays/s", "config": {"workload": w.name, "bvh_layout": args.layout}}
+    for label, rays, any_hit in (("secondary", w.rays, False), ("shadow", w.shadow, True)):
+        if rays is None:
+            continue
+        n = rays.n
+        hcc.hcc_reserve(ctx, n, 32)
+        org = torch.from_numpy(rays.org).to(dev)
+        dir_ = torch.from_numpy(rays.dir).to(dev)
+        perm = torch.empty(n, dtype=torch.int32, device=dev)
+        keys = torch.empty(n, dtype=torch.int32, device=dev)
+        hits = torch.empty((n, 4), dtype=torch.int32, device=dev)
+        c0 = hcc.hcc_trace_counts(ctx, bvh, org, dir_, any_hit=any_hit)
+        t0 = tm(lambda: hcc.hcc_trace(ctx, bvh, org, dir_, hits, any_hit=any_hit))
+        rows = {"nosort": {"trace_ms": round(t0, 4), "mrays_s": round(n / (t0 * 1e3), 1),
+                           "warp_efficiency": eff(c0), "node_visits_per_ray": round(c0["node_visits"] / n, 3)}}
+        for name, method, k, cut_name in methods:
+            cut = cuts[cut_name] if cut_name else None
+            te = tm(lambda: hcc.hcc_encode(ctx, method, bvh, cut, org, dir_, k, keys))
+            ts = tm(lambda: hcc.hcc_sort(ctx, keys, k, n, perm))
+            tt = tm(lambda: hcc.hcc_trace_sorted(ctx, bvh, org, dir_, perm, hits, any_hit=any_hit))
+            st = hcc.hcc_key_stats(ctx, keys, k, perm, n)
+            c = hcc.hcc_trace_counts(ctx, bvh, org, dir_, perm=perm, any_hit=any_hit)
+            hcc.hcc_sync(ctx)
+            tot = te + ts + tt
+            rows[name] = {"key_bits": k, "encode_ms": round(te, 4), "sort_ms": round(ts, 4), "trace_ms": round(tt, 4),
+                          "total_ms": round(tot, 4), "mrays_s": round(n / (tot * 1e3), 1),
+                          "trace_mrays_s": round(n / (tt * 1e3), 1),
+                          "trace_speedup_vs_nosort": round(t0 / tt, 3), "speedup_vs_nosort": round(t0 / tot, 3),
+                          "overhead_pct_of_trace": round(100 * (te + ts) / tt, 1), "anc": round(st["anc"], 4),
+                          "distinct_keys": st["distinct"], "warp_efficiency": eff(c),
+                          "node_visits_per_ray": round(c["node_visits"] / n, 3)}
+        out[label] = {"rays": n, "any_hit": any_hit, "methods": rows}
+        del org, dir_, perm, keys, hits
+        torch.cuda.empty_cache()
+    for c in cuts.values():
+        hcc.hcc_cut_destroy(c)
     hcc.hcc_bvh_destroy(bvh)
     hcc.hcc_destroy(ctx)
     print(json.dumps(out), flush=True)
@@ -816,7 +901,7 @@ def main(argv=None):
     ap.add_argument("--ref-sample", type=int, default=300_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", choices=["trace-small", "sort-16m"], help="run a small profiling case and exit")
-    ap.add_argument("--sweep", choices=["keylen", "batch", "serve"],
+    ap.add_argument("--sweep", choices=["keylen", "batch", "serve", "methods"],
                     help="run a study instead of the headline benchmark")
     ap.add_argument("--slots", type=int, default=4, help="serving: requests on the GPU at once")
     ap.add_argument("--serve-requests", type=int, default=1000, help="serving: requests per run")
@@ -829,6 +914,8 @@ def main(argv=None):
         return run_batch_sweep(args)
     if args.sweep == "serve":
         return run_serve_sweep(args)
+    if args.sweep == "methods":
+        return run_methods_sweep(args)
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = dist_env()
     if world > 1:

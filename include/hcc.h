@@ -130,6 +130,24 @@ hcc_status hcc_set_stream(hcc_ctx *ctx, void *stream);
  * cudaMalloc).  Errors: INVALID_ARG, OOM. */
 hcc_status hcc_reserve(hcc_ctx *ctx, uint64_t max_n, uint32_t max_key_bits);
 
+/*
+ * How the context's traces schedule rays on warps.  PER_RAY: one thread per
+ * ray slot for the whole traversal (the plain tracer).  REFILL: persistent
+ * warps take ray slots from a counter in increasing order, and after each
+ * traversal round the lanes whose ray has finished take new slots once 16
+ * lanes of the warp are idle (Aila & Laine 2009, "replacing terminated
+ * rays").  AUTO (the default): REFILL for closest-hit traces, PER_RAY for
+ * any-hit traces (measured faster for each on GB300).  Results do not depend
+ * on the schedule, except which hit an any-hit query reports.
+ */
+typedef enum hcc_trace_schedule {
+    HCC_TRACE_AUTO = 0,
+    HCC_TRACE_PER_RAY = 1,
+    HCC_TRACE_REFILL = 2
+} hcc_trace_schedule;
+
+hcc_status hcc_set_trace_schedule(hcc_ctx *ctx, hcc_trace_schedule schedule);
+
 /* Wait for all work queued on the context's stream, then read and clear the
  * device error word: STACK_OVERFLOW or TIMEOUT if a kernel reported one
  * since the last hcc_sync, INVALID_ARG if a gather or scatter met an index

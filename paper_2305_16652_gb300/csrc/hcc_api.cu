@@ -25,7 +25,9 @@ struct DevBuf {
 struct hcc_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
-    uint32_t *d_err = nullptr;
+    uint32_t *d_err = nullptr;                 // device error word (16-byte allocation) ...
+    unsigned long long *d_work = nullptr;      // ... whose second half is the trace's slot counter
+    hcc_trace_schedule schedule = HCC_TRACE_AUTO;
     std::string last_error;
     DevBuf sort_scratch;
     DevBuf keys, perm;                          // hcc_run
@@ -309,6 +311,12 @@ void cut_view(const hcc_cut *c, const float4 **boxes, uint32_t *on_device, int *
 
 }  // namespace hcc
 
+// Slot counter for the persistent trace, or NULL for one thread per ray.
+static unsigned long long *trace_work(const hcc_ctx *ctx, int any_hit) {
+    const bool refill = ctx->schedule == HCC_TRACE_REFILL || (ctx->schedule == HCC_TRACE_AUTO && !any_hit);
+    return refill ? ctx->d_work : nullptr;
+}
+
 // ================================================================== C ABI
 
 extern "C" {
@@ -342,17 +350,26 @@ hcc_status hcc_create(hcc_ctx **out, int device, void *stream) {
     c->device = device;
     c->stream = static_cast<cudaStream_t>(stream);
     DeviceGuard g(device);
-    if (cudaMalloc(&c->d_err, sizeof(uint32_t)) != cudaSuccess) {
+    if (cudaMalloc(&c->d_err, 16) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return HCC_ERR_OOM;
     }
-    if (cudaMemset(c->d_err, 0, sizeof(uint32_t)) != cudaSuccess) {
+    c->d_work = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(c->d_err) + 8);
+    if (cudaMemset(c->d_err, 0, 16) != cudaSuccess) {
         cudaFree(c->d_err);
         delete c;
         return HCC_ERR_CUDA;
     }
     *out = c;
+    return HCC_OK;
+}
+
+hcc_status hcc_set_trace_schedule(hcc_ctx *ctx, hcc_trace_schedule schedule) {
+    if (!ctx) return HCC_ERR_INVALID_ARG;
+    if (schedule != HCC_TRACE_AUTO && schedule != HCC_TRACE_PER_RAY && schedule != HCC_TRACE_REFILL)
+        return fail(ctx, HCC_ERR_INVALID_ARG, "unknown trace schedule");
+    ctx->schedule = schedule;
     return HCC_OK;
 }
 
@@ -943,6 +960,7 @@ hcc_status hcc_trace(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *rays, int
     a.scatter = scatter;
     a.hits = reinterpret_cast<int4 *>(hits);
     a.err = ctx->d_err;
+    a.work = trace_work(ctx, any_hit);
     a.counts = nullptr;
     a.scenes = nullptr;
     a.offsets = nullptr;
@@ -974,6 +992,7 @@ hcc_status hcc_trace_sorted(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *ra
     a.scatter = perm;
     a.hits = reinterpret_cast<int4 *>(hits);
     a.err = ctx->d_err;
+    a.work = trace_work(ctx, any_hit);
     a.counts = nullptr;
     a.scenes = nullptr;
     a.offsets = nullptr;
@@ -1010,6 +1029,7 @@ hcc_status hcc_trace_counts(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *ra
     a.scatter = perm;
     a.hits = reinterpret_cast<int4 *>(tmp.p);
     a.err = ctx->d_err;
+    a.work = trace_work(ctx, any_hit);
     a.counts = cnt;
     a.scenes = nullptr;
     a.offsets = nullptr;
@@ -1112,13 +1132,13 @@ hcc_status hcc_batch_run(hcc_ctx *ctx, const hcc_batch *b, hcc_method method, co
         return fail(ctx, HCC_ERR_INVALID_ARG, "key_bits plus %u scene bits must fit 64 bits", b->scene_bits);
     DeviceGuard g(ctx->device);
     TraceArgs a;
-    std::memset(&a, 0, sizeof a);
     a.layout = b->layout;
     a.org = reinterpret_cast<const float4 *>(rays->org_tmin);
     a.dir = reinterpret_cast<const float4 *>(rays->dir_tmax);
     a.n = n;
     a.hits = reinterpret_cast<int4 *>(hits);
     a.err = ctx->d_err;
+    a.work = trace_work(ctx, any_hit);
     a.scenes = b->d_scenes;
     a.offsets = b->d_offsets;
     a.num_scenes = b->num_scenes;

@@ -115,22 +115,23 @@ cudaError_t launch_gather(cudaStream_t s, const float4 *in_org, const float4 *in
                           const uint32_t *perm, float4 *out_org, float4 *out_dir, uint64_t n, uint32_t *err);
 
 struct TraceArgs {
-    const uint4 *nodes;  // 2 (quantised) or 4 (exact) per node
-    int layout;          // 0 = 32-byte quantised, 1 = 64-byte exact
-    const float4 *tris;  // 3 per triangle
-    uint32_t root_ref;
-    const float4 *org;
-    const float4 *dir;
-    uint64_t n;
-    const uint32_t *gather;   // ray j is read from org/dir[gather[j]] (NULL = j)
-    const uint32_t *scatter;  // its hit goes to hits[scatter[j]] (NULL = j)
-    int4 *hits;
-    uint32_t *err;
-    unsigned long long *counts;  // diagnostic (NULL = off): node visits, triangle tests,
+    const uint4 *nodes = nullptr;  // 2 (quantised) or 4 (exact) per node
+    int layout = 0;          // 0 = 32-byte quantised, 1 = 64-byte exact
+    const float4 *tris = nullptr;  // 3 per triangle
+    uint32_t root_ref = 0;
+    const float4 *org = nullptr;
+    const float4 *dir = nullptr;
+    uint64_t n = 0;
+    const uint32_t *gather = nullptr;   // ray j is read from org/dir[gather[j]] (NULL = j)
+    const uint32_t *scatter = nullptr;  // its hit goes to hits[scatter[j]] (NULL = j)
+    int4 *hits = nullptr;
+    uint32_t *err = nullptr;
+    unsigned long long *counts = nullptr;  // diagnostic (NULL = off): node visits, triangle tests,
                                  // warp node steps, warp leaf steps
-    const SceneDesc *scenes;     // batch mode (NULL = single BVH above)
-    const uint64_t *offsets;     // scene s owns rays [offsets[s], offsets[s+1])
-    uint32_t num_scenes;
+    const SceneDesc *scenes = nullptr;     // batch mode (NULL = single BVH above)
+    const uint64_t *offsets = nullptr;     // scene s owns rays [offsets[s], offsets[s+1])
+    uint32_t num_scenes = 0;
+    unsigned long long *work = nullptr;    // slot counter of the persistent trace (NULL: one thread per slot)
 };
 
 cudaError_t launch_trace(cudaStream_t s, const TraceArgs &a, int any_hit);

@@ -54,7 +54,7 @@ struct Request {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
-    uint32_t *d_err = nullptr;
+    uint32_t *d_err = nullptr;  // error word (16-byte allocation; the second half is the trace's slot counter)
     uint32_t *h_err = nullptr;  // page-locked copy of d_err, written by the request's last copy
     Request *req = nullptr;     // running request, nullptr = free
     hcc_server *owner = nullptr;
@@ -134,7 +134,6 @@ hcc_status launch_request(hcc_server *s, const Request &r, Slot &sl) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(dir, r.dir, n * 16, cudaMemcpyHostToDevice, st);
     const hcc::SceneDesc &sc = s->scenes[r.scene];
     hcc::TraceArgs a;
-    std::memset(&a, 0, sizeof a);
     a.nodes = sc.nodes;
     a.layout = s->layout;
     a.tris = sc.tris;
@@ -144,6 +143,8 @@ hcc_status launch_request(hcc_server *s, const Request &r, Slot &sl) {
     a.n = n;
     a.hits = static_cast<int4 *>(d_hits);
     a.err = sl.d_err;
+    // closest hit: persistent trace with ray replacement; any hit: one thread per ray
+    a.work = r.any_hit ? nullptr : reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(sl.d_err) + 8);
     if (e == cudaSuccess && sorts) {
         uint32_t *perm = static_cast<uint32_t *>(d_perm);
         switch (s->method) {
@@ -344,7 +345,7 @@ hcc_status hcc_server_create(int device, uint32_t num_scenes, const hcc_bvh *con
         sl.owner = s;
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess) sl.stream = nullptr;
         if (cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) sl.done = nullptr;
-        if (cudaMalloc(&sl.d_err, sizeof(uint32_t)) != cudaSuccess) sl.d_err = nullptr;
+        if (cudaMalloc(&sl.d_err, 16) != cudaSuccess) sl.d_err = nullptr;
         if (cudaMallocHost(&sl.h_err, sizeof(uint32_t)) != cudaSuccess) sl.h_err = nullptr;
         if (!sl.stream || !sl.done || !sl.d_err || !sl.h_err) return fail(HCC_ERR_CUDA);
         if (cudaMemset(sl.d_err, 0, sizeof(uint32_t)) != cudaSuccess) return fail(HCC_ERR_CUDA);

@@ -13,6 +13,8 @@
 // Triangle arithmetic is the canonical Moller-Trumbore sequence with explicit
 // round-to-nearest intrinsics (built with --fmad=false), so the (t, u, v) of
 // a triangle are the same bit patterns on every run and in every ray order.
+#include <algorithm>
+
 #include "hcc_internal.cuh"
 
 namespace hcc {
@@ -23,6 +25,7 @@ constexpr int STACK = HCC_TRACE_STACK;
 // 1 + 2 * gamma(3), gamma(n) = n u / (1 - n u), u = 2^-24
 constexpr float ROBUST_FAR = 1.0000003576279f;
 constexpr float PRUNE_SLACK = 1.0f + 1.0f / 65536.0f;
+constexpr uint32_t REFILL_MIN = 16;  // idle lanes that make a warp take new rays
 
 __device__ __forceinline__ float byte_to_float(uint32_t w, uint32_t sel) {
     // 0x4B0000bb as float is 2^23 + bb exactly
@@ -137,195 +140,316 @@ struct Counters {
     uint32_t nodes = 0, tris = 0, warp_nodes = 0, warp_leaves = 0;
 };
 
-// Traversal loop ("while-while" with postponed leaves, Aila & Laine 2009):
-// a lane that reaches a leaf parks it and keeps descending until every lane
-// of the warp holds a leaf, so triangle tests run with full warps; the
+// Traversal state of one ray: the ray, the best hit so far, the node being
+// descended and the parked leaf.  The stack lives beside it in the kernel.
+struct RayState {
+    Ray r;
+    float best_t, best_u, best_v, tcap;  // tcap: best_t widened by the prune slack
+    int32_t best_prim;
+    int sp;
+    uint32_t node, leaf;
+    bool overflow;
+};
+
+__device__ __forceinline__ void ray_init(RayState &s, const float4 o4, const float4 d4, uint32_t root_ref) {
+    s.r.ox = o4.x;
+    s.r.oy = o4.y;
+    s.r.oz = o4.z;
+    s.r.tmin = o4.w;
+    s.r.dx = d4.x;
+    s.r.dy = d4.y;
+    s.r.dz = d4.z;
+    s.r.tmax = d4.w;
+    s.r.ix = safe_inv(d4.x);
+    s.r.iy = safe_inv(d4.y);
+    s.r.iz = safe_inv(d4.z);
+    s.best_t = s.r.tmax;
+    s.best_u = s.best_v = 0.0f;
+    s.best_prim = -1;
+    s.tcap = s.r.tmax;
+    s.sp = 0;
+    s.overflow = false;
+    s.node = root_ref;
+    s.leaf = REF_NONE;
+    if (s.node & REF_LEAF) {
+        s.leaf = s.node;
+        s.node = REF_NONE;
+    }
+}
+
+__device__ __forceinline__ bool ray_done(const RayState &s) { return s.node == REF_NONE && s.leaf == REF_NONE; }
+
+// Next pending subtree that can still hold a closer hit, or REF_NONE.
+__device__ __forceinline__ uint32_t ray_pop(RayState &s, const uint32_t *st_ref, const float *st_t) {
+    while (s.sp > 0) {
+        --s.sp;
+        if (st_t[s.sp] <= s.tcap) return st_ref[s.sp];
+    }
+    return REF_NONE;
+}
+
+// One round of the traversal loop ("while-while" with postponed leaves,
+// Aila & Laine 2009): descend internal nodes until every lane of the warp
+// holds a leaf (a lane that reaches a leaf parks it and keeps descending),
+// then test the parked leaf and any leaf that is next on the stack.  The
 // nearer child is visited first and the farther one is pushed with its
 // entry distance, which lets a pop skip subtrees beyond the best hit.
-// Returns the hit record {prim, t, u, v} (prim -1 and t = +inf on a miss);
-// sets overflow if the ray needed more than STACK entries.
 template <bool ANY, bool COUNT, int LAYOUT>
-__device__ __forceinline__ int4 trace_ray(const uint4 *__restrict__ nodes, const float4 *__restrict__ tris,
-                                          uint32_t root_ref, const float4 o4, const float4 d4, Counters &cn,
-                                          bool &overflow) {
+__device__ __forceinline__ void ray_round(RayState &s, uint32_t *st_ref, float *st_t, const uint4 *__restrict__ nodes,
+                                          const float4 *__restrict__ tris, Counters &cn) {
     const uint32_t lane = threadIdx.x & 31;
-    Ray r;
-    r.ox = o4.x;
-    r.oy = o4.y;
-    r.oz = o4.z;
-    r.tmin = o4.w;
-    r.dx = d4.x;
-    r.dy = d4.y;
-    r.dz = d4.z;
-    r.tmax = d4.w;
-    r.ix = safe_inv(d4.x);
-    r.iy = safe_inv(d4.y);
-    r.iz = safe_inv(d4.z);
-
-    float best_t = r.tmax, best_u = 0.0f, best_v = 0.0f;
-    int32_t best_prim = -1;
-    float tcap = r.tmax;  // best_t widened by the prune slack
-    uint32_t st_ref[STACK];
-    float st_t[STACK];
-    int sp = 0;
-    overflow = false;
-    // next pending subtree that can still hold a closer hit, or REF_NONE
-    auto pop = [&]() -> uint32_t {
-        while (sp > 0) {
-            --sp;
-            if (st_t[sp] <= tcap) return st_ref[sp];
+    // internal nodes: descend until every lane has a leaf parked
+    while (s.node != REF_NONE && !(s.node & REF_LEAF)) {
+        ChildBoxes c;
+        if (LAYOUT == 0)
+            fetch_quant8(nodes, s.node, c);
+        else
+            fetch_exact(nodes, s.node, c);
+        if (COUNT) {
+            ++cn.nodes;  // this lane's node visit; the lowest active lane counts the warp's step
+            if (lane == (uint32_t)(__ffs(__activemask()) - 1)) ++cn.warp_nodes;
         }
-        return REF_NONE;
-    };
-    uint32_t node = root_ref, leaf = REF_NONE;
-    if (node & REF_LEAF) {
-        leaf = node;
-        node = REF_NONE;
-    }
-    while (node != REF_NONE || leaf != REF_NONE) {
-        // internal nodes: descend until every lane has a leaf parked
-        while (node != REF_NONE && !(node & REF_LEAF)) {
-            ChildBoxes c;
-            if (LAYOUT == 0)
-                fetch_quant8(nodes, node, c);
-            else
-                fetch_exact(nodes, node, c);
-            if (COUNT) {
-                ++cn.nodes;  // this lane's node visit; the lowest active lane counts the warp's step
-                if (lane == (uint32_t)(__ffs(__activemask()) - 1)) ++cn.warp_nodes;
-            }
-            float tn0, tf0, tn1, tf1;
-            slab(r, c.lo0x, c.lo0y, c.lo0z, c.hi0x, c.hi0y, c.hi0z, tcap, tn0, tf0);
-            slab(r, c.lo1x, c.lo1y, c.lo1z, c.hi1x, c.hi1y, c.hi1z, tcap, tn1, tf1);
-            const bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
-            if (h0 && h1) {
-                const bool first0 = tn0 <= tn1;
-                if (sp == STACK) {
-                    overflow = true;
-                    node = leaf = REF_NONE;
-                    break;
-                }
-                st_ref[sp] = first0 ? c.ref1 : c.ref0;
-                st_t[sp] = first0 ? tn1 : tn0;
-                ++sp;
-                node = first0 ? c.ref0 : c.ref1;
-            } else if (h0) {
-                node = c.ref0;
-            } else if (h1) {
-                node = c.ref1;
-            } else {
-                node = pop();
-            }
-            if (node != REF_NONE && (node & REF_LEAF) && leaf == REF_NONE) {
-                leaf = node;
-                node = pop();
-            }
-            if (__all_sync(__activemask(), leaf != REF_NONE)) break;
-        }
-        // leaves: the parked one, then any leaf that is next on the stack
-        while (leaf != REF_NONE) {
-            if (COUNT && lane == (uint32_t)(__ffs(__activemask()) - 1)) ++cn.warp_leaves;
-            const uint32_t first = leaf & REF_TRI_MASK, cnt = ((leaf >> 29) & 3u) + 1u;
-            bool hit_any = false;
-            for (uint32_t k = 0; k < cnt; ++k) {
-                const float4 *rec = tris + 3 * (size_t)(first + k);
-                const float4 A = __ldg(rec), E1 = __ldg(rec + 1), E2 = __ldg(rec + 2);
-                if (COUNT) ++cn.tris;
-                float t, u, v;
-                if (!intersect(r, A, E1, E2, t, u, v)) continue;
-                const int32_t prim = __float_as_int(A.w);
-                if (best_prim < 0 || t < best_t || (t == best_t && prim < best_prim)) {
-                    best_t = t;
-                    best_u = u;
-                    best_v = v;
-                    best_prim = prim;
-                    tcap = __fmul_rn(t, PRUNE_SLACK);
-                }
-                hit_any = true;
-                if (ANY) break;
-            }
-            if (ANY && hit_any) {
-                node = leaf = REF_NONE;
+        float tn0, tf0, tn1, tf1;
+        slab(s.r, c.lo0x, c.lo0y, c.lo0z, c.hi0x, c.hi0y, c.hi0z, s.tcap, tn0, tf0);
+        slab(s.r, c.lo1x, c.lo1y, c.lo1z, c.hi1x, c.hi1y, c.hi1z, s.tcap, tn1, tf1);
+        const bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
+        if (h0 && h1) {
+            const bool first0 = tn0 <= tn1;
+            if (s.sp == STACK) {
+                s.overflow = true;
+                s.node = s.leaf = REF_NONE;
                 break;
             }
-            leaf = REF_NONE;
-            if (node != REF_NONE && (node & REF_LEAF)) {
-                leaf = node;
-                node = pop();
+            st_ref[s.sp] = first0 ? c.ref1 : c.ref0;
+            st_t[s.sp] = first0 ? tn1 : tn0;
+            ++s.sp;
+            s.node = first0 ? c.ref0 : c.ref1;
+        } else if (h0) {
+            s.node = c.ref0;
+        } else if (h1) {
+            s.node = c.ref1;
+        } else {
+            s.node = ray_pop(s, st_ref, st_t);
+        }
+        if (s.node != REF_NONE && (s.node & REF_LEAF) && s.leaf == REF_NONE) {
+            s.leaf = s.node;
+            s.node = ray_pop(s, st_ref, st_t);
+        }
+        if (__all_sync(__activemask(), s.leaf != REF_NONE)) break;
+    }
+    // leaves: the parked one, then any leaf that is next on the stack
+    while (s.leaf != REF_NONE) {
+        if (COUNT && lane == (uint32_t)(__ffs(__activemask()) - 1)) ++cn.warp_leaves;
+        const uint32_t first = s.leaf & REF_TRI_MASK, cnt = ((s.leaf >> 29) & 3u) + 1u;
+        bool hit_any = false;
+        for (uint32_t k = 0; k < cnt; ++k) {
+            const float4 *rec = tris + 3 * (size_t)(first + k);
+            const float4 A = __ldg(rec), E1 = __ldg(rec + 1), E2 = __ldg(rec + 2);
+            if (COUNT) ++cn.tris;
+            float t, u, v;
+            if (!intersect(s.r, A, E1, E2, t, u, v)) continue;
+            const int32_t prim = __float_as_int(A.w);
+            if (s.best_prim < 0 || t < s.best_t || (t == s.best_t && prim < s.best_prim)) {
+                s.best_t = t;
+                s.best_u = u;
+                s.best_v = v;
+                s.best_prim = prim;
+                s.tcap = __fmul_rn(t, PRUNE_SLACK);
             }
+            hit_any = true;
+            if (ANY) break;
+        }
+        if (ANY && hit_any) {
+            s.node = s.leaf = REF_NONE;
+            break;
+        }
+        s.leaf = REF_NONE;
+        if (s.node != REF_NONE && (s.node & REF_LEAF)) {
+            s.leaf = s.node;
+            s.node = ray_pop(s, st_ref, st_t);
         }
     }
-    if (overflow) best_prim = -1;
+}
+
+// The hit record {prim, t, u, v} (prim -1 and t = +inf on a miss or a
+// stack overflow).
+__device__ __forceinline__ int4 ray_result(const RayState &s) {
+    const bool miss = s.overflow || s.best_prim < 0;
     int4 out;
-    out.x = best_prim;
-    out.y = __float_as_int(best_prim < 0 ? __int_as_float(0x7F800000) : best_t);
-    out.z = __float_as_int(best_prim < 0 ? 0.0f : best_u);
-    out.w = __float_as_int(best_prim < 0 ? 0.0f : best_v);
+    out.x = miss ? -1 : s.best_prim;
+    out.y = __float_as_int(miss ? __int_as_float(0x7F800000) : s.best_t);
+    out.z = __float_as_int(miss ? 0.0f : s.best_u);
+    out.w = __float_as_int(miss ? 0.0f : s.best_v);
     return out;
 }
 
-// One thread per ray slot i: the ray is org/dir[gather[i]] (or i), its record
-// goes to hits[scatter[i]] (or i).  MULTI: the ray's BVH is that of its scene
-// in a batch (a.scenes, ray ranges a.offsets).  COUNT = true is a diagnostic
-// variant that also adds up work counters into a.counts (never timed).
-template <bool ANY, bool COUNT, int LAYOUT, bool MULTI>
-__global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
-    const uint64_t i = (uint64_t)blockIdx.x * TRACE_BLOCK + threadIdx.x;
-    if (i >= a.n) return;
+template <bool COUNT>
+__device__ __forceinline__ void add_counts(const TraceArgs &a, const Counters &cn) {
+    if (COUNT) {
+        if (cn.nodes) atomicAdd(a.counts, (unsigned long long)cn.nodes);
+        if (cn.tris) atomicAdd(a.counts + 1, (unsigned long long)cn.tris);
+        if (cn.warp_nodes) atomicAdd(a.counts + 2, (unsigned long long)cn.warp_nodes);
+        if (cn.warp_leaves) atomicAdd(a.counts + 3, (unsigned long long)cn.warp_leaves);
+    }
+}
+
+// Reads ray slot i: the ray is org/dir[gather[i]] (or i).  Returns false
+// (and reports) for an out-of-range permutation entry.
+template <bool MULTI>
+__device__ __forceinline__ bool fetch_ray(const TraceArgs &a, uint64_t i, float4 &o4, float4 &d4,
+                                          const uint4 *&nodes, const float4 *&tris, uint32_t &root) {
     uint64_t src = i;
     if (a.gather) {
         src = a.gather[i];
         if (src >= a.n) {  // invalid permutation entry: report, never read out of bounds
             atomicOr(a.err, ERR_INDEX);
-            return;
+            return false;
         }
     }
-    const float4 o4 = __ldcs(a.org + src), d4 = __ldcs(a.dir + src);
-    const uint4 *nodes = a.nodes;
-    const float4 *tris = a.tris;
-    uint32_t root = a.root_ref;
+    o4 = __ldcs(a.org + src);
+    d4 = __ldcs(a.dir + src);
+    nodes = a.nodes;
+    tris = a.tris;
+    root = a.root_ref;
     if (MULTI) {
         const SceneDesc &sc = a.scenes[scene_of(a.offsets, a.num_scenes, src)];
         nodes = sc.nodes;
         tris = sc.tris;
         root = sc.root_ref;
     }
-    Counters cn;
-    bool overflow;
-    const int4 out = trace_ray<ANY, COUNT, LAYOUT>(nodes, tris, root, o4, d4, cn, overflow);
-    if (overflow) atomicOr(a.err, ERR_STACK);
+    return true;
+}
+
+// Writes the record of ray slot i to hits[scatter[i]] (or i).
+__device__ __forceinline__ void store_hit(const TraceArgs &a, uint64_t i, const RayState &s) {
+    if (s.overflow) atomicOr(a.err, ERR_STACK);
     const uint64_t dst = a.scatter ? (uint64_t)a.scatter[i] : i;
     if (dst < a.n)
-        __stcs(a.hits + dst, out);
+        __stcs(a.hits + dst, ray_result(s));
     else  // invalid scatter entry: report, never write out of bounds
         atomicOr(a.err, ERR_INDEX);
-    if (COUNT) {
-        atomicAdd(a.counts, (unsigned long long)cn.nodes);
-        atomicAdd(a.counts + 1, (unsigned long long)cn.tris);
-        if (cn.warp_nodes) atomicAdd(a.counts + 2, (unsigned long long)cn.warp_nodes);
-        if (cn.warp_leaves) atomicAdd(a.counts + 3, (unsigned long long)cn.warp_leaves);
+}
+
+// One thread per ray slot.  MULTI: the ray's BVH is that of its scene in a
+// batch (a.scenes, ray ranges a.offsets).  COUNT = true is a diagnostic
+// variant that also adds up work counters into a.counts (never timed).
+template <bool ANY, bool COUNT, int LAYOUT, bool MULTI>
+__global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
+    const uint64_t i = (uint64_t)blockIdx.x * TRACE_BLOCK + threadIdx.x;
+    if (i >= a.n) return;
+    float4 o4, d4;
+    const uint4 *nodes;
+    const float4 *tris;
+    uint32_t root;
+    if (!fetch_ray<MULTI>(a, i, o4, d4, nodes, tris, root)) return;
+    RayState s;
+    uint32_t st_ref[STACK];
+    float st_t[STACK];
+    Counters cn;
+    ray_init(s, o4, d4, root);
+    while (!ray_done(s)) ray_round<ANY, COUNT, LAYOUT>(s, st_ref, st_t, nodes, tris, cn);
+    store_hit(a, i, s);
+    add_counts<COUNT>(a, cn);
+}
+
+// Persistent variant with ray replacement (Aila & Laine 2009, "replacing
+// terminated rays"): each warp takes ray slots from a global counter, runs
+// traversal rounds, and after each round the lanes whose ray has finished
+// take new slots (all at once, one atomic per warp) as soon as REFILL_MIN of
+// them are idle or none is busy.  Slots are handed out in increasing order,
+// so lanes of a warp trace neighbouring slots -- in sorted order, rays with
+// equal keys.  Every ray's record is the same as in k_trace: a ray's own
+// traversal does not depend on which rays share its warp, except for which
+// of several hits an any-hit query returns first.
+template <bool ANY, bool COUNT, int LAYOUT, bool MULTI>
+__global__ void __launch_bounds__(TRACE_BLOCK, 10) k_trace_pool(TraceArgs a) {
+    constexpr uint32_t FULL = 0xFFFFFFFFu;
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    RayState s;
+    uint32_t st_ref[STACK];
+    float st_t[STACK];
+    Counters cn;
+    const uint4 *nodes = a.nodes;
+    const float4 *tris = a.tris;
+    uint64_t slot = 0;
+    bool have = false, exhausted = false;
+    for (;;) {
+        const bool want = !have && !exhausted;
+        const uint32_t need = __ballot_sync(FULL, want);
+        const uint32_t busy = __ballot_sync(FULL, have);
+        if (need && (busy == 0 || (uint32_t)__popc(need) >= REFILL_MIN)) {
+            const int leader = __ffs(need) - 1;
+            unsigned long long base = 0;
+            if ((int)lane == leader) base = atomicAdd(a.work, (unsigned long long)__popc(need));
+            base = __shfl_sync(FULL, base, leader);
+            if (want) {
+                slot = base + __popc(need & lt);
+                if (slot < a.n) {
+                    float4 o4, d4;
+                    uint32_t root;
+                    if (fetch_ray<MULTI>(a, slot, o4, d4, nodes, tris, root)) {
+                        ray_init(s, o4, d4, root);
+                        have = true;
+                    }
+                } else {
+                    exhausted = true;
+                }
+            }
+        }
+        if (!__any_sync(FULL, have)) {
+            if (__all_sync(FULL, exhausted)) break;
+            continue;
+        }
+        if (have) {
+            ray_round<ANY, COUNT, LAYOUT>(s, st_ref, st_t, nodes, tris, cn);
+            if (ray_done(s)) {
+                store_hit(a, slot, s);
+                have = false;
+            }
+        }
     }
+    add_counts<COUNT>(a, cn);
 }
 
 }  // namespace
 
 cudaError_t launch_trace(cudaStream_t s, const TraceArgs &a, int any_hit) {
     if (a.n == 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((a.n + TRACE_BLOCK - 1) / TRACE_BLOCK);
-    const bool count = a.counts != nullptr, multi = a.scenes != nullptr;
-#define HCC_TRACE_LAUNCH(ANY, CNT)                                                  \
-    do {                                                                            \
-        if (multi) {                                                                \
-            if (a.layout == 0)                                                      \
-                k_trace<ANY, CNT, 0, true><<<blocks, TRACE_BLOCK, 0, s>>>(a);       \
-            else                                                                    \
-                k_trace<ANY, CNT, 1, true><<<blocks, TRACE_BLOCK, 0, s>>>(a);       \
-        } else {                                                                    \
-            if (a.layout == 0)                                                      \
-                k_trace<ANY, CNT, 0, false><<<blocks, TRACE_BLOCK, 0, s>>>(a);      \
-            else                                                                    \
-                k_trace<ANY, CNT, 1, false><<<blocks, TRACE_BLOCK, 0, s>>>(a);      \
-        }                                                                           \
+    const bool count = a.counts != nullptr, multi = a.scenes != nullptr, pool = a.work != nullptr;
+    unsigned blocks = (unsigned)((a.n + TRACE_BLOCK - 1) / TRACE_BLOCK);
+    if (pool) {
+        // persistent grid: every block resident at once
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_pool<false, false, 1, false>, TRACE_BLOCK, 0);
+        const unsigned cap = (unsigned)std::max(1, sms) * (unsigned)std::max(1, per_sm);
+        blocks = std::min(blocks, cap);
+        cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return e;
+    }
+#define HCC_TRACE_KERNEL(K, ANY, CNT)                                           \
+    do {                                                                        \
+        if (multi) {                                                            \
+            if (a.layout == 0)                                                  \
+                K<ANY, CNT, 0, true><<<blocks, TRACE_BLOCK, 0, s>>>(a);         \
+            else                                                                \
+                K<ANY, CNT, 1, true><<<blocks, TRACE_BLOCK, 0, s>>>(a);         \
+        } else {                                                                \
+            if (a.layout == 0)                                                  \
+                K<ANY, CNT, 0, false><<<blocks, TRACE_BLOCK, 0, s>>>(a);        \
+            else                                                                \
+                K<ANY, CNT, 1, false><<<blocks, TRACE_BLOCK, 0, s>>>(a);        \
+        }                                                                       \
+    } while (0)
+#define HCC_TRACE_LAUNCH(ANY, CNT)                 \
+    do {                                           \
+        if (pool)                                  \
+            HCC_TRACE_KERNEL(k_trace_pool, ANY, CNT); \
+        else                                       \
+            HCC_TRACE_KERNEL(k_trace, ANY, CNT);   \
     } while (0)
     if (any_hit && count)
         HCC_TRACE_LAUNCH(true, true);
@@ -336,6 +460,7 @@ cudaError_t launch_trace(cudaStream_t s, const TraceArgs &a, int any_hit) {
     else
         HCC_TRACE_LAUNCH(false, false);
 #undef HCC_TRACE_LAUNCH
+#undef HCC_TRACE_KERNEL
     return cudaGetLastError();
 }
 

@@ -493,3 +493,40 @@ def test_stack_overflow_is_reported_and_context_survives(ctx, tiny, layout):
     # the context keeps working
     g = gpu_trace(ctx, tiny, tiny.org, tiny.dir)
     compare_hits(g, oracle.trace_bvh(tiny.w.bvh, tiny.w.rays.org, tiny.w.rays.dir))
+
+
+@pytest.mark.parametrize("which", ["tiny", "room"])
+def test_trace_schedules_give_the_same_records(ctx, which, request):
+    """One thread per ray and the persistent trace with ray replacement return
+    the same closest-hit records (and the same occlusion for any hit)."""
+    sc = request.getfixturevalue(which)
+    ref = oracle.trace_bvh(sc.w.bvh, sc.w.rays.org, sc.w.rays.dir)
+    ref_any = oracle.trace_bvh(sc.w.bvh, sc.w.rays.org, sc.w.rays.dir, any_hit=True)
+    keys = torch.empty(sc.n, dtype=torch.int32, device=DEV)
+    perm = torch.empty(sc.n, dtype=torch.int32, device=DEV)
+    cut = hcc.hcc_select_cut(ctx, sc.bvh_exact, 32, 0.125)
+    hcc.hcc_encode(ctx, "hcc", sc.bvh_exact, cut, sc.org, sc.dir, 32, keys)
+    hcc.hcc_sort(ctx, keys, 32, sc.n, perm)
+    try:
+        for schedule in ("per_ray", "refill", "auto"):
+            hcc.hcc_set_trace_schedule(ctx, schedule)
+            for bvh in (sc.bvh, sc.bvh_exact):
+                hits = torch.zeros((sc.n, 4), dtype=torch.int32, device=DEV)
+                hcc.hcc_trace(ctx, bvh, sc.org, sc.dir, hits)
+                hcc.hcc_sync(ctx)
+                assert hcc.hits_to_numpy(hits).tobytes() == ref.tobytes(), schedule
+                hits.zero_()
+                hcc.hcc_trace_sorted(ctx, bvh, sc.org, sc.dir, perm, hits)
+                hcc.hcc_sync(ctx)
+                assert hcc.hits_to_numpy(hits).tobytes() == ref.tobytes(), schedule
+                hits.zero_()
+                hcc.hcc_trace(ctx, bvh, sc.org, sc.dir, hits, any_hit=True)
+                hcc.hcc_sync(ctx)
+                assert np.array_equal(hcc.hits_to_numpy(hits)["prim"] >= 0, ref_any["prim"] >= 0), schedule
+            c = hcc.hcc_trace_counts(ctx, sc.bvh_exact, sc.org, sc.dir, perm=perm)
+            assert c["warp_node_steps"] <= c["node_visits"] <= 32 * c["warp_node_steps"]
+        with pytest.raises(hcc.HccError):
+            hcc.hcc_set_trace_schedule(ctx, 7)
+    finally:
+        hcc.hcc_set_trace_schedule(ctx, "auto")
+        hcc.hcc_cut_destroy(cut)
