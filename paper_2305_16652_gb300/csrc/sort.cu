@@ -8,10 +8,11 @@
 //            stable result); the ping-pong buffer of every active pass is
 //            chosen so that the first active pass reads the caller's keys and
 //            synthesises ids, and the last one writes only the permutation
-//   k_pass   per 4096-key tile: warp-level ranking with match.any, per-digit
-//            tile counts published to a decoupled look-back chain (bounded
-//            waits), keys reordered in shared memory and written out in runs
-//            of equal digits (coalesced)
+//   k_pass   per 4096-key tile: warp-level ranking (match.any, or a ballot
+//            split when a warp's digits are spread), per-digit tile counts
+//            published to a decoupled look-back chain (bounded waits), keys
+//            reordered in shared memory and written out in runs of equal
+//            digits (coalesced)
 //   k_ident  perm = identity when no pass is active (all keys equal, n <= 1)
 // Tiles take their position from an atomic counter in launch order, so a tile
 // only ever waits for tiles that are already running.
@@ -34,6 +35,7 @@ constexpr uint32_t ST_INC = 2u << 30;  // inclusive prefix of this digit availab
 constexpr uint32_t ST_VALUE = (1u << 30) - 1u;
 constexpr uint32_t SPIN_LIMIT = 1u << 22;  // total status reads a tile may wait
 constexpr int LOOKBACK = 8;                // predecessors read per look-back round
+constexpr int MATCH_MAX_DISTINCT = 16;     // distinct digits per warp item below which match.any ranks
 
 enum : int { KB_USER = 0, KB_A = 1, KB_B = 2, KB_NONE = 3 };
 enum : int { VB_SYNTH = 0, VB_A = 1, VB_PERM = 2 };
@@ -271,14 +273,12 @@ __device__ __forceinline__ void load_tile_async(T *dst, const T *src, uint32_t c
 // A block handles its tiles in increasing order, so the lowest unfinished
 // tile is always being worked on and every wait ends.
 template <typename K>
-__global__ void __launch_bounds__(SORT_BLOCK) k_pass(PassArgs<K> a, int pass) {
+__global__ void __launch_bounds__(SORT_BLOCK, sizeof(K) == 4 ? 3 : 2) k_pass(PassArgs<K> a, int pass) {
     const PassPlan pl = a.h->plan[pass];
     if (!pl.active) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     K *in_keys = reinterpret_cast<K *>(smem_raw);                                  // [2][TILE]
     uint32_t *in_vals = reinterpret_cast<uint32_t *>(in_keys + 2 * SORT_TILE);     // [2][TILE]
-    K *out_keys = reinterpret_cast<K *>(in_vals + 2 * SORT_TILE);                  // [TILE]
-    uint32_t *out_vals = reinterpret_cast<uint32_t *>(out_keys + SORT_TILE);       // [TILE]
     __shared__ uint32_t s_whist[SORT_WARPS][RADIX];
     __shared__ uint32_t s_local[RADIX];
     __shared__ uint32_t s_base[RADIX];
@@ -332,19 +332,36 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_pass(PassArgs<K> a, int pass) {
         const uint32_t tile = cur;
         const uint64_t base = (uint64_t)tile * SORT_TILE;
         const uint32_t tile_n = tile_count(tile);
-        const K *tk = in_keys + buf * SORT_TILE;
-        const uint32_t *tv = in_vals + buf * SORT_TILE;
+        K *tk = in_keys + buf * SORT_TILE;  // the tile's keys, then (reordered) its staging area
+        uint32_t *tv = in_vals + buf * SORT_TILE;
 
-        // warp-level stable ranking
+        // this thread's items in registers; the buffer is reused for the reorder
+        K kreg[SORT_ITEMS];
+        uint32_t vreg[SORT_ITEMS];
+#pragma unroll
+        for (int i = 0; i < SORT_ITEMS; ++i) {
+            const uint32_t pos = wfirst + (uint32_t)i * 32;
+            kreg[i] = pos < tile_n ? (tk[pos] & mask) : (K)0;
+            vreg[i] = synth ? (uint32_t)(base + pos) : (pos < tile_n ? tv[pos] : 0u);
+        }
+
+        // warp-level stable ranking: lanes with equal digits found by match.any
+        // while the warp's items hold few distinct digits (ray keys do), by
+        // the fixed-cost ballot split otherwise; the choice follows the
+        // previous item's number of distinct digits
         uint32_t rank[SORT_ITEMS];
         uint32_t *wh = s_whist[warp];
+        bool use_match = true;
 #pragma unroll
         for (int i = 0; i < SORT_ITEMS; ++i) {
             const uint32_t pos = wfirst + (uint32_t)i * 32;
             const bool valid = pos < tile_n;
-            const uint32_t d = valid ? (uint32_t)((tk[pos] & mask) >> shift) & 255u : 0u;
-            const uint32_t peers = digit_peers(d, dbits, __ballot_sync(0xFFFFFFFFu, valid));
+            const uint32_t d = valid ? (uint32_t)(kreg[i] >> shift) & 255u : 0u;
+            const uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
+            const uint32_t peers = use_match ? (__match_any_sync(0xFFFFFFFFu, valid ? d : 256u + lane) & vmask)
+                                             : digit_peers(d, dbits, vmask);
             const uint32_t leader = __ffs(peers) - 1;
+            use_match = __popc(__ballot_sync(0xFFFFFFFFu, valid && (uint32_t)lane == leader)) <= MATCH_MAX_DISTINCT;
             uint32_t prior = 0;
             if (valid && (uint32_t)lane == leader) prior = atomicAdd(&wh[d], (uint32_t)__popc(peers));
             prior = __shfl_sync(0xFFFFFFFFu, prior, valid ? leader : lane);
@@ -376,16 +393,16 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_pass(PassArgs<K> a, int pass) {
         for (int w = 0; w < warp; ++w) wpre += s_wsum[w];
         s_local[tid] = wpre + incl - total;
         __syncthreads();
-        // reorder the tile by digit in shared memory (stable)
+        // reorder the tile by digit (stable) into its own buffer: every thread
+        // read its items before the barriers above
 #pragma unroll
         for (int i = 0; i < SORT_ITEMS; ++i) {
             const uint32_t pos = wfirst + (uint32_t)i * 32;
             if (pos < tile_n) {
-                const K k = tk[pos] & mask;
-                const uint32_t d = (uint32_t)(k >> shift) & 255u;
+                const uint32_t d = (uint32_t)(kreg[i] >> shift) & 255u;
                 const uint32_t o = s_local[d] + wh[d] + rank[i];
-                out_keys[o] = k;
-                out_vals[o] = synth ? (uint32_t)(base + pos) : tv[pos];
+                tk[o] = kreg[i];
+                tv[o] = vreg[i];
             }
         }
         // decoupled look-back for digit tid
@@ -440,11 +457,11 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_pass(PassArgs<K> a, int pass) {
         // runs of equal digits to their global positions
 #pragma unroll 4
         for (uint32_t p = tid; p < tile_n; p += SORT_BLOCK) {
-            const K k = out_keys[p];
+            const K k = tk[p];
             const uint32_t d = (uint32_t)(k >> shift) & 255u;
             const uint32_t g = s_base[d] + (p - s_local[d]);
             if (kout) __stcs(kout + g, k);
-            __stcs(vout + g, out_vals[p]);
+            __stcs(vout + g, tv[p]);
         }
         cur = nxt;
         buf ^= 1;
@@ -488,7 +505,7 @@ cudaError_t run_sort(cudaStream_t s, const K *keys, uint32_t key_bits, uint64_t 
     a.key_bits = key_bits;
     a.num_tiles = tiles;
     a.err = err;
-    const size_t dyn = 3 * (sizeof(K) + sizeof(uint32_t)) * SORT_TILE;  // 2 input buffers + 1 staging
+    const size_t dyn = 2 * (sizeof(K) + sizeof(uint32_t)) * SORT_TILE;  // 2 tile buffers (prefetch, current)
     // the shared-memory opt-in is set once per device (so that a sort can be
     // captured in a CUDA graph without any non-stream call)
     static std::atomic<uint64_t> opted{0};
@@ -497,7 +514,7 @@ cudaError_t run_sort(cudaStream_t s, const K *keys, uint32_t key_bits, uint64_t 
         if (e != cudaSuccess) return e;
         opted.fetch_or(1ull << dev);
     }
-    const uint32_t per_sm = sizeof(K) == 4 ? 2u : 1u;  // blocks that fit the shared memory
+    const uint32_t per_sm = sizeof(K) == 4 ? 3u : 2u;  // blocks that fit the shared memory
     const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)(sms > 0 ? sms : 1) * per_sm);
     for (int p = 0; p < passes; ++p) k_pass<K><<<grid, SORT_BLOCK, dyn, s>>>(a, p);
     uint64_t iblocks = (n + 255) / 256;
