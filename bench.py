@@ -771,9 +771,19 @@ def run_serve_sweep(args):
     ring = _HitRing(torch, 64 << 20 if not args.quick else 8 << 20)
     key_bits = args.key_bits
 
+    big = int(np.argmax(reqs["n"]))
+
     def server(slots):
         srv = hcc.hcc_server_create(0, bvhs, cuts, slots=slots, method="hcc", key_bits=key_bits)
-        _serve_run(srv, ring, pools, reqs, min(24, count), outstanding=2 * slots)  # warm the pool
+        # grow the server's memory pool to the largest request on every slot, so
+        # that no timed request waits for the driver to map new memory
+        s, n, off = int(reqs["scene"][big]), int(reqs["n"][big]), int(reqs["offset"][big])
+        hits_w = [torch.empty((n, 4), dtype=torch.int32).pin_memory() for _ in range(slots)]
+        tickets = [hcc.hcc_server_submit(srv, s, pools[s][0][off:off + n], pools[s][1][off:off + n], h)
+                   for h in hits_w]
+        for t in tickets:
+            hcc.hcc_server_wait(srv, t)
+        _serve_run(srv, ring, pools, reqs, min(24, count), outstanding=2 * slots)
         return srv
 
     def summary(mrays, lat, st):

@@ -14,6 +14,7 @@
 // round-to-nearest intrinsics (built with --fmad=false), so the (t, u, v) of
 // a triangle are the same bit patterns on every run and in every ray order.
 #include <algorithm>
+#include <atomic>
 
 #include "hcc_internal.cuh"
 
@@ -420,11 +421,18 @@ cudaError_t launch_trace(cudaStream_t s, const TraceArgs &a, int any_hit) {
     const bool count = a.counts != nullptr, multi = a.scenes != nullptr, pool = a.work != nullptr;
     unsigned blocks = (unsigned)((a.n + TRACE_BLOCK - 1) / TRACE_BLOCK);
     if (pool) {
-        // persistent grid: every block resident at once
-        int dev = 0, sms = 0, per_sm = 0;
+        // persistent grid: every block resident at once (the residency is
+        // queried once per device; all pool variants share the launch bounds)
+        static std::atomic<int> resident[64];
+        int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_pool<false, false, 1, false>, TRACE_BLOCK, 0);
+        int per_sm = (dev >= 0 && dev < 64) ? resident[dev].load() : 0;
+        if (per_sm <= 0) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_pool<false, false, 1, false>, TRACE_BLOCK,
+                                                          0);
+            if (dev >= 0 && dev < 64 && per_sm > 0) resident[dev].store(per_sm);
+        }
         const unsigned cap = (unsigned)std::max(1, sms) * (unsigned)std::max(1, per_sm);
         blocks = std::min(blocks, cap);
         cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), s);
