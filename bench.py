@@ -606,7 +606,7 @@ def run_batch_sweep(args):
     t0 = time.perf_counter()
     tuned = tune.tune_batch(ctx, stream, bvhs, per_scene)
     tune_s = time.perf_counter() - t0
-    cuts = [hcc.hcc_select_cut(ctx, b, C, 0.125) for b, C in zip(bvhs, tuned["cut_sizes"])]
+    cuts = [hcc.hcc_select_cut(ctx, b, C, lam) for b, C, lam in zip(bvhs, tuned["cut_sizes"], tuned["lambdas"])]
     batch = hcc.hcc_batch_create(ctx, bvhs, cuts, offsets)
     hcc.hcc_reserve(ctx, n, 64)
     results = {}
@@ -657,8 +657,8 @@ def run_batch_sweep(args):
            "config": {"workload": f"{S} rooms (seeds 2-17), {sum(w.tris.shape[0] for w in ws)} triangles, "
                                   f"{n} rays per bounce", "bvh_layout": args.layout,
                       "scenes": [{"tris": int(w.tris.shape[0]), "rays": int(w.rays.n)} for w in ws]},
-           "autotune": {"key_bits": tuned["key_bits"], "cut_sizes": tuned["cut_sizes"],
-                        "totals_ms": {str(k): round(v, 3) for k, v in tuned["totals_ms"].items()},
+           "autotune": {"key_bits": tuned["key_bits"], "cut_sizes": tuned["cut_sizes"], "lambdas": tuned["lambdas"],
+                        "schedule": tuned["schedule"], "totals_ms": tuned["totals_ms"],
                         "seconds": round(tune_s, 1)},
            "generation_s": round(gen_s, 1), "methods": results}
     for c in cuts:

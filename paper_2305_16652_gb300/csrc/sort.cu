@@ -34,7 +34,7 @@ constexpr uint32_t ST_AGG = 1u << 30;  // tile count of this digit available
 constexpr uint32_t ST_INC = 2u << 30;  // inclusive prefix of this digit available
 constexpr uint32_t ST_VALUE = (1u << 30) - 1u;
 constexpr uint32_t SPIN_LIMIT = 1u << 22;  // total status reads a tile may wait
-constexpr int LOOKBACK = 8;                // predecessors read per look-back round
+constexpr int LOOKBACK = 4;                // predecessors read per look-back round
 constexpr int MATCH_MAX_DISTINCT = 16;     // distinct digits per warp item below which match.any ranks
 
 enum : int { KB_USER = 0, KB_A = 1, KB_B = 2, KB_NONE = 3 };

@@ -149,3 +149,32 @@ def test_graph_capture_replays_a_bounce(env):
     finally:
         hcc.hcc_batch_destroy(batch)
         hcc.hcc_destroy(ctx)
+
+
+def test_autotuner_choices_are_valid_and_keep_the_results(env):
+    from paper_2305_16652_gb300 import tune
+    stream = torch.cuda.Stream()
+    ctx = hcc.hcc_create(0, stream)
+    bvhs, _ = env["layouts"]["exact"]
+    off = env["offsets"].astype(np.int64)
+    o = torch.from_numpy(env["org"]).to(DEV)
+    d = torch.from_numpy(env["dir"]).to(DEV)
+    per_scene = [(o[off[s]:off[s + 1]], d[off[s]:off[s + 1]]) for s in range(len(bvhs))]
+    torch.cuda.synchronize()
+    try:
+        t = tune.tune_batch(ctx, stream, bvhs, per_scene, cut_sizes=(8, 32), key_bits=(16, 32),
+                            lambdas=(0.0625, 0.125), schedules=("refill", "per_ray"), reps=1)
+        assert t["key_bits"] in (16, 32) and t["schedule"] in ("refill", "per_ray")
+        assert len(t["cut_sizes"]) == len(bvhs) and set(t["cut_sizes"]) <= {8, 32}
+        assert set(t["lambdas"]) <= {0.0625, 0.125}
+        cuts = [hcc.hcc_select_cut(ctx, b, C, lam) for b, C, lam in zip(bvhs, t["cut_sizes"], t["lambdas"])]
+        batch = hcc.hcc_batch_create(ctx, bvhs, cuts, env["offsets"])
+        hits = torch.zeros((o.shape[0], 4), dtype=torch.int32, device=DEV)
+        hcc.hcc_batch_run(ctx, batch, "hcc", o, d, t["key_bits"], hits)
+        hcc.hcc_sync(ctx)
+        assert hcc.hits_to_numpy(hits).tobytes() == env["ref"].tobytes()
+        hcc.hcc_batch_destroy(batch)
+        for c in cuts:
+            hcc.hcc_cut_destroy(c)
+    finally:
+        hcc.hcc_destroy(ctx)
