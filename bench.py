@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -110,7 +111,7 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.proc = None
         self.dev = device_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"hcc_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:

@@ -45,7 +45,7 @@ typedef enum hcc_status {
     HCC_ERR_INVALID_ARG = 1,    /* null pointer, bad size, misaligned buffer, bad enum */
     HCC_ERR_OOM = 2,            /* device or host allocation failed */
     HCC_ERR_CUDA = 3,           /* a CUDA runtime call failed; see hcc_last_error */
-    HCC_ERR_UNSUPPORTED = 4,    /* valid request this build does not implement */
+    HCC_ERR_UNSUPPORTED = 4,    /* valid request this library does not implement */
     HCC_ERR_STACK_OVERFLOW = 5, /* a ray needed more traversal-stack entries than exist */
     HCC_ERR_TIMEOUT = 6         /* a bounded device-side wait gave up */
 } hcc_status;
