@@ -572,7 +572,8 @@ hcc_status hcc_server_query(hcc_server *s, uint64_t ticket, int *done);
 
 /*
  * Blocks until the request finishes, releases its ticket and returns its
- * status: OK, STACK_OVERFLOW (a ray's traversal needed more than
+ * status (wait once per ticket, from one thread; every wait must return
+ * before hcc_server_destroy): OK, STACK_OVERFLOW (a ray's traversal needed more than
  * HCC_TRACE_STACK entries; its record is incomplete), TIMEOUT (a bounded
  * wait in the sort gave up), OOM (the pool could not grow), CUDA.  A failed
  * request does not affect any other.  *latency_ms (may be NULL) = time from

@@ -31,8 +31,8 @@ __device__ __forceinline__ bool meets(const float4 &o, const float4 &d, float ix
     const float ax = __fmul_rn(__fsub_rn(lo.x, o.x), ix), bx = __fmul_rn(__fsub_rn(hi.x, o.x), ix);
     const float ay = __fmul_rn(__fsub_rn(lo.y, o.y), iy), by = __fmul_rn(__fsub_rn(hi.y, o.y), iy);
     const float az = __fmul_rn(__fsub_rn(lo.z, o.z), iz), bz = __fmul_rn(__fsub_rn(hi.z, o.z), iz);
-    const float tnear = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), o.w));
-    const float tfar = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), d.w));
+    const float tnear = fmax3(fminf(ax, bx), fminf(ay, by), fmaxf(fminf(az, bz), o.w));
+    const float tfar = fmin3(fmaxf(ax, bx), fmaxf(ay, by), fminf(fmaxf(az, bz), d.w));
     return tnear <= tfar;
 }
 

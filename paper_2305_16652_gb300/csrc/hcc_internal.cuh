@@ -64,6 +64,20 @@ __device__ __forceinline__ uint32_t scene_of(const uint64_t *__restrict__ offset
     return lo;
 }
 
+// Three-input max / min (sm_100+ PTX): like nested fmaxf / fminf, NaN inputs
+// are ignored and the result is one of the inputs, so a slab test written
+// with them gives the same comparisons in one instruction fewer.
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // ------------------------------------------------------------------ launchers
 // All return the launch error (cudaSuccess when queued).
 

@@ -51,8 +51,8 @@ __device__ __forceinline__ void slab(const Ray &r, float lox, float loy, float l
     const float ax = __fmul_rn(__fsub_rn(lox, r.ox), r.ix), bx = __fmul_rn(__fsub_rn(hix, r.ox), r.ix);
     const float ay = __fmul_rn(__fsub_rn(loy, r.oy), r.iy), by = __fmul_rn(__fsub_rn(hiy, r.oy), r.iy);
     const float az = __fmul_rn(__fsub_rn(loz, r.oz), r.iz), bz = __fmul_rn(__fsub_rn(hiz, r.oz), r.iz);
-    tn = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), r.tmin));
-    const float f = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fmaxf(az, bz));
+    tn = fmax3(fminf(ax, bx), fminf(ay, by), fmaxf(fminf(az, bz), r.tmin));
+    const float f = fmin3(fmaxf(ax, bx), fmaxf(ay, by), fmaxf(az, bz));
     tf = fminf(__fmul_rn(f, ROBUST_FAR), tcap);
 }
 
