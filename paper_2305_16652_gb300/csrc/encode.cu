@@ -39,17 +39,38 @@ __device__ __forceinline__ bool meets(const float4 &o, const float4 &d, float ix
 // Algorithm 1: the cut nodes are staged in shared memory once per block
 // (line 1); every ray is tested against every cut node and each result sets
 // one key bit.  Cut node r drives bit (key_bits - 1 - r).
+//
+// For a ray whose three reciprocal direction components are finite and a cut
+// whose boxes all have lo <= hi, the per-axis min / max of the slab test is
+// known from the sign of the reciprocal: with inv > 0, (lo - o) * inv <=
+// (hi - o) * inv (rounding is monotonic), and the order flips for inv < 0.
+// Those rays read each bound they need by a per-lane index instead of
+// computing both and taking min and max -- the same comparisons with six
+// fewer min/max operations per node.  Other rays (a zero or denormal
+// direction component, where 0 * inf makes a NaN that fminf / fmaxf skip) take
+// the general test.
 template <typename K>
 __global__ void __launch_bounds__(ENC_BLOCK) k_encode_hcc(const float4 *__restrict__ org,
                                                           const float4 *__restrict__ dir, uint64_t n,
                                                           const float4 *__restrict__ cut, uint32_t used,
                                                           uint32_t key_bits, K *__restrict__ keys) {
     __shared__ float4 s_lo[MAX_CUT_BITS], s_hi[MAX_CUT_BITS];
+    __shared__ float s_b[MAX_CUT_BITS * 6];  // per node: lo.x hi.x lo.y hi.y lo.z hi.z
+    bool ordered = true;
     for (uint32_t r = threadIdx.x; r < used; r += blockDim.x) {
-        s_lo[r] = cut[2 * r];
-        s_hi[r] = cut[2 * r + 1];
+        const float4 lo = cut[2 * r], hi = cut[2 * r + 1];
+        s_lo[r] = lo;
+        s_hi[r] = hi;
+        float *b = s_b + 6 * r;
+        b[0] = lo.x;
+        b[1] = hi.x;
+        b[2] = lo.y;
+        b[3] = hi.y;
+        b[4] = lo.z;
+        b[5] = hi.z;
+        ordered = ordered && lo.x <= hi.x && lo.y <= hi.y && lo.z <= hi.z;
     }
-    __syncthreads();
+    ordered = __syncthreads_and(ordered);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const float4 o = __ldcs(org + i);
@@ -57,8 +78,25 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_hcc(const float4 *__restri
         const float ix = __frcp_rn(d.x), iy = __frcp_rn(d.y), iz = __frcp_rn(d.z);
         K key = 0;
         K bit = (K)1 << (key_bits - 1);
-        for (uint32_t r = 0; r < used; ++r, bit >>= 1)
-            if (meets(o, d, ix, iy, iz, s_lo[r], s_hi[r])) key |= bit;
+        if (ordered && isfinite(ix) && isfinite(iy) && isfinite(iz)) {
+            const uint32_t nx = ix < 0.0f, ny = 2u + (iy < 0.0f), nz = 4u + (iz < 0.0f);  // near-bound slots
+            const uint32_t fx = 1u - nx, fy = 5u - ny, fz = 9u - nz;                      // far-bound slots
+            for (uint32_t r = 0; r < used; ++r, bit >>= 1) {
+                const float *b = s_b + 6 * r;
+                const float tnx = __fmul_rn(__fsub_rn(b[nx], o.x), ix);
+                const float tny = __fmul_rn(__fsub_rn(b[ny], o.y), iy);
+                const float tnz = __fmul_rn(__fsub_rn(b[nz], o.z), iz);
+                const float tfx = __fmul_rn(__fsub_rn(b[fx], o.x), ix);
+                const float tfy = __fmul_rn(__fsub_rn(b[fy], o.y), iy);
+                const float tfz = __fmul_rn(__fsub_rn(b[fz], o.z), iz);
+                const float tnear = fmax3(tnx, tny, fmaxf(tnz, o.w));
+                const float tfar = fmin3(tfx, tfy, fminf(tfz, d.w));
+                if (tnear <= tfar) key |= bit;
+            }
+        } else {
+            for (uint32_t r = 0; r < used; ++r, bit >>= 1)
+                if (meets(o, d, ix, iy, iz, s_lo[r], s_hi[r])) key |= bit;
+        }
         __stcs(keys + i, key);
     }
 }
