@@ -293,8 +293,25 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_multi(const float4 *__rest
         if (METHOD == HCC_METHOD_HCC) {
             const float ix = __frcp_rn(d.x), iy = __frcp_rn(d.y), iz = __frcp_rn(d.z);
             K bit = (K)1 << (key_bits - 1);
-            for (uint32_t r = 0; r < sc.used; ++r, bit >>= 1)
-                if (meets(o, d, ix, iy, iz, __ldg(sc.cut + 2 * r), __ldg(sc.cut + 2 * r + 1))) key |= bit;
+            if (sc.cut_ordered && isfinite(ix) && isfinite(iy) && isfinite(iz)) {
+                // bounds selected by the direction signs, as in k_encode_hcc
+                const float *cf = reinterpret_cast<const float *>(sc.cut);  // per node: lo.xyzw hi.xyzw
+                const uint32_t nx = ix < 0.0f ? 4u : 0u, ny = iy < 0.0f ? 5u : 1u, nz = iz < 0.0f ? 6u : 2u;
+                const uint32_t fx = 4u - nx, fy = 6u - ny, fz = 8u - nz;
+                for (uint32_t r = 0; r < sc.used; ++r, bit >>= 1) {
+                    const float *b = cf + 8 * r;
+                    const float tnear = fmax3(__fmul_rn(__fsub_rn(__ldg(b + nx), o.x), ix),
+                                              __fmul_rn(__fsub_rn(__ldg(b + ny), o.y), iy),
+                                              fmaxf(__fmul_rn(__fsub_rn(__ldg(b + nz), o.z), iz), o.w));
+                    const float tfar = fmin3(__fmul_rn(__fsub_rn(__ldg(b + fx), o.x), ix),
+                                             __fmul_rn(__fsub_rn(__ldg(b + fy), o.y), iy),
+                                             fminf(__fmul_rn(__fsub_rn(__ldg(b + fz), o.z), iz), d.w));
+                    if (tnear <= tfar) key |= bit;
+                }
+            } else {
+                for (uint32_t r = 0; r < sc.used; ++r, bit >>= 1)
+                    if (meets(o, d, ix, iy, iz, __ldg(sc.cut + 2 * r), __ldg(sc.cut + 2 * r + 1))) key |= bit;
+            }
         } else if (METHOD == HCC_METHOD_TWOPOINT) {
             key = twopoint_key<K>(o, d, sc, key_bits);
         } else if (METHOD == HCC_METHOD_ORIGIN) {
@@ -381,7 +398,7 @@ namespace {
 // Multi-level HCC (Sec. 4.3): the top field as in Algorithm 1; the first met
 // top node (HAD order) is the representative, and its low-level cut fills the
 // next low_field bits.  All boxes of both levels are staged in shared memory:
-// top pairs first, then the low pairs row by row.
+// top boxes first, then the low boxes row by row.
 template <typename K>
 __global__ void __launch_bounds__(ENC_BLOCK) k_encode_mlhcc(const float4 *__restrict__ org,
                                                             const float4 *__restrict__ dir, uint64_t n,
@@ -389,29 +406,56 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_mlhcc(const float4 *__rest
                                                             uint32_t top_field, const float4 *__restrict__ low,
                                                             uint32_t low_field, uint32_t key_bits,
                                                             K *__restrict__ keys) {
-    extern __shared__ float4 s_box[];
-    float4 *s_top = s_box, *s_low = s_box + 2 * ntop;
-    for (uint32_t r = threadIdx.x; r < 2 * ntop; r += blockDim.x) s_top[r] = top[r];
-    for (uint32_t r = threadIdx.x; r < 2 * ntop * low_field; r += blockDim.x) s_low[r] = low[r];
-    __syncthreads();
+    extern __shared__ float s_box[];  // per box: lo.x hi.x lo.y hi.y lo.z hi.z; top boxes, then low rows
+    const uint32_t nbox = ntop + ntop * low_field;
+    bool ordered = true;
+    for (uint32_t q = threadIdx.x; q < nbox; q += blockDim.x) {
+        const float4 lo = q < ntop ? top[2 * q] : low[2 * (q - ntop)];
+        const float4 hi = q < ntop ? top[2 * q + 1] : low[2 * (q - ntop) + 1];
+        float *b = s_box + 6 * q;
+        b[0] = lo.x;
+        b[1] = hi.x;
+        b[2] = lo.y;
+        b[3] = hi.y;
+        b[4] = lo.z;
+        b[5] = hi.z;
+        ordered = ordered && lo.x <= hi.x && lo.y <= hi.y && lo.z <= hi.z;
+    }
+    ordered = __syncthreads_and(ordered);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const float4 o = __ldcs(org + i);
         const float4 d = __ldcs(dir + i);
         const float ix = __frcp_rn(d.x), iy = __frcp_rn(d.y), iz = __frcp_rn(d.z);
+        // the slab test of box q: bounds selected by the direction signs when
+        // that is exact (see k_encode_hcc), the general test otherwise
+        const bool fast = ordered && isfinite(ix) && isfinite(iy) && isfinite(iz);
+        const uint32_t nx = ix < 0.0f, ny = 2u + (iy < 0.0f), nz = 4u + (iz < 0.0f);
+        const uint32_t fx = 1u - nx, fy = 5u - ny, fz = 9u - nz;
+        auto hit = [&](uint32_t q) {
+            const float *b = s_box + 6 * q;
+            if (fast) {
+                const float tnear = fmax3(__fmul_rn(__fsub_rn(b[nx], o.x), ix), __fmul_rn(__fsub_rn(b[ny], o.y), iy),
+                                          fmaxf(__fmul_rn(__fsub_rn(b[nz], o.z), iz), o.w));
+                const float tfar = fmin3(__fmul_rn(__fsub_rn(b[fx], o.x), ix), __fmul_rn(__fsub_rn(b[fy], o.y), iy),
+                                         fminf(__fmul_rn(__fsub_rn(b[fz], o.z), iz), d.w));
+                return tnear <= tfar;
+            }
+            return meets(o, d, ix, iy, iz, make_float4(b[0], b[2], b[4], 0.f), make_float4(b[1], b[3], b[5], 0.f));
+        };
         K key = 0;
         K bit = (K)1 << (key_bits - 1);
         uint32_t rep = ntop;
         for (uint32_t r = 0; r < ntop; ++r, bit >>= 1)
-            if (meets(o, d, ix, iy, iz, s_top[2 * r], s_top[2 * r + 1])) {
+            if (hit(r)) {
                 key |= bit;
                 rep = min(rep, r);
             }
         if (rep < ntop) {
-            const float4 *row = s_low + 2 * (size_t)rep * low_field;
+            const uint32_t row = ntop + rep * low_field;
             K lbit = (K)1 << (key_bits - 1 - top_field);
             for (uint32_t j = 0; j < low_field; ++j, lbit >>= 1)
-                if (meets(o, d, ix, iy, iz, row[2 * j], row[2 * j + 1])) key |= lbit;
+                if (hit(row + j)) key |= lbit;
         }
         __stcs(keys + i, key);
     }
@@ -486,7 +530,7 @@ cudaError_t launch_encode_mlhcc(cudaStream_t s, const float4 *org, const float4 
     if (n == 0) return cudaSuccess;
     if (ntop > top_field || top_field + low_field > MAX_CUT_BITS || top_field + low_field > key_bits)
         return cudaErrorInvalidValue;
-    const size_t smem = sizeof(float4) * 2 * ((size_t)ntop + (size_t)ntop * low_field);
+    const size_t smem = sizeof(float) * 6 * ((size_t)ntop + (size_t)ntop * low_field);
     const int grid = encode_grid(n, ENC_BLOCK, 8);
     if (key_bits <= 32)
         k_encode_mlhcc<uint32_t><<<grid, ENC_BLOCK, smem, s>>>(org, dir, n, top, ntop, top_field, low, low_field,

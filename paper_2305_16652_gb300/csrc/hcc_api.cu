@@ -1073,6 +1073,9 @@ hcc_status hcc_batch_create(hcc_ctx *ctx, uint32_t num_scenes, const hcc_bvh *co
         const hcc_cut *c = cuts ? cuts[s] : nullptr;
         d.cut = c ? c->d_boxes : nullptr;
         d.used = c ? c->on_device : 0;
+        d.cut_ordered = 1;
+        if (c)
+            for (size_t q = 0; q < c->lo.size(); ++q) d.cut_ordered &= c->lo[q] <= c->hi[q] ? 1u : 0u;
         for (int a = 0; a < 3; ++a) {
             d.lo[a] = b->lo[a];
             d.ext[a] = b->hi[a] - b->lo[a];

@@ -49,6 +49,7 @@ struct SceneDesc {
     uint32_t used;      // cut nodes that drive key bits
     float lo[3], ext[3], L;
     uint32_t num_tris;
+    uint32_t cut_ordered;  // every cut box has lo <= hi on every axis
 };
 
 // Scene of ray src in a batch: the last s with offsets[s] <= src.

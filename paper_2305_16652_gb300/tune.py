@@ -33,11 +33,13 @@ def _time(stream, fn, reps):
 
 
 def tune_batch(ctx, stream, bvhs, rays, cut_sizes=(16, 32, 64, 128), key_bits=(24, 32, 48),
-               lambdas=(0.0625, 0.125, 0.25), schedules=("refill", "per_ray"), max_rays=1 << 20, reps=3):
+               lambdas=(0.0625, 0.125, 0.25), schedules=("auto",), max_rays=1 << 20, reps=3):
     """rays: list of (org, dir) CUDA tensor pairs, one per scene (the scene's wavefront).
 
     Searches each scene's cut size C and HAD weight lambda (Eq. 1), the key length shared by the
-    batch, and the trace schedule of the context.  Returns {"key_bits": k, "cut_sizes": [C per
+    batch, and (when more than one is given) the trace schedule of the context.  The schedule is
+    not searched by default: timed scene by scene on capped wavefronts it favoured one thread per
+    ray, while the batched trace of all scenes at once runs faster with ray replacement.  Returns {"key_bits": k, "cut_sizes": [C per
     scene], "lambdas": [lambda per scene], "schedule": s, "totals_ms": {...}, "table": {...}}
     where table[schedule][k][scene][(C, lambda)] is the measured ms of that scene's bounce (first
     max_rays rays).  The context is left with the chosen schedule.
