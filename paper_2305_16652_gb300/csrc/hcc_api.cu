@@ -22,6 +22,11 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+// Rays per chunk and lanes (contexts with their own streams) of the
+// pipelined hcc_run_host.
+constexpr uint64_t HOST_CHUNK = 1ull << 22;
+constexpr uint32_t HOST_LANES = 2;
+
 struct hcc_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -32,6 +37,7 @@ struct hcc_ctx {
     DevBuf sort_scratch;
     DevBuf keys, perm;                          // hcc_run
     DevBuf in_org, in_dir, hits;                // hcc_run_host
+    hcc_ctx *lane[HOST_LANES] = {};             // hcc_run_host pipeline: contexts on their own streams
 };
 
 struct hcc_bvh {
@@ -375,6 +381,14 @@ hcc_status hcc_set_trace_schedule(hcc_ctx *ctx, hcc_trace_schedule schedule) {
 
 hcc_status hcc_destroy(hcc_ctx *ctx) {
     if (!ctx) return HCC_ERR_INVALID_ARG;
+    for (hcc_ctx *&l : ctx->lane)
+        if (l) {
+            cudaStream_t s = l->stream;
+            hcc_destroy(l);
+            DeviceGuard g(ctx->device);
+            cudaStreamDestroy(s);
+            l = nullptr;
+        }
     {
         DeviceGuard g(ctx->device);
         cudaStreamSynchronize(ctx->stream);
@@ -1322,18 +1336,78 @@ hcc_status hcc_run_host(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, con
     if (n > HCC_MAX_SORT_N) return fail(ctx, HCC_ERR_INVALID_ARG, "n above HCC_MAX_SORT_N");
     DeviceGuard g(ctx->device);
     hcc_status st;
-    if ((st = ensure(ctx, ctx->in_org, n * 16, "input rays")) != HCC_OK) return st;
-    if ((st = ensure(ctx, ctx->in_dir, n * 16, "input rays")) != HCC_OK) return st;
-    if ((st = ensure(ctx, ctx->hits, n * sizeof(hcc_hit), "hits")) != HCC_OK) return st;
-    cudaError_t e = cudaMemcpyAsync(ctx->in_org.p, org_tmin, n * 16, cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->in_dir.p, dir_tmax, n * 16, cudaMemcpyHostToDevice, ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "host-to-device copy of rays");
-    hcc_rays r{static_cast<float *>(ctx->in_org.p), static_cast<float *>(ctx->in_dir.p), n};
-    if ((st = hcc_run(ctx, method, bvh, cut, &r, key_bits, any_hit, static_cast<hcc_hit *>(ctx->hits.p))) != HCC_OK)
-        return st;
-    e = cudaMemcpyAsync(hits, ctx->hits.p, n * sizeof(hcc_hit), cudaMemcpyDeviceToHost, ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "device-to-host copy of hits");
-    return hcc_sync(ctx);
+    cudaError_t e;
+    if (n <= HOST_CHUNK) {
+        // one pass on the context's stream
+        if ((st = ensure(ctx, ctx->in_org, n * 16, "input rays")) != HCC_OK) return st;
+        if ((st = ensure(ctx, ctx->in_dir, n * 16, "input rays")) != HCC_OK) return st;
+        if ((st = ensure(ctx, ctx->hits, n * sizeof(hcc_hit), "hits")) != HCC_OK) return st;
+        e = cudaMemcpyAsync(ctx->in_org.p, org_tmin, n * 16, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->in_dir.p, dir_tmax, n * 16, cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "host-to-device copy of rays");
+        hcc_rays r{static_cast<float *>(ctx->in_org.p), static_cast<float *>(ctx->in_dir.p), n};
+        if ((st = hcc_run(ctx, method, bvh, cut, &r, key_bits, any_hit, static_cast<hcc_hit *>(ctx->hits.p))) !=
+            HCC_OK)
+            return st;
+        e = cudaMemcpyAsync(hits, ctx->hits.p, n * sizeof(hcc_hit), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "device-to-host copy of hits");
+        return hcc_sync(ctx);
+    }
+    // Pipelined: chunks of HOST_CHUNK rays take turns on the lane contexts,
+    // each with its own stream and scratch, so that one chunk's copies overlap
+    // another's kernels.  Each chunk is encoded, sorted and traced on its
+    // own; hits do not depend on the order rays are traced in.
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "context stream");
+    for (hcc_ctx *&l : ctx->lane) {
+        if (l) continue;
+        cudaStream_t s = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(ctx, e, "pipeline stream");
+        if ((st = hcc_create(&l, ctx->device, s)) != HCC_OK) {
+            cudaStreamDestroy(s);
+            return fail(ctx, st, "pipeline context");
+        }
+    }
+    hcc_status result = HCC_OK;
+    for (uint64_t c0 = 0, c = 0; c0 < n && result == HCC_OK; c0 += HOST_CHUNK, ++c) {
+        hcc_ctx *L = ctx->lane[c % HOST_LANES];
+        L->schedule = ctx->schedule;
+        const uint64_t m = std::min<uint64_t>(HOST_CHUNK, n - c0);
+        if ((st = ensure(L, L->in_org, HOST_CHUNK * 16, "input rays")) != HCC_OK ||
+            (st = ensure(L, L->in_dir, HOST_CHUNK * 16, "input rays")) != HCC_OK ||
+            (st = ensure(L, L->hits, HOST_CHUNK * sizeof(hcc_hit), "hits")) != HCC_OK) {
+            result = st;
+            ctx->last_error = L->last_error;
+            break;
+        }
+        e = cudaMemcpyAsync(L->in_org.p, org_tmin + 4 * c0, m * 16, cudaMemcpyHostToDevice, L->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(L->in_dir.p, dir_tmax + 4 * c0, m * 16, cudaMemcpyHostToDevice, L->stream);
+        if (e != cudaSuccess) {
+            result = cuda_fail(ctx, e, "host-to-device copy of rays");
+            break;
+        }
+        hcc_rays r{static_cast<float *>(L->in_org.p), static_cast<float *>(L->in_dir.p), m};
+        if ((st = hcc_run(L, method, bvh, cut, &r, key_bits, any_hit, static_cast<hcc_hit *>(L->hits.p))) != HCC_OK) {
+            result = st;
+            ctx->last_error = L->last_error;
+            break;
+        }
+        e = cudaMemcpyAsync(hits + c0, L->hits.p, m * sizeof(hcc_hit), cudaMemcpyDeviceToHost, L->stream);
+        if (e != cudaSuccess) {
+            result = cuda_fail(ctx, e, "device-to-host copy of hits");
+            break;
+        }
+    }
+    for (hcc_ctx *L : ctx->lane) {  // always drain every lane and read its error word
+        st = hcc_sync(L);
+        if (st != HCC_OK && result == HCC_OK) {
+            result = st;
+            ctx->last_error = L->last_error;
+        }
+    }
+    return result;
 }
 
 }  // extern "C"

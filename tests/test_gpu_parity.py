@@ -530,3 +530,32 @@ def test_trace_schedules_give_the_same_records(ctx, which, request):
     finally:
         hcc.hcc_set_trace_schedule(ctx, "auto")
         hcc.hcc_cut_destroy(cut)
+
+
+def test_run_host_pipeline_over_chunks(ctx):
+    """4.7M rays go through the two-stream chunked host pipeline: every hit equals
+    the device pipeline's, and a sample equals the oracle's."""
+    w = gen.room_workload(2, target_tris=60_000, W=1024, H=576, spp=8, shadow=False)
+    n = w.rays.n
+    assert n >= 1 << 22
+    bvh = hcc.hcc_bvh_upload(ctx, w.bvh, layout="exact")
+    cut = hcc.hcc_select_cut(ctx, bvh, 32, 0.125)
+    try:
+        org = torch.from_numpy(w.rays.org).pin_memory()
+        dir_ = torch.from_numpy(w.rays.dir).pin_memory()
+        for method in ("hcc", "nosort"):
+            h_host = torch.zeros((n, 4), dtype=torch.int32).pin_memory()
+            hcc.hcc_run_host(ctx, method, bvh, cut, org, dir_, 32, h_host)
+            d_hits = torch.zeros((n, 4), dtype=torch.int32, device=DEV)
+            hcc.hcc_run(ctx, method, bvh, cut, org.to(DEV), dir_.to(DEV), 32, d_hits)
+            hcc.hcc_sync(ctx)
+            assert torch.equal(h_host, d_hits.cpu()), method
+        idx = np.random.default_rng(5).choice(n, 3000, replace=False)
+        ref = oracle.trace_bvh(w.bvh, w.rays.org[idx], w.rays.dir[idx])
+        assert hcc.hits_to_numpy(h_host)[idx].tobytes() == ref.tobytes()
+        # the chunked path reports errors like the one-pass path
+        with pytest.raises(hcc.HccError):
+            hcc.hcc_run_host(ctx, "hcc", bvh, None, org, dir_, 32, h_host)
+    finally:
+        hcc.hcc_cut_destroy(cut)
+        hcc.hcc_bvh_destroy(bvh)
