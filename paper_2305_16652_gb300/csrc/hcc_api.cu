@@ -38,6 +38,7 @@ struct hcc_ctx {
     DevBuf keys, perm;                          // hcc_run
     DevBuf in_org, in_dir, hits;                // hcc_run_host
     hcc_ctx *lane[HOST_LANES] = {};             // hcc_run_host pipeline: contexts on their own streams
+    cudaEvent_t lane_in[HOST_LANES] = {};       // ... and the end of each lane's last input copy
 };
 
 struct hcc_bvh {
@@ -381,7 +382,8 @@ hcc_status hcc_set_trace_schedule(hcc_ctx *ctx, hcc_trace_schedule schedule) {
 
 hcc_status hcc_destroy(hcc_ctx *ctx) {
     if (!ctx) return HCC_ERR_INVALID_ARG;
-    for (hcc_ctx *&l : ctx->lane)
+    for (uint32_t i = 0; i < HOST_LANES; ++i) {
+        hcc_ctx *&l = ctx->lane[i];
         if (l) {
             cudaStream_t s = l->stream;
             hcc_destroy(l);
@@ -389,6 +391,12 @@ hcc_status hcc_destroy(hcc_ctx *ctx) {
             cudaStreamDestroy(s);
             l = nullptr;
         }
+        if (ctx->lane_in[i]) {
+            DeviceGuard g(ctx->device);
+            cudaEventDestroy(ctx->lane_in[i]);
+            ctx->lane_in[i] = nullptr;
+        }
+    }
     {
         DeviceGuard g(ctx->device);
         cudaStreamSynchronize(ctx->stream);
@@ -1359,7 +1367,12 @@ hcc_status hcc_run_host(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, con
     // own; hits do not depend on the order rays are traced in.
     e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "context stream");
-    for (hcc_ctx *&l : ctx->lane) {
+    for (uint32_t i = 0; i < HOST_LANES; ++i) {
+        hcc_ctx *&l = ctx->lane[i];
+        if (!ctx->lane_in[i] && (e = cudaEventCreateWithFlags(&ctx->lane_in[i], cudaEventDisableTiming)) != cudaSuccess) {
+            ctx->lane_in[i] = nullptr;
+            return cuda_fail(ctx, e, "pipeline event");
+        }
         if (l) continue;
         cudaStream_t s = nullptr;
         if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess)
@@ -1381,9 +1394,14 @@ hcc_status hcc_run_host(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, con
             ctx->last_error = L->last_error;
             break;
         }
-        e = cudaMemcpyAsync(L->in_org.p, org_tmin + 4 * c0, m * 16, cudaMemcpyHostToDevice, L->stream);
+        // input copies run one chunk after another (a chunk's copy does not
+        // share the link with the next one's), overlapping the kernels
+        e = c > 0 ? cudaStreamWaitEvent(L->stream, ctx->lane_in[(c - 1) % HOST_LANES], 0) : cudaSuccess;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(L->in_org.p, org_tmin + 4 * c0, m * 16, cudaMemcpyHostToDevice, L->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(L->in_dir.p, dir_tmax + 4 * c0, m * 16, cudaMemcpyHostToDevice, L->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->lane_in[c % HOST_LANES], L->stream);
         if (e != cudaSuccess) {
             result = cuda_fail(ctx, e, "host-to-device copy of rays");
             break;
