@@ -181,10 +181,11 @@ __device__ __forceinline__ void ray_init(RayState &s, const float4 o4, const flo
 __device__ __forceinline__ bool ray_done(const RayState &s) { return s.node == REF_NONE && s.leaf == REF_NONE; }
 
 // Next pending subtree that can still hold a closer hit, or REF_NONE.
-__device__ __forceinline__ uint32_t ray_pop(RayState &s, const uint32_t *st_ref, const float *st_t) {
+__device__ __forceinline__ uint32_t ray_pop(RayState &s, const uint2 *stack) {
     while (s.sp > 0) {
         --s.sp;
-        if (st_t[s.sp] <= s.tcap) return st_ref[s.sp];
+        const uint2 e = stack[s.sp];  // (node reference, entry distance): one 8-byte access
+        if (__uint_as_float(e.y) <= s.tcap) return e.x;
     }
     return REF_NONE;
 }
@@ -196,7 +197,7 @@ __device__ __forceinline__ uint32_t ray_pop(RayState &s, const uint32_t *st_ref,
 // nearer child is visited first and the farther one is pushed with its
 // entry distance, which lets a pop skip subtrees beyond the best hit.
 template <bool ANY, bool COUNT, int LAYOUT>
-__device__ __forceinline__ void ray_round(RayState &s, uint32_t *st_ref, float *st_t, const uint4 *__restrict__ nodes,
+__device__ __forceinline__ void ray_round(RayState &s, uint2 *stack, const uint4 *__restrict__ nodes,
                                           const float4 *__restrict__ tris, Counters &cn) {
     const uint32_t lane = threadIdx.x & 31;
     // internal nodes: descend until every lane has a leaf parked
@@ -221,8 +222,7 @@ __device__ __forceinline__ void ray_round(RayState &s, uint32_t *st_ref, float *
                 s.node = s.leaf = REF_NONE;
                 break;
             }
-            st_ref[s.sp] = first0 ? c.ref1 : c.ref0;
-            st_t[s.sp] = first0 ? tn1 : tn0;
+            stack[s.sp] = make_uint2(first0 ? c.ref1 : c.ref0, __float_as_uint(first0 ? tn1 : tn0));
             ++s.sp;
             s.node = first0 ? c.ref0 : c.ref1;
         } else if (h0) {
@@ -230,11 +230,11 @@ __device__ __forceinline__ void ray_round(RayState &s, uint32_t *st_ref, float *
         } else if (h1) {
             s.node = c.ref1;
         } else {
-            s.node = ray_pop(s, st_ref, st_t);
+            s.node = ray_pop(s, stack);
         }
         if (s.node != REF_NONE && (s.node & REF_LEAF) && s.leaf == REF_NONE) {
             s.leaf = s.node;
-            s.node = ray_pop(s, st_ref, st_t);
+            s.node = ray_pop(s, stack);
         }
         if (__all_sync(__activemask(), s.leaf != REF_NONE)) break;
     }
@@ -267,7 +267,7 @@ __device__ __forceinline__ void ray_round(RayState &s, uint32_t *st_ref, float *
         s.leaf = REF_NONE;
         if (s.node != REF_NONE && (s.node & REF_LEAF)) {
             s.leaf = s.node;
-            s.node = ray_pop(s, st_ref, st_t);
+            s.node = ray_pop(s, stack);
         }
     }
 }
@@ -344,11 +344,10 @@ __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
     uint32_t root;
     if (!fetch_ray<MULTI>(a, i, o4, d4, nodes, tris, root)) return;
     RayState s;
-    uint32_t st_ref[STACK];
-    float st_t[STACK];
+    uint2 stack[STACK];
     Counters cn;
     ray_init(s, o4, d4, root);
-    while (!ray_done(s)) ray_round<ANY, COUNT, LAYOUT>(s, st_ref, st_t, nodes, tris, cn);
+    while (!ray_done(s)) ray_round<ANY, COUNT, LAYOUT>(s, stack, nodes, tris, cn);
     store_hit(a, i, s);
     add_counts<COUNT>(a, cn);
 }
@@ -369,8 +368,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK, 10) k_trace_pool(TraceArgs a) {
     uint32_t lt;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
     RayState s;
-    uint32_t st_ref[STACK];
-    float st_t[STACK];
+    uint2 stack[STACK];
     Counters cn;
     const uint4 *nodes = a.nodes;
     const float4 *tris = a.tris;
@@ -404,7 +402,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK, 10) k_trace_pool(TraceArgs a) {
             continue;
         }
         if (have) {
-            ray_round<ANY, COUNT, LAYOUT>(s, st_ref, st_t, nodes, tris, cn);
+            ray_round<ANY, COUNT, LAYOUT>(s, stack, nodes, tris, cn);
             if (ray_done(s)) {
                 store_hit(a, slot, s);
                 have = false;
