@@ -89,10 +89,17 @@ struct ChildBoxes {
     uint32_t ref0, ref1;
 };
 
+// One 32-byte read-only load (sm_100+ 256-bit vector load); p must be 32-byte aligned.
+__device__ __forceinline__ void ldg256(const void *p, uint4 &a, uint4 &b) {
+    asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+        : "l"(p));
+}
+
 // 32-byte quantised node: bounds are origin + q * 2^E rounded outward.
 __device__ __forceinline__ void fetch_quant8(const uint4 *nodes, uint32_t ref, ChildBoxes &c) {
-    const uint4 A = __ldg(nodes + 2 * (size_t)ref);
-    const uint4 B = __ldg(nodes + 2 * (size_t)ref + 1);
+    uint4 A, B;
+    ldg256(nodes + 2 * (size_t)ref, A, B);
     const float ox = __uint_as_float(A.x & 0xFFFFFF00u);
     const float oy = __uint_as_float(A.y & 0xFFFFFF00u);
     const float oz = __uint_as_float(A.z & 0xFFFFFF00u);
@@ -117,9 +124,15 @@ __device__ __forceinline__ void fetch_quant8(const uint4 *nodes, uint32_t ref, C
 
 // 64-byte exact node: the children's FP32 boxes as stored in the input BVH.
 __device__ __forceinline__ void fetch_exact(const uint4 *nodes, uint32_t ref, ChildBoxes &c) {
-    const float4 *f = reinterpret_cast<const float4 *>(nodes) + 4 * (size_t)ref;
-    const float4 n0 = __ldg(f), n1 = __ldg(f + 1), n2 = __ldg(f + 2);
-    const uint4 n3 = __ldg(nodes + 4 * (size_t)ref + 3);
+    uint4 w0, w1, w2, n3;
+    ldg256(nodes + 4 * (size_t)ref, w0, w1);
+    ldg256(nodes + 4 * (size_t)ref + 2, w2, n3);
+    const float4 n0 = make_float4(__uint_as_float(w0.x), __uint_as_float(w0.y), __uint_as_float(w0.z),
+                                  __uint_as_float(w0.w));
+    const float4 n1 = make_float4(__uint_as_float(w1.x), __uint_as_float(w1.y), __uint_as_float(w1.z),
+                                  __uint_as_float(w1.w));
+    const float4 n2 = make_float4(__uint_as_float(w2.x), __uint_as_float(w2.y), __uint_as_float(w2.z),
+                                  __uint_as_float(w2.w));
     c.lo0x = n0.x;
     c.lo0y = n0.y;
     c.lo0z = n0.z;
