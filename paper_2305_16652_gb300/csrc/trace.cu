@@ -26,7 +26,11 @@ constexpr int STACK = HCC_TRACE_STACK;
 // 1 + 2 * gamma(3), gamma(n) = n u / (1 - n u), u = 2^-24
 constexpr float ROBUST_FAR = 1.0000003576279f;
 constexpr float PRUNE_SLACK = 1.0f + 1.0f / 65536.0f;
-constexpr uint32_t REFILL_MIN = 16;  // idle lanes that make a warp take new rays
+// idle lanes that make a warp take new rays: in input order, and in sorted
+// order (rays fetched through a permutation), where waiting longer keeps the
+// warp's neighbouring rays together (measured faster for each)
+constexpr uint32_t REFILL_MIN = 16;
+constexpr uint32_t REFILL_MIN_SORTED = 24;
 
 __device__ __forceinline__ float byte_to_float(uint32_t w, uint32_t sel) {
     // 0x4B0000bb as float is 2^23 + bb exactly
@@ -368,7 +372,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
 // Persistent variant with ray replacement (Aila & Laine 2009, "replacing
 // terminated rays"): each warp takes ray slots from a global counter, runs
 // traversal rounds, and after each round the lanes whose ray has finished
-// take new slots (all at once, one atomic per warp) as soon as REFILL_MIN of
+// take new slots (all at once, one atomic per warp) as soon as refill_min of
 // them are idle or none is busy.  Slots are handed out in increasing order,
 // so lanes of a warp trace neighbouring slots -- in sorted order, rays with
 // equal keys.  Every ray's record is the same as in k_trace: a ray's own
@@ -387,11 +391,12 @@ __global__ void __launch_bounds__(TRACE_BLOCK, 10) k_trace_pool(TraceArgs a) {
     const float4 *tris = a.tris;
     uint64_t slot = 0;
     bool have = false, exhausted = false;
+    const uint32_t refill_min = a.gather ? REFILL_MIN_SORTED : REFILL_MIN;
     for (;;) {
         const bool want = !have && !exhausted;
         const uint32_t need = __ballot_sync(FULL, want);
         const uint32_t busy = __ballot_sync(FULL, have);
-        if (need && (busy == 0 || (uint32_t)__popc(need) >= REFILL_MIN)) {
+        if (need && (busy == 0 || (uint32_t)__popc(need) >= refill_min)) {
             const int leader = __ffs(need) - 1;
             unsigned long long base = 0;
             if ((int)lane == leader) base = atomicAdd(a.work, (unsigned long long)__popc(need));
