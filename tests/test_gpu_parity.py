@@ -559,3 +559,28 @@ def test_run_host_pipeline_over_chunks(ctx):
     finally:
         hcc.hcc_cut_destroy(cut)
         hcc.hcc_bvh_destroy(bvh)
+
+
+def test_encode_with_an_inverted_cut_box_takes_the_general_test(ctx, tiny):
+    """A cut box with lo > hi on an axis voids the sign-selected slab bounds
+    (they assume lo <= hi); the encoder must notice and give the oracle's keys."""
+    import copy
+    b = copy.deepcopy(tiny.w.bvh)
+    b.lo[0, 1], b.hi[0, 1] = b.hi[0, 1], b.lo[0, 1]  # root box inverted on y
+    h = hcc.hcc_bvh_upload(ctx, b, layout="exact")
+    cut = hcc.hcc_select_cut(ctx, h, 1, 0.125)  # the cut is the root alone
+    try:
+        assert hcc.hcc_cut_info(cut).tolist() == [0]
+        keys = torch.zeros(tiny.n, dtype=torch.int32, device=DEV)
+        hcc.hcc_encode(ctx, "hcc", h, cut, tiny.org, tiny.dir, 8, keys)
+        hcc.hcc_sync(ctx)
+        g = keys.cpu().numpy().view(np.uint32).astype(np.uint64)
+        o = oracle.encode_hcc(tiny.w.rays.org, tiny.w.rays.dir, b.lo[[0]], b.hi[[0]], 8)
+        assert np.array_equal(g, o)
+        # min/max make the test symmetric in lo and hi, so every ray still meets the box;
+        # near/far bounds picked by direction sign (lo near for a positive direction)
+        # would have missed it for most rays
+        assert np.count_nonzero(o) == tiny.n
+    finally:
+        hcc.hcc_cut_destroy(cut)
+        hcc.hcc_bvh_destroy(h)
