@@ -584,3 +584,53 @@ def test_encode_with_an_inverted_cut_box_takes_the_general_test(ctx, tiny):
     finally:
         hcc.hcc_cut_destroy(cut)
         hcc.hcc_bvh_destroy(h)
+
+
+def test_full_size_headline_configuration():
+    """The benchmark's workload and launch configuration (1920x1080x8spp room,
+    16,588,800 rays, ~1M triangles, cut 32, 32-bit keys, exact nodes): keys on a
+    sample against the oracle, the whole permutation by the properties of a
+    stable sort, hits on a sample against the oracle and all hits against NoSort."""
+    w = gen.room_workload(1, target_tris=1_000_000, W=1920, H=1080, spp=8, shadow=False)
+    n = w.rays.n
+    assert n == 16_588_800
+    c = hcc.hcc_create(0)
+    bvh = hcc.hcc_bvh_upload(c, w.bvh, layout="exact")
+    cut = hcc.hcc_select_cut(c, bvh, 32, 0.125)
+    try:
+        ids = hcc.hcc_cut_info(cut)
+        assert ids.tolist() == oracle.select_cut(w.bvh, 32).tolist()
+        org = torch.from_numpy(w.rays.org).to(DEV)
+        dir_ = torch.from_numpy(w.rays.dir).to(DEV)
+        keys = torch.empty(n, dtype=torch.int32, device=DEV)
+        perm = torch.empty(n, dtype=torch.int32, device=DEV)
+        hcc.hcc_encode(c, "hcc", bvh, cut, org, dir_, 32, keys)
+        hcc.hcc_sort(c, keys, 32, n, perm)
+        hits = torch.empty((n, 4), dtype=torch.int32, device=DEV)
+        hcc.hcc_trace_sorted(c, bvh, org, dir_, perm, hits)
+        hits0 = torch.empty_like(hits)
+        hcc.hcc_trace(c, bvh, org, dir_, hits0)
+        hcc.hcc_sync(c)
+        assert torch.equal(hits, hits0)
+        k = keys.cpu().numpy().view(np.uint32).astype(np.uint64)
+        p = perm.cpu().numpy().view(np.uint32).astype(np.int64)
+        rng = np.random.default_rng(11)
+        idx = rng.choice(n, 20_000, replace=False)
+        ref_k = oracle.encode_hcc(w.rays.org[idx], w.rays.dir[idx], w.bvh.lo[ids], w.bvh.hi[ids], 32)
+        bad = np.nonzero(k[idx] != ref_k)[0]
+        if len(bad):
+            m = oracle.key_margin(w.rays.org[idx[bad]], w.rays.dir[idx[bad]], w.bvh.lo[ids], w.bvh.hi[ids], 32)
+            assert np.all(m < 1e-6)
+        # the permutation: every id once, keys non-decreasing, equal keys in id order
+        assert np.array_equal(np.sort(p), np.arange(n))
+        ks = k[p]
+        assert np.all(ks[1:] >= ks[:-1])
+        same = ks[1:] == ks[:-1]
+        assert np.all(p[1:][same] > p[:-1][same])
+        sample = idx[:3000]
+        ref_h = oracle.trace_bvh(w.bvh, w.rays.org[sample], w.rays.dir[sample])
+        assert hcc.hits_to_numpy(hits)[sample].tobytes() == ref_h.tobytes()
+    finally:
+        hcc.hcc_cut_destroy(cut)
+        hcc.hcc_bvh_destroy(bvh)
+        hcc.hcc_destroy(c)
