@@ -59,6 +59,8 @@ def _load():
     lib.oracle_encode_ppc.argtypes = [u64, P, P, u32, P, P, P, P, u32, P]
     lib.oracle_encode_ppc.restype = None
     lib.oracle_encode_twopoint.argtypes = [u64, P, P, P, P, u32, P]
+    lib.oracle_encode_twopoint_frac.argtypes = [u64, P, P, P, P, f32, u32, P]
+    lib.oracle_encode_twopoint_frac.restype = None
     lib.oracle_encode_twopoint.restype = None
     lib.oracle_encode_origin.argtypes = [u64, P, P, P, u32, P]
     lib.oracle_encode_origin.restype = None
@@ -183,12 +185,16 @@ def encode_ppc(org, dir, bvh, key_bits: int) -> np.ndarray:
     return keys
 
 
-def encode_twopoint(org, dir, scene_lo, scene_hi, key_bits: int) -> np.ndarray:
+def encode_twopoint(org, dir, scene_lo, scene_hi, key_bits: int, fraction=None) -> np.ndarray:
+    """TwoPoint keys; fraction = estimated ray length / largest scene extent (None: Sec. 5's 0.25)."""
     org, dir = _c(org, np.float32), _c(dir, np.float32)
     lo, hi = _c(scene_lo, np.float32), _c(scene_hi, np.float32)
     n = org.shape[0]
     keys = np.zeros(n, np.uint64)
-    _load().oracle_encode_twopoint(n, _p(org), _p(dir), _p(lo), _p(hi), key_bits, _p(keys))
+    if fraction is None:
+        _load().oracle_encode_twopoint(n, _p(org), _p(dir), _p(lo), _p(hi), key_bits, _p(keys))
+    else:
+        _load().oracle_encode_twopoint_frac(n, _p(org), _p(dir), _p(lo), _p(hi), fraction, key_bits, _p(keys))
     return keys
 
 

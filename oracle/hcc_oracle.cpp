@@ -236,10 +236,12 @@ void oracle_key_margin(uint64_t n, const float *org, const float *dir, uint32_t 
 // coordinates of (origin, estimated termination) is normalised to the scene
 // box, quantised to b = floor(k/6) bits and the bits are interleaved from the
 // most significant level down (Morton order).
-void oracle_encode_twopoint(uint64_t n, const float *org, const float *dir, const float *scene_lo,
-                            const float *scene_hi, uint32_t key_bits, uint64_t *keys) {
+// The estimated ray length is `fraction` of the largest extent (App. B
+// sweeps it; Sec. 5 uses 0.25, the value oracle_encode_twopoint passes).
+void oracle_encode_twopoint_frac(uint64_t n, const float *org, const float *dir, const float *scene_lo,
+                                 const float *scene_hi, float fraction, uint32_t key_bits, uint64_t *keys) {
     float ext[3] = {scene_hi[0] - scene_lo[0], scene_hi[1] - scene_lo[1], scene_hi[2] - scene_lo[2]};
-    float L = 0.25f * std::fmax(ext[0], std::fmax(ext[1], ext[2]));
+    float L = fraction * std::fmax(ext[0], std::fmax(ext[1], ext[2]));
     uint32_t b = key_bits / 6;
     double levels = std::ldexp(1.0, (int)b);
     uint32_t qmax = (b == 0) ? 0u : ((1u << b) - 1u);
@@ -261,6 +263,11 @@ void oracle_encode_twopoint(uint64_t n, const float *org, const float *dir, cons
         if (key_bits > 6 * b) key <<= (key_bits - 6 * b);
         keys[i] = key;
     }
+}
+
+void oracle_encode_twopoint(uint64_t n, const float *org, const float *dir, const float *scene_lo,
+                            const float *scene_hi, uint32_t key_bits, uint64_t *keys) {
+    oracle_encode_twopoint_frac(n, org, dir, scene_lo, scene_hi, 0.25f, key_bits, keys);
 }
 
 // ------------------------------------------------ method variants (Sec. 4.1, 4.3, 5)

@@ -565,3 +565,23 @@ def test_spawn_rays_are_cosine_distributed_on_the_visible_side():
     assert np.all(oo3[::2, 3] == 1) and np.all(od3[::2, 3] == 0)
     _, od4 = oracle.spawn(org, dir_, hits, tri, seed=8, tmin=1e-4)
     assert not np.array_equal(od3[1::2], od4[1::2])
+
+
+def test_twopoint_length_fraction_scales_the_direction():
+    # termination o + (f * E) d: for powers of two, f = 0.5 with d equals f = 0.25 with 2 d
+    # bit for bit (the scalings are exact), and f = 0 puts the termination on the origin
+    w = gen.tiny_workload(0, ntris=2000, nrays=1500)
+    o, d = w.rays.org, w.rays.dir
+    lo, hi = w.bvh.lo[0], w.bvh.hi[0]
+    base = oracle.encode_twopoint(o, d, lo, hi, 60)
+    assert np.array_equal(base, oracle.encode_twopoint(o, d, lo, hi, 60, fraction=0.25))
+    for f, s in ((0.5, 2.0), (1.0, 4.0), (0.125, 0.5)):
+        d2 = d.copy()
+        d2[:, :3] *= s
+        assert np.array_equal(oracle.encode_twopoint(o, d, lo, hi, 60, fraction=f),
+                              oracle.encode_twopoint(o, d2, lo, hi, 60))
+    zero = d.copy()
+    zero[:, :3] = 0.0
+    assert np.array_equal(oracle.encode_twopoint(o, d, lo, hi, 60, fraction=0.0),
+                          oracle.encode_twopoint(o, zero, lo, hi, 60))
+    assert not np.array_equal(oracle.encode_twopoint(o, d, lo, hi, 60, fraction=0.75), base)
