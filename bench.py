@@ -577,6 +577,68 @@ def run_methods_sweep(args):
     print(json.dumps(out), flush=True)
 
 
+def run_hyper_sweep(args):
+    """Hyperparameter study (App. B): the HAD weight lambda of Eq. 1 for HCC (cut 32,
+    32-bit keys) and the TwoPoint estimated ray length as a fraction of the largest
+    scene extent, each from 0.1 to 1.0, on the 1080p wavefront; per point the stage
+    times, end-to-end Mrays/s, trace speedup over NoSort and ANC."""
+    import torch
+    from paper_2305_16652_gb300 import build, hcc
+    build()
+    dev = torch.device("cuda", 0)
+    w = make_workload(1, args.quick)
+    n = w.rays.n
+    ctx = hcc.hcc_create(0)
+    bvh = hcc.hcc_bvh_upload(ctx, w.bvh, layout=args.layout)
+    hcc.hcc_reserve(ctx, n, 32)
+    org = torch.from_numpy(w.rays.org).to(dev)
+    dir_ = torch.from_numpy(w.rays.dir).to(dev)
+    keys = torch.empty(n, dtype=torch.int32, device=dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    hits = torch.empty((n, 4), dtype=torch.int32, device=dev)
+
+    def tm(f, reps=5):
+        ts = []
+        for _ in range(reps + 2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            f()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts[2:])
+
+    t0 = tm(lambda: hcc.hcc_trace(ctx, bvh, org, dir_, hits))
+
+    def point(method, cut):
+        te = tm(lambda: hcc.hcc_encode(ctx, method, bvh, cut, org, dir_, 32, keys))
+        ts = tm(lambda: hcc.hcc_sort(ctx, keys, 32, n, perm))
+        tt = tm(lambda: hcc.hcc_trace_sorted(ctx, bvh, org, dir_, perm, hits))
+        st = hcc.hcc_key_stats(ctx, keys, 32, perm, n)
+        hcc.hcc_sync(ctx)
+        return {"encode_ms": round(te, 4), "sort_ms": round(ts, 4), "trace_ms": round(tt, 4),
+                "mrays_s": round(n / ((te + ts + tt) * 1e3), 1), "trace_speedup_vs_nosort": round(t0 / tt, 3),
+                "anc": round(st["anc"], 4)}
+
+    grid = [round(0.1 * i, 1) for i in range(1, 11)]
+    lam_rows, tp_rows = [], []
+    for lam in grid:
+        cut = hcc.hcc_select_cut(ctx, bvh, 32, lam)
+        lam_rows.append({"lambda": lam, **point("hcc", cut)})
+        hcc.hcc_cut_destroy(cut)
+    for f in grid:
+        hcc.hcc_set_twopoint_distance(ctx, f)
+        tp_rows.append({"fraction": f, **point("twopoint", None)})
+    hcc.hcc_set_twopoint_distance(ctx, 0.25)
+    out = {"metric": "hyperparameter study: HCC lambda and TwoPoint length fraction", "unit": "Mrays/s",
+           "config": {"workload": w.name + f" ({n} secondary rays)", "bvh_layout": args.layout, "cut_size": 32,
+                      "key_bits": 32},
+           "nosort_trace_ms": round(t0, 4), "hcc_lambda": lam_rows, "twopoint_fraction": tp_rows}
+    hcc.hcc_bvh_destroy(bvh)
+    hcc.hcc_destroy(ctx)
+    print(json.dumps(out), flush=True)
+
+
 def run_batch_sweep(args):
     """Batched wavefronts: 16 rooms (seeds 2-17, 50k-2M triangles) with log-uniform
     wavefronts of 64k-8M rays, two bounces, each bounce one captured CUDA graph
@@ -912,7 +974,7 @@ def main(argv=None):
     ap.add_argument("--ref-sample", type=int, default=300_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", choices=["trace-small", "sort-16m"], help="run a small profiling case and exit")
-    ap.add_argument("--sweep", choices=["keylen", "batch", "serve", "methods"],
+    ap.add_argument("--sweep", choices=["keylen", "batch", "serve", "methods", "hyper"],
                     help="run a study instead of the headline benchmark")
     ap.add_argument("--slots", type=int, default=4, help="serving: requests on the GPU at once")
     ap.add_argument("--serve-requests", type=int, default=1000, help="serving: requests per run")
@@ -927,6 +989,8 @@ def main(argv=None):
         return run_serve_sweep(args)
     if args.sweep == "methods":
         return run_methods_sweep(args)
+    if args.sweep == "hyper":
+        return run_hyper_sweep(args)
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = dist_env()
     if world > 1:

@@ -148,6 +148,12 @@ typedef enum hcc_trace_schedule {
 
 hcc_status hcc_set_trace_schedule(hcc_ctx *ctx, hcc_trace_schedule schedule);
 
+/* The TwoPoint key's estimated ray length as a fraction of the root box's
+ * largest extent (App. B sweeps it; Sec. 5 and the default use 0.25), for
+ * this context's hcc_encode and hcc_run.  Batches and servers use 0.25.
+ * Errors: INVALID_ARG (negative or not finite). */
+hcc_status hcc_set_twopoint_distance(hcc_ctx *ctx, float fraction);
+
 /* Wait for all work queued on the context's stream, then read and clear the
  * device error word: STACK_OVERFLOW or TIMEOUT if a kernel reported one
  * since the last hcc_sync, INVALID_ARG if a gather or scatter met an index

@@ -33,6 +33,7 @@ struct hcc_ctx {
     uint32_t *d_err = nullptr;                 // device error word (16-byte allocation) ...
     unsigned long long *d_work = nullptr;      // ... whose second half is the trace's slot counter
     hcc_trace_schedule schedule = HCC_TRACE_AUTO;
+    float twopoint_fraction = 0.25f;            // TwoPoint length estimate / largest extent
     std::string last_error;
     DevBuf sort_scratch;
     DevBuf keys, perm;                          // hcc_run
@@ -377,6 +378,16 @@ hcc_status hcc_set_trace_schedule(hcc_ctx *ctx, hcc_trace_schedule schedule) {
     if (schedule != HCC_TRACE_AUTO && schedule != HCC_TRACE_PER_RAY && schedule != HCC_TRACE_REFILL)
         return fail(ctx, HCC_ERR_INVALID_ARG, "unknown trace schedule");
     ctx->schedule = schedule;
+    return HCC_OK;
+}
+
+hcc_status hcc_set_twopoint_distance(hcc_ctx *ctx, float fraction) {
+    if (!ctx) return HCC_ERR_INVALID_ARG;
+    if (!(fraction >= 0.0f) || !std::isfinite(fraction))
+        return fail(ctx, HCC_ERR_INVALID_ARG, "the TwoPoint distance must be finite and non-negative");
+    ctx->twopoint_fraction = fraction;
+    for (hcc_ctx *l : ctx->lane)
+        if (l) l->twopoint_fraction = fraction;
     return HCC_OK;
 }
 
@@ -879,7 +890,7 @@ hcc_status hcc_encode(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const
             ext[a] = bvh->hi[a] - bvh->lo[a];
         }
         if (method == HCC_METHOD_TWOPOINT) {
-            const float L = 0.25f * std::max(ext[0], std::max(ext[1], ext[2]));
+            const float L = ctx->twopoint_fraction * std::max(ext[0], std::max(ext[1], ext[2]));
             e = launch_encode_twopoint(ctx->stream, o, d, rays->n, lo, ext, L, key_bits, keys);
         } else if (method == HCC_METHOD_ORIGIN) {
             e = launch_encode_origin(ctx->stream, o, rays->n, lo, ext, key_bits, keys);
@@ -1386,6 +1397,7 @@ hcc_status hcc_run_host(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, con
     for (uint64_t c0 = 0, c = 0; c0 < n && result == HCC_OK; c0 += HOST_CHUNK, ++c) {
         hcc_ctx *L = ctx->lane[c % HOST_LANES];
         L->schedule = ctx->schedule;
+        L->twopoint_fraction = ctx->twopoint_fraction;
         const uint64_t m = std::min<uint64_t>(HOST_CHUNK, n - c0);
         if ((st = ensure(L, L->in_org, HOST_CHUNK * 16, "input rays")) != HCC_OK ||
             (st = ensure(L, L->in_dir, HOST_CHUNK * 16, "input rays")) != HCC_OK ||

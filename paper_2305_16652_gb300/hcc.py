@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
         "hcc_destroy": [P],
         "hcc_set_stream": [P, P],
         "hcc_set_trace_schedule": [P, i32],
+        "hcc_set_twopoint_distance": [P, ctypes.c_float],
         "hcc_reserve": [P, u64, u32],
         "hcc_sync": [P],
         "hcc_bvh_upload": [P, ctypes.POINTER(_BvhDesc), PP],
@@ -232,6 +233,11 @@ TRACE_SCHEDULES = {"auto": 0, "per_ray": 1, "refill": 2}
 def hcc_set_trace_schedule(ctx, schedule="auto"):
     """Ray scheduling of the context's traces: auto, per_ray or refill."""
     _check(load().hcc_set_trace_schedule(ctx, TRACE_SCHEDULES.get(schedule, schedule)), ctx)
+
+
+def hcc_set_twopoint_distance(ctx, fraction: float = 0.25):
+    """TwoPoint ray-length estimate as a fraction of the largest scene extent."""
+    _check(load().hcc_set_twopoint_distance(ctx, fraction), ctx)
 
 
 def hcc_select_cut(ctx, bvh, cut_size: int, lam: float = 0.125):

@@ -634,3 +634,17 @@ def test_full_size_headline_configuration():
         hcc.hcc_cut_destroy(cut)
         hcc.hcc_bvh_destroy(bvh)
         hcc.hcc_destroy(c)
+
+
+@pytest.mark.parametrize("fraction", [0.0, 0.1, 0.5, 1.0])
+def test_twopoint_distance_fraction_matches_oracle(ctx, room, fraction):
+    try:
+        hcc.hcc_set_twopoint_distance(ctx, fraction)
+        g = gpu_encode(ctx, room, "twopoint", 48)
+    finally:
+        hcc.hcc_set_twopoint_distance(ctx, 0.25)
+    o = oracle.encode_twopoint(room.w.rays.org, room.w.rays.dir, room.w.bvh.lo[0], room.w.bvh.hi[0], 48,
+                               fraction=fraction)
+    assert np.array_equal(g, o)
+    with pytest.raises(hcc.HccError):
+        hcc.hcc_set_twopoint_distance(ctx, -1.0)
