@@ -156,11 +156,12 @@ class ClockSampler:
 
 # -------------------------------------------------------------- workload
 
-def make_workload(seed: int, quick: bool, shadow: bool = False):
+def make_workload(seed: int, quick: bool, shadow: bool = False, limited: bool = False):
     from paper_2305_16652_gb300 import gen
+    camera = gen.LIMITED_CAMERA if limited else gen.ROOM_CAMERA
     if quick:
-        return gen.room_workload(seed, target_tris=200_000, W=480, H=270, spp=8, shadow=shadow)
-    return gen.room_workload(seed, target_tris=1_000_000, W=1920, H=1080, spp=8, shadow=shadow)
+        return gen.room_workload(seed, target_tris=200_000, W=480, H=270, spp=8, shadow=shadow, camera=camera)
+    return gen.room_workload(seed, target_tris=1_000_000, W=1920, H=1080, spp=8, shadow=shadow, camera=camera)
 
 
 def peaks():
@@ -507,7 +508,7 @@ def run_methods_sweep(args):
     from paper_2305_16652_gb300 import build, hcc
     build()
     dev = torch.device("cuda", 0)
-    w = make_workload(1, args.quick, shadow=True)
+    w = make_workload(1, args.quick, shadow=True, limited=args.viewport == "limited")
     ctx = hcc.hcc_create(0)
     bvh = hcc.hcc_bvh_upload(ctx, w.bvh, layout=args.layout)
 
@@ -977,6 +978,8 @@ def main(argv=None):
     ap.add_argument("--sweep", choices=["keylen", "batch", "serve", "methods", "hyper"],
                     help="run a study instead of the headline benchmark")
     ap.add_argument("--slots", type=int, default=4, help="serving: requests on the GPU at once")
+    ap.add_argument("--viewport", choices=["full", "limited"], default="full",
+                    help="method study: the 60-degree room view or a 10-degree view of the floor (Sec. 6.3)")
     ap.add_argument("--serve-requests", type=int, default=1000, help="serving: requests per run")
     args = ap.parse_args(argv)
     if args.case:

@@ -269,14 +269,23 @@ def serve_requests(seed: int, count: int, pool_sizes, rays_range=(65_536, 4_194_
     return {"scene": scene, "n": n, "offset": off, "gap": gap}
 
 
+ROOM_CAMERA = ((5.0, 1.6, 0.4), (5.0, 1.2, 8.0), 60.0)
+# a limited viewport (Sec. 6.3): a narrow view of the floor from the same eye point
+LIMITED_CAMERA = ((5.0, 1.6, 0.4), (5.5, 0.0, 4.0), 10.0)
+
+
 def room_workload(seed: int = 1, target_tris: int = 1_000_000, W: int = 1920, H: int = 1080, spp: int = 8,
-                  shadow: bool = True, bvh: BVH | None = None, tris: np.ndarray | None = None) -> Workload:
-    """Closed furnished room, one diffuse bounce plus 2 shadow rays per sample."""
+                  shadow: bool = True, bvh: BVH | None = None, tris: np.ndarray | None = None,
+                  camera=ROOM_CAMERA) -> Workload:
+    """Closed furnished room, one diffuse bounce plus 2 shadow rays per sample.
+    camera = (eye, target, vertical FOV in degrees)."""
     if tris is None:
         tris = room_tris(seed, target_tris)
     if bvh is None:
         bvh = build_bvh(tris)
-    sec, sh, prim = camera_rays(tris, (5.0, 1.6, 0.4), (5.0, 1.2, 8.0), 60.0, W, H, spp, seed,
+    eye, target, vfov = camera
+    sec, sh, prim = camera_rays(tris, eye, target, vfov, W, H, spp, seed,
                                 sample_major=False, n_shadow=2 if shadow else 0, lights=ROOM_LIGHTS,
                                 light_half=0.25)
-    return Workload(f"room-{tris.shape[0]}-tris-{W}x{H}x{spp}spp", tris, bvh, sec, sh, prim)
+    tag = "" if camera == ROOM_CAMERA else f"-fov{vfov:g}"
+    return Workload(f"room-{tris.shape[0]}-tris-{W}x{H}x{spp}spp{tag}", tris, bvh, sec, sh, prim)
