@@ -43,8 +43,11 @@ SMS, LANES_PER_SM = 152, 128
 # 12 min/max, 1 mul, 1 min each = 26) and orders/pushes (~10); the quantised
 # layout adds the decode of 12 bounds (byte select, convert, outward fma: 3
 # ops each) and of the node frame (6); one triangle test is the
-# Moller-Trumbore sequence (~45 ops incl. the reciprocal).
-OPS_PER_NODE = {"exact": 2 * 26 + 10, "quantised": 36 + 6 + 2 * 26 + 10}
+# Moller-Trumbore sequence (~45 ops incl. the reciprocal).  A 4-ary node
+# visit (wide layout) runs four directed slab tests (6 fma, 5 min/max/mul,
+# 4 to mark and clamp the met child = 15 each), selects its near/far rows
+# (9), sorts the four entries (5 exchanges of 5 ops) and pushes (~12).
+OPS_PER_NODE = {"exact": 2 * 26 + 10, "quantised": 36 + 6 + 2 * 26 + 10, "wide": 4 * 15 + 9 + 25 + 12}
 OPS_PER_TRI = 45
 # HBM bytes each stage must move per ray (32-bit keys; see the design notes)
 BYTES_ENCODE = 32 + 4
@@ -969,7 +972,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cut-size", type=int, default=32)
     ap.add_argument("--key-bits", type=int, default=32)
-    ap.add_argument("--layout", choices=["exact", "quantised"], default="exact")
+    ap.add_argument("--layout", choices=["exact", "quantised", "wide"], default="exact")
     ap.add_argument("--quick", action="store_true", help="480x270 image, 200k triangles (development only)")
     ap.add_argument("--cpu-sample", type=int, default=1_500_000)
     ap.add_argument("--ref-sample", type=int, default=300_000)

@@ -181,12 +181,17 @@ hcc_status hcc_bvh_upload(hcc_ctx *ctx, const hcc_bvh_desc *desc, hcc_bvh **out)
  * children's boxes and references). */
 typedef enum hcc_bvh_layout {
     HCC_BVH_QUANTISED = 0, /* 32 bytes: 8-bit child bounds on a per-node power-of-two grid, rounded outward */
-    HCC_BVH_EXACT = 1      /* 64 bytes: the children's exact FP32 boxes */
+    HCC_BVH_EXACT = 1,     /* 64 bytes: the children's exact FP32 boxes */
+    HCC_BVH_WIDE = 2       /* 128 bytes: a 4-ary node collapsed from the BVH2 (each internal child with
+                              the largest surface area replaced by its two children until four are
+                              held), the children's exact FP32 boxes as rows of four per bound */
 } hcc_bvh_layout;
 
-/* hcc_bvh_upload with a choice of node layout.  Both layouts give the same
- * hits (boxes only decide which triangles are tested); the quantised one
- * halves node memory, the exact one avoids decoding work per node visit.
+/* hcc_bvh_upload with a choice of node layout.  Every layout gives the same
+ * hits (boxes only decide which triangles are tested, and every box holds
+ * the exact box of its BVH2 node); the quantised one halves node memory, the
+ * exact one avoids decoding work per node visit, and the wide one visits
+ * about half as many nodes per ray.  Cuts are always chosen on the BVH2.
  * Errors: as hcc_bvh_upload, plus INVALID_ARG for an unknown layout. */
 hcc_status hcc_bvh_upload_layout(hcc_ctx *ctx, const hcc_bvh_desc *desc, hcc_bvh_layout layout, hcc_bvh **out);
 

@@ -3,6 +3,7 @@
 // the per-bounce pipeline (Sec. 5).  Kernels live in encode.cu, sort.cu,
 // gather.cu and trace.cu.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -462,6 +463,69 @@ hcc_status hcc_sync(hcc_ctx *ctx) {
 
 // ------------------------------------------------------------------- BVH
 
+// 4-ary traversal nodes from a validated BVH2 (root internal): starting
+// from a BVH2 node's two children, the internal child with the largest
+// surface area is replaced by its two children until four are held or all
+// are leaves (the usual collapse of a binary tree into a wide one).  Node i
+// is 32 words, eight rows of four (one entry per child): lo.x, hi.x, lo.y,
+// hi.y, lo.z, hi.z of the exact boxes of the BVH2 nodes they stand for,
+// the references, and zeros; an unused child has reference 0xFFFFFFFF and
+// a zero box.  Returns the node count.
+static uint32_t collapse_wide(const hcc_bvh_desc *d, std::vector<uint32_t> &words) {
+    auto is_leaf = [&](int32_t k) { return d->left[k] < 0; };
+    auto leaf_ref = [&](int32_t k) { return REF_LEAF | ((d->count[k] - 1u) << 29) | d->first[k]; };
+    auto area = [&](int32_t k) {
+        const double ex = (double)d->hi[3 * k] - d->lo[3 * k], ey = (double)d->hi[3 * k + 1] - d->lo[3 * k + 1],
+                     ez = (double)d->hi[3 * k + 2] - d->lo[3 * k + 2];
+        return ex * ey + ey * ez + ez * ex;
+    };
+    std::vector<int32_t> order{0};  // BVH2 node of each wide node, in creation order
+    std::vector<std::array<int32_t, 4>> slots;
+    std::vector<uint32_t> used;
+    for (size_t w = 0; w < order.size(); ++w) {
+        const int32_t k = order[w];
+        std::vector<int32_t> ch{d->left[k], d->right[k]};
+        while (ch.size() < 4) {
+            int best = -1;
+            double best_a = -1.0;
+            for (int c = 0; c < (int)ch.size(); ++c)
+                if (!is_leaf(ch[c]) && area(ch[c]) > best_a) {
+                    best = c;
+                    best_a = area(ch[c]);
+                }
+            if (best < 0) break;
+            const int32_t n = ch[best];
+            ch[best] = d->left[n];
+            ch.insert(ch.begin() + best + 1, d->right[n]);
+        }
+        std::array<int32_t, 4> sl{-1, -1, -1, -1};
+        for (size_t c = 0; c < ch.size(); ++c) sl[c] = ch[c];
+        slots.push_back(sl);
+        used.push_back((uint32_t)ch.size());
+        for (int32_t c : ch)
+            if (!is_leaf(c)) order.push_back(c);
+    }
+    std::vector<int32_t> widx(d->num_nodes, -1);
+    for (size_t w = 0; w < order.size(); ++w) widx[order[w]] = (int32_t)w;
+    words.assign(order.size() * 32, 0u);
+    for (size_t w = 0; w < order.size(); ++w) {
+        uint32_t *q = &words[32 * w];
+        for (uint32_t c = 0; c < 4; ++c) {
+            if (c >= used[w]) {
+                q[24 + c] = 0xFFFFFFFFu;
+                continue;
+            }
+            const int32_t k = slots[w][c];
+            for (int a = 0; a < 3; ++a) {
+                std::memcpy(&q[8 * a + c], d->lo + 3 * (size_t)k + a, 4);
+                std::memcpy(&q[8 * a + 4 + c], d->hi + 3 * (size_t)k + a, 4);
+            }
+            q[24 + c] = is_leaf(k) ? leaf_ref(k) : (uint32_t)widx[k];
+        }
+    }
+    return (uint32_t)order.size();
+}
+
 hcc_status hcc_bvh_upload(hcc_ctx *ctx, const hcc_bvh_desc *d, hcc_bvh **out) {
     return hcc_bvh_upload_layout(ctx, d, HCC_BVH_QUANTISED, out);
 }
@@ -469,7 +533,7 @@ hcc_status hcc_bvh_upload(hcc_ctx *ctx, const hcc_bvh_desc *d, hcc_bvh **out) {
 hcc_status hcc_bvh_upload_layout(hcc_ctx *ctx, const hcc_bvh_desc *d, hcc_bvh_layout layout, hcc_bvh **out) {
     if (!ctx || !d || !out) return fail(ctx, HCC_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
-    if (layout != HCC_BVH_QUANTISED && layout != HCC_BVH_EXACT)
+    if (layout != HCC_BVH_QUANTISED && layout != HCC_BVH_EXACT && layout != HCC_BVH_WIDE)
         return fail(ctx, HCC_ERR_INVALID_ARG, "unknown BVH layout");
     if (d->num_nodes == 0 || d->num_tris == 0) return fail(ctx, HCC_ERR_INVALID_ARG, "empty BVH");
     if (!d->lo || !d->hi || !d->left || !d->right || !d->first || !d->count || !d->tris || !d->order)
@@ -512,17 +576,36 @@ hcc_status hcc_bvh_upload_layout(hcc_ctx *ctx, const hcc_bvh_desc *d, hcc_bvh_la
         if (d->left[k] < 0) return REF_LEAF | ((d->count[k] - 1u) << 29) | d->first[k];
         return (uint32_t)qidx[k];
     };
-    const size_t wpn = layout == HCC_BVH_EXACT ? 16 : 8;  // 32-bit words per node
-    std::vector<uint32_t> words((size_t)std::max<size_t>(internal.size(), 1) * wpn, 0u);
-    for (size_t i = 0; i < internal.size(); ++i) {
+    // node boxes with lo <= hi on every axis (the traversal's slab test picks
+    // the near plane by the direction's sign); a box given inverted on an
+    // axis means the same slab to a min/max slab test, so it is swapped
+    std::vector<float> blo(d->lo, d->lo + 3 * (size_t)N), bhi(d->hi, d->hi + 3 * (size_t)N);
+    for (size_t j = 0; j < blo.size(); ++j)
+        if (blo[j] > bhi[j]) std::swap(blo[j], bhi[j]);
+    hcc_bvh_desc nd = *d;
+    nd.lo = blo.data();
+    nd.hi = bhi.data();
+    std::vector<uint32_t> words;
+    uint32_t num_device_nodes = (uint32_t)internal.size();
+    if (layout == HCC_BVH_WIDE) {
+        if (internal.empty())
+            words.assign(32, 0u);  // a leaf root: the traversal reads no node
+        else
+            num_device_nodes = collapse_wide(&nd, words);
+    } else {
+        const size_t wpn = layout == HCC_BVH_EXACT ? 16 : 8;  // 32-bit words per node
+        words.assign((size_t)std::max<size_t>(internal.size(), 1) * wpn, 0u);
+    }
+    for (size_t i = 0; layout != HCC_BVH_WIDE && i < internal.size(); ++i) {
+        const size_t wpn = layout == HCC_BVH_EXACT ? 16 : 8;
         const int32_t k = internal[i], l = d->left[k], r = d->right[k];
         uint32_t *w = &words[wpn * i];
         if (layout == HCC_BVH_QUANTISED) {
-            quantise_node(d->lo + 3 * l, d->hi + 3 * l, d->lo + 3 * r, d->hi + 3 * r, ref_of(l), ref_of(r), w);
+            quantise_node(&blo[3 * l], &bhi[3 * l], &blo[3 * r], &bhi[3 * r], ref_of(l), ref_of(r), w);
         } else {
-            const float f[12] = {d->lo[3 * l], d->lo[3 * l + 1], d->lo[3 * l + 2], d->hi[3 * l],
-                                 d->hi[3 * l + 1], d->hi[3 * l + 2], d->lo[3 * r], d->lo[3 * r + 1],
-                                 d->lo[3 * r + 2], d->hi[3 * r], d->hi[3 * r + 1], d->hi[3 * r + 2]};
+            const float f[12] = {blo[3 * l], blo[3 * l + 1], blo[3 * l + 2], bhi[3 * l],
+                                 bhi[3 * l + 1], bhi[3 * l + 2], blo[3 * r], blo[3 * r + 1],
+                                 blo[3 * r + 2], bhi[3 * r], bhi[3 * r + 1], bhi[3 * r + 2]};
             std::memcpy(w, f, sizeof f);
             w[12] = ref_of(l);
             w[13] = ref_of(r);
@@ -549,7 +632,7 @@ hcc_status hcc_bvh_upload_layout(hcc_ctx *ctx, const hcc_bvh_desc *d, hcc_bvh_la
     b->device = ctx->device;
     b->layout = layout;
     b->num_nodes = N;
-    b->num_internal = (uint32_t)internal.size();
+    b->num_internal = num_device_nodes;
     b->num_tris = T;
     b->depth = depth;
     b->root_ref = ref_of(0);

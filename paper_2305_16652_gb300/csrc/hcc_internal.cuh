@@ -33,6 +33,9 @@ constexpr uint32_t REF_TRI_MASK = 0x1FFFFFFFu;
 // Exact layout: one internal node = 64 bytes = four uint4: the children's
 // FP32 boxes c0.lo.xyz c0.hi.x | c0.hi.yz c1.lo.xy | c1.lo.z c1.hi.xyz |
 // ref0 ref1 0 0.
+// Wide layout: one 4-ary node = 128 bytes = eight float4 rows, one entry per
+// child: lo.x, hi.x, lo.y, hi.y, lo.z, hi.z, references, zeros; an unused
+// child has ref 0xFFFFFFFF.  An internal reference indexes wide nodes.
 
 // Triangle record = three float4: (v0.xyz, id bits), (e1.xyz, 0), (e2.xyz, 0)
 // with e1 = v1 - v0, e2 = v2 - v0 rounded to float.
@@ -130,8 +133,8 @@ cudaError_t launch_gather(cudaStream_t s, const float4 *in_org, const float4 *in
                           const uint32_t *perm, float4 *out_org, float4 *out_dir, uint64_t n, uint32_t *err);
 
 struct TraceArgs {
-    const uint4 *nodes = nullptr;  // 2 (quantised) or 4 (exact) per node
-    int layout = 0;          // 0 = 32-byte quantised, 1 = 64-byte exact
+    const uint4 *nodes = nullptr;  // 2 (quantised), 4 (exact) or 8 (wide) per node
+    int layout = 0;          // 0 = 32-byte quantised, 1 = 64-byte exact, 2 = 128-byte wide
     const float4 *tris = nullptr;  // 3 per triangle
     uint32_t root_ref = 0;
     const float4 *org = nullptr;

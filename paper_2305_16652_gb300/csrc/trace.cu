@@ -1,13 +1,15 @@
 // Closest-hit / any-hit tracing: stack-based traversal of the BVH2 (Sec. 3.1)
 // with the Moller-Trumbore ray/triangle test (1997).  GB300 has no
 // ray-tracing cores, so traversal is software: one thread per ray, each
-// internal node holding both children's boxes (32-byte 8-bit quantised
-// layout, or 64-byte exact FP32 layout), a per-thread stack of
-// (node, entry distance) pairs.
+// internal node holding its children's boxes (32-byte 8-bit quantised
+// layout or 64-byte exact FP32 layout of the BVH2, or 128-byte 4-ary nodes
+// collapsed from it), a per-thread stack of (node, entry distance) pairs.
 //
 // Robustness: decoded child boxes are rounded outward (they contain the exact
-// boxes), the slab test widens the far distance by 1 + 2*gamma(3) (Ize 2013,
-// "Robust BVH Ray Traversal"), and a subtree is dropped only when its entry
+// boxes), the slab distances are directed-rounding bounds of the distances
+// under the rounded reciprocal direction, the far distance is widened by
+// 1 + 2*gamma(3) for the reciprocal's own rounding (after Ize 2013, "Robust
+// BVH Ray Traversal"), and a subtree is dropped only when its entry
 // distance exceeds the best hit by more than 2^-16 relative, so traversal
 // never loses a triangle that the closest-hit definition would pick.
 // Triangle arithmetic is the canonical Moller-Trumbore sequence with explicit
@@ -30,6 +32,10 @@ constexpr float PRUNE_SLACK = 1.0f + 1.0f / 65536.0f;
 // order (rays fetched through a permutation), where waiting longer keeps the
 // warp's neighbouring rays together (measured faster for each)
 constexpr uint32_t REFILL_MIN = 16;
+// resident blocks per SM the persistent kernel is built for: binary nodes
+// (48 registers) and wide nodes (56)
+constexpr int POOL_BLOCKS = 10;
+constexpr int POOL_BLOCKS_WIDE = 9;
 constexpr uint32_t REFILL_MIN_SORTED = 24;
 
 __device__ __forceinline__ float byte_to_float(uint32_t w, uint32_t sel) {
@@ -41,6 +47,7 @@ constexpr uint32_t SEL0 = 0x7540u, SEL1 = 0x7541u, SEL2 = 0x7542u, SEL3 = 0x7543
 
 struct Ray {
     float ox, oy, oz, tmin, dx, dy, dz, tmax, ix, iy, iz;
+    float lx, ly, lz, ux, uy, uz;  // o * (1/d) rounded down and up, per axis
 };
 
 __device__ __forceinline__ float safe_inv(float d) {
@@ -49,15 +56,34 @@ __device__ __forceinline__ float safe_inv(float d) {
     return __frcp_rn(fabsf(d) > 1e-30f ? d : copysignf(1e-30f, d));
 }
 
-// Entry / exit distance of the ray through one decoded child box.
+// Entry / exit distance of the ray through one decoded child box, in one
+// of two forms that never miss a box the exact slab test meets.
+// Rounded form: t = (bound - o) * inv with round-to-nearest, near and far by
+// min/max per axis; its three roundings make it a relative-error estimate.
+// Directed form (boxes stored with lo <= hi): per axis the near plane is lo
+// for a positive reciprocal direction and hi for a negative one; its
+// distance is bounded from below by one fma rounded down against o * inv
+// rounded up, the far plane's from above by one fma rounded up against
+// o * inv rounded down, so the only error left is the relative one of the
+// rounded reciprocal.  Both widen the far distance by 1 + 2*gamma(3).
+template <bool DIRECTED>
 __device__ __forceinline__ void slab(const Ray &r, float lox, float loy, float loz, float hix, float hiy, float hiz,
                                      float tcap, float &tn, float &tf) {
-    const float ax = __fmul_rn(__fsub_rn(lox, r.ox), r.ix), bx = __fmul_rn(__fsub_rn(hix, r.ox), r.ix);
-    const float ay = __fmul_rn(__fsub_rn(loy, r.oy), r.iy), by = __fmul_rn(__fsub_rn(hiy, r.oy), r.iy);
-    const float az = __fmul_rn(__fsub_rn(loz, r.oz), r.iz), bz = __fmul_rn(__fsub_rn(hiz, r.oz), r.iz);
-    tn = fmax3(fminf(ax, bx), fminf(ay, by), fmaxf(fminf(az, bz), r.tmin));
-    const float f = fmin3(fmaxf(ax, bx), fmaxf(ay, by), fmaxf(az, bz));
-    tf = fminf(__fmul_rn(f, ROBUST_FAR), tcap);
+    if (DIRECTED) {
+        const bool sx = r.ix < 0.0f, sy = r.iy < 0.0f, sz = r.iz < 0.0f;
+        const float ax = __fmaf_rd(sx ? hix : lox, r.ix, -r.ux), bx = __fmaf_ru(sx ? lox : hix, r.ix, -r.lx);
+        const float ay = __fmaf_rd(sy ? hiy : loy, r.iy, -r.uy), by = __fmaf_ru(sy ? loy : hiy, r.iy, -r.ly);
+        const float az = __fmaf_rd(sz ? hiz : loz, r.iz, -r.uz), bz = __fmaf_ru(sz ? loz : hiz, r.iz, -r.lz);
+        tn = fmax3(ax, ay, fmaxf(az, r.tmin));
+        tf = fminf(__fmul_rn(fmin3(bx, by, bz), ROBUST_FAR), tcap);
+    } else {
+        const float ax = __fmul_rn(__fsub_rn(lox, r.ox), r.ix), bx = __fmul_rn(__fsub_rn(hix, r.ox), r.ix);
+        const float ay = __fmul_rn(__fsub_rn(loy, r.oy), r.iy), by = __fmul_rn(__fsub_rn(hiy, r.oy), r.iy);
+        const float az = __fmul_rn(__fsub_rn(loz, r.oz), r.iz), bz = __fmul_rn(__fsub_rn(hiz, r.oz), r.iz);
+        tn = fmax3(fminf(ax, bx), fminf(ay, by), fmaxf(fminf(az, bz), r.tmin));
+        const float f = fmin3(fmaxf(ax, bx), fmaxf(ay, by), fmaxf(az, bz));
+        tf = fminf(__fmul_rn(f, ROBUST_FAR), tcap);
+    }
 }
 
 // Moller-Trumbore on record k; returns true with (t, u, v) on a hit in
@@ -153,6 +179,30 @@ __device__ __forceinline__ void fetch_exact(const uint4 *nodes, uint32_t ref, Ch
     c.ref1 = n3.y;
 }
 
+// Child c of a 128-byte wide node (rows of four floats: lo.x hi.x lo.y
+// hi.y lo.z hi.z, then the four references) given the ray's near and far
+// rows: the directed slab test of its exact box.  t is the child's entry
+// distance if the ray meets it (clamped to the largest float, so +inf
+// marks only unused and missed slots), else +inf.
+__device__ __forceinline__ float wide_child(const Ray &r, float nx, float ny, float nz, float fx, float fy, float fz,
+                                            uint32_t ref, float tcap) {
+    const float tn = fmax3(__fmaf_rd(nx, r.ix, -r.ux), __fmaf_rd(ny, r.iy, -r.uy), fmaxf(__fmaf_rd(nz, r.iz, -r.uz), r.tmin));
+    const float f = fmin3(__fmaf_ru(fx, r.ix, -r.lx), __fmaf_ru(fy, r.iy, -r.ly), __fmaf_ru(fz, r.iz, -r.lz));
+    const float tf = fminf(__fmul_rn(f, ROBUST_FAR), tcap);
+    return (tn <= tf && ref != 0xFFFFFFFFu) ? fminf(tn, 3.40282347e38f) : __int_as_float(0x7F800000);
+}
+
+// Orders two (distance, reference) pairs by distance.
+__device__ __forceinline__ void order2(float &ta, uint32_t &ra, float &tb, uint32_t &rb) {
+    const bool sw = tb < ta;
+    const float t = ta;
+    const uint32_t x = ra;
+    ta = sw ? tb : ta;
+    ra = sw ? rb : ra;
+    tb = sw ? t : tb;
+    rb = sw ? x : rb;
+}
+
 // Diagnostic counters of one ray (the COUNT variants only).
 struct Counters {
     uint32_t nodes = 0, tris = 0, warp_nodes = 0, warp_leaves = 0;
@@ -181,6 +231,12 @@ __device__ __forceinline__ void ray_init(RayState &s, const float4 o4, const flo
     s.r.ix = safe_inv(d4.x);
     s.r.iy = safe_inv(d4.y);
     s.r.iz = safe_inv(d4.z);
+    s.r.lx = __fmul_rd(o4.x, s.r.ix);
+    s.r.ly = __fmul_rd(o4.y, s.r.iy);
+    s.r.lz = __fmul_rd(o4.z, s.r.iz);
+    s.r.ux = __fmul_ru(o4.x, s.r.ix);
+    s.r.uy = __fmul_ru(o4.y, s.r.iy);
+    s.r.uz = __fmul_ru(o4.z, s.r.iz);
     s.best_t = s.r.tmax;
     s.best_u = s.best_v = 0.0f;
     s.best_prim = -1;
@@ -217,8 +273,54 @@ template <bool ANY, bool COUNT, int LAYOUT>
 __device__ __forceinline__ void ray_round(RayState &s, uint2 *stack, const uint4 *__restrict__ nodes,
                                           const float4 *__restrict__ tris, Counters &cn) {
     const uint32_t lane = threadIdx.x & 31;
+    // wide nodes: the met children sorted by entry distance (a five-exchange
+    // network on four pairs), the nearest descended, the others pushed
+    // farthest first
+    while (LAYOUT == 2 && s.node != REF_NONE && !(s.node & REF_LEAF)) {
+        const float4 *nd = reinterpret_cast<const float4 *>(nodes) + 8 * (size_t)s.node;
+        if (COUNT) {
+            ++cn.nodes;
+            if (lane == (uint32_t)(__ffs(__activemask()) - 1)) ++cn.warp_nodes;
+        }
+        // the near row of an axis is lo for a positive reciprocal direction
+        const uint32_t sx = s.r.ix < 0.0f, sy = s.r.iy < 0.0f, sz = s.r.iz < 0.0f;
+        const float4 nx = __ldg(nd + sx), fx = __ldg(nd + 1 - sx);
+        const float4 ny = __ldg(nd + 2 + sy), fy = __ldg(nd + 3 - sy);
+        const float4 nz = __ldg(nd + 4 + sz), fz = __ldg(nd + 5 - sz);
+        const uint4 rf = __ldg(reinterpret_cast<const uint4 *>(nd + 6));
+        uint32_t r0 = rf.x, r1 = rf.y, r2 = rf.z, r3 = rf.w;
+        float t0 = wide_child(s.r, nx.x, ny.x, nz.x, fx.x, fy.x, fz.x, r0, s.tcap);
+        float t1 = wide_child(s.r, nx.y, ny.y, nz.y, fx.y, fy.y, fz.y, r1, s.tcap);
+        float t2 = wide_child(s.r, nx.z, ny.z, nz.z, fx.z, fy.z, fz.z, r2, s.tcap);
+        float t3 = wide_child(s.r, nx.w, ny.w, nz.w, fx.w, fy.w, fz.w, r3, s.tcap);
+        order2(t0, r0, t1, r1);
+        order2(t2, r2, t3, r3);
+        order2(t0, r0, t2, r2);
+        order2(t1, r1, t3, r3);
+        order2(t1, r1, t2, r2);
+        const float INF = __int_as_float(0x7F800000);
+        const int met = (t0 < INF) + (t1 < INF) + (t2 < INF) + (t3 < INF);
+        if (met == 0) {
+            s.node = ray_pop(s, stack);
+        } else {
+            if (s.sp + met - 1 > STACK) {
+                s.overflow = true;
+                s.node = s.leaf = REF_NONE;
+                break;
+            }
+            if (met > 3) stack[s.sp++] = make_uint2(r3, __float_as_uint(t3));
+            if (met > 2) stack[s.sp++] = make_uint2(r2, __float_as_uint(t2));
+            if (met > 1) stack[s.sp++] = make_uint2(r1, __float_as_uint(t1));
+            s.node = r0;
+        }
+        if (s.node != REF_NONE && (s.node & REF_LEAF) && s.leaf == REF_NONE) {
+            s.leaf = s.node;
+            s.node = ray_pop(s, stack);
+        }
+        if (__all_sync(__activemask(), s.leaf != REF_NONE)) break;
+    }
     // internal nodes: descend until every lane has a leaf parked
-    while (s.node != REF_NONE && !(s.node & REF_LEAF)) {
+    while (LAYOUT != 2 && s.node != REF_NONE && !(s.node & REF_LEAF)) {
         ChildBoxes c;
         if (LAYOUT == 0)
             fetch_quant8(nodes, s.node, c);
@@ -229,8 +331,8 @@ __device__ __forceinline__ void ray_round(RayState &s, uint2 *stack, const uint4
             if (lane == (uint32_t)(__ffs(__activemask()) - 1)) ++cn.warp_nodes;
         }
         float tn0, tf0, tn1, tf1;
-        slab(s.r, c.lo0x, c.lo0y, c.lo0z, c.hi0x, c.hi0y, c.hi0z, s.tcap, tn0, tf0);
-        slab(s.r, c.lo1x, c.lo1y, c.lo1z, c.hi1x, c.hi1y, c.hi1z, s.tcap, tn1, tf1);
+        slab<ANY>(s.r, c.lo0x, c.lo0y, c.lo0z, c.hi0x, c.hi0y, c.hi0z, s.tcap, tn0, tf0);
+        slab<ANY>(s.r, c.lo1x, c.lo1y, c.lo1z, c.hi1x, c.hi1y, c.hi1z, s.tcap, tn1, tf1);
         const bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
         if (h0 && h1) {
             const bool first0 = tn0 <= tn1;
@@ -379,7 +481,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
 // traversal does not depend on which rays share its warp, except for which
 // of several hits an any-hit query returns first.
 template <bool ANY, bool COUNT, int LAYOUT, bool MULTI>
-__global__ void __launch_bounds__(TRACE_BLOCK, 10) k_trace_pool(TraceArgs a) {
+__global__ void __launch_bounds__(TRACE_BLOCK, LAYOUT == 2 ? POOL_BLOCKS_WIDE : POOL_BLOCKS) k_trace_pool(TraceArgs a) {
     constexpr uint32_t FULL = 0xFFFFFFFFu;
     const uint32_t lane = threadIdx.x & 31;
     uint32_t lt;
@@ -439,15 +541,20 @@ cudaError_t launch_trace(cudaStream_t s, const TraceArgs &a, int any_hit) {
     if (pool) {
         // persistent grid: every block resident at once (the residency is
         // queried once per device; all pool variants share the launch bounds)
-        static std::atomic<int> resident[64];
+        static std::atomic<int> resident[64][2];
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        int per_sm = (dev >= 0 && dev < 64) ? resident[dev].load() : 0;
+        const int wide = a.layout == 2 ? 1 : 0;
+        int per_sm = (dev >= 0 && dev < 64) ? resident[dev][wide].load() : 0;
         if (per_sm <= 0) {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_pool<false, false, 1, false>, TRACE_BLOCK,
-                                                          0);
-            if (dev >= 0 && dev < 64 && per_sm > 0) resident[dev].store(per_sm);
+            if (wide)
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_pool<false, false, 2, false>,
+                                                              TRACE_BLOCK, 0);
+            else
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_pool<false, false, 1, false>,
+                                                              TRACE_BLOCK, 0);
+            if (dev >= 0 && dev < 64 && per_sm > 0) resident[dev][wide].store(per_sm);
         }
         const unsigned cap = (unsigned)std::max(1, sms) * (unsigned)std::max(1, per_sm);
         blocks = std::min(blocks, cap);
@@ -459,13 +566,17 @@ cudaError_t launch_trace(cudaStream_t s, const TraceArgs &a, int any_hit) {
         if (multi) {                                                            \
             if (a.layout == 0)                                                  \
                 K<ANY, CNT, 0, true><<<blocks, TRACE_BLOCK, 0, s>>>(a);         \
-            else                                                                \
+            else if (a.layout == 1)                                             \
                 K<ANY, CNT, 1, true><<<blocks, TRACE_BLOCK, 0, s>>>(a);         \
+            else                                                                \
+                K<ANY, CNT, 2, true><<<blocks, TRACE_BLOCK, 0, s>>>(a);         \
         } else {                                                                \
             if (a.layout == 0)                                                  \
                 K<ANY, CNT, 0, false><<<blocks, TRACE_BLOCK, 0, s>>>(a);        \
-            else                                                                \
+            else if (a.layout == 1)                                             \
                 K<ANY, CNT, 1, false><<<blocks, TRACE_BLOCK, 0, s>>>(a);        \
+            else                                                                \
+                K<ANY, CNT, 2, false><<<blocks, TRACE_BLOCK, 0, s>>>(a);        \
         }                                                                       \
     } while (0)
 #define HCC_TRACE_LAUNCH(ANY, CNT)                 \

@@ -185,15 +185,15 @@ def hcc_sync(ctx):
 
 # ---------------------------------------------------------------------- BVH
 
-HCC_BVH_QUANTISED, HCC_BVH_EXACT = 0, 1
-LAYOUTS = {"quantised": HCC_BVH_QUANTISED, "exact": HCC_BVH_EXACT}
+HCC_BVH_QUANTISED, HCC_BVH_EXACT, HCC_BVH_WIDE = 0, 1, 2
+LAYOUTS = {"quantised": HCC_BVH_QUANTISED, "exact": HCC_BVH_EXACT, "wide": HCC_BVH_WIDE}
 
 
 def hcc_bvh_upload(ctx, bvh, layout=None):
     """bvh: an object with lo, hi, left, right, first, count, order, tris numpy arrays.
 
-    layout None calls hcc_bvh_upload (quantised nodes); "quantised" or "exact"
-    calls hcc_bvh_upload_layout.
+    layout None calls hcc_bvh_upload (quantised nodes); "quantised", "exact" or
+    "wide" calls hcc_bvh_upload_layout.
     """
     arrs = dict(lo=np.ascontiguousarray(bvh.lo, np.float32), hi=np.ascontiguousarray(bvh.hi, np.float32),
                 left=np.ascontiguousarray(bvh.left, np.int32), right=np.ascontiguousarray(bvh.right, np.int32),

@@ -30,7 +30,7 @@ def env():
     ctx = hcc.hcc_create(0)
     ws = _scenes()
     layouts = {}
-    for layout in ("exact", "quantised"):
+    for layout in ("exact", "quantised", "wide"):
         bvhs = [hcc.hcc_bvh_upload(ctx, w.bvh, layout=layout) for w in ws]
         cuts = [hcc.hcc_select_cut(ctx, b, 32, 0.125) for b in bvhs]
         layouts[layout] = (bvhs, cuts)
@@ -62,7 +62,7 @@ def _run(e, method, k, layout="exact", org=None, dir_=None):
     return hcc.hits_to_numpy(hits)
 
 
-@pytest.mark.parametrize("layout", ["exact", "quantised"])
+@pytest.mark.parametrize("layout", ["exact", "quantised", "wide"])
 @pytest.mark.parametrize("method,k", [("nosort", 32), ("hcc", 32), ("hcc", 62), ("twopoint", 30), ("origin_dir", 48),
                                       ("origin", 12)])
 def test_batch_matches_per_scene_oracle(env, method, k, layout):

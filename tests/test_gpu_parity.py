@@ -32,6 +32,7 @@ class Scene:
         self.w = w
         self.bvh = hcc.hcc_bvh_upload(ctx, w.bvh)
         self.bvh_exact = hcc.hcc_bvh_upload(ctx, w.bvh, layout="exact")
+        self.bvh_wide = hcc.hcc_bvh_upload(ctx, w.bvh, layout="wide")
         self.org = torch.from_numpy(w.rays.org).to(DEV)
         self.dir = torch.from_numpy(w.rays.dir).to(DEV)
         self.n = w.rays.n
@@ -92,7 +93,7 @@ def gpu_sort(ctx, keys_u64, k):
 
 def gpu_trace(ctx, sc, org, dir_, any_hit=False, scatter=None, layout="quantised"):
     hits = torch.zeros((org.shape[0], 4), dtype=torch.int32, device=DEV)
-    bvh = sc.bvh if layout == "quantised" else sc.bvh_exact
+    bvh = {"quantised": sc.bvh, "exact": sc.bvh_exact, "wide": sc.bvh_wide}[layout]
     hcc.hcc_trace(ctx, bvh, org, dir_, hits, any_hit=any_hit, scatter=scatter)
     hcc.hcc_sync(ctx)
     return hcc.hits_to_numpy(hits)
@@ -307,7 +308,7 @@ def test_gather_bit_exact(ctx, n):
 
 # ------------------------------------------------------------------- trace
 
-@pytest.mark.parametrize("layout", ["quantised", "exact"])
+@pytest.mark.parametrize("layout", ["quantised", "exact", "wide"])
 @pytest.mark.parametrize("which", ["tiny", "dense", "room"])
 def test_trace_closest_matches_oracle(ctx, which, layout, request):
     sc = request.getfixturevalue(which)
@@ -317,14 +318,14 @@ def test_trace_closest_matches_oracle(ctx, which, layout, request):
     assert (g["prim"] >= 0).mean() > 0.2
 
 
-@pytest.mark.parametrize("layout", ["quantised", "exact"])
+@pytest.mark.parametrize("layout", ["quantised", "exact", "wide"])
 def test_trace_matches_brute_force_definition(ctx, dense, layout):
     g = gpu_trace(ctx, dense, dense.org, dense.dir, layout=layout)
     o = oracle.trace_brute(dense.w.tris, dense.w.rays.org, dense.w.rays.dir)
     compare_hits(g, o)
 
 
-@pytest.mark.parametrize("layout", ["quantised", "exact"])
+@pytest.mark.parametrize("layout", ["quantised", "exact", "wide"])
 def test_trace_any_hit_shadow_rays(ctx, room, layout):
     sh = room.w.shadow
     org, dir_ = torch.from_numpy(sh.org).to(DEV), torch.from_numpy(sh.dir).to(DEV)
@@ -339,7 +340,7 @@ def test_trace_any_hit_shadow_rays(ctx, room, layout):
         assert ok and np.float32(t) == g["t"][i]
 
 
-@pytest.mark.parametrize("layout", ["quantised", "exact"])
+@pytest.mark.parametrize("layout", ["quantised", "exact", "wide"])
 def test_trace_special_rays(ctx, dense, layout):
     rng = np.random.default_rng(1)
     n = 400
@@ -475,7 +476,7 @@ def _chain_bvh(depth):
     return gen.BVH(lo, hi, left, right, first, count, np.arange(depth + 1, dtype=np.uint32), tris, depth)
 
 
-@pytest.mark.parametrize("layout", ["quantised", "exact"])
+@pytest.mark.parametrize("layout", ["quantised", "exact", "wide"])
 def test_stack_overflow_is_reported_and_context_survives(ctx, tiny, layout):
     deep = _chain_bvh(100)
     h = hcc.hcc_bvh_upload(ctx, deep, layout=layout)
@@ -510,7 +511,7 @@ def test_trace_schedules_give_the_same_records(ctx, which, request):
     try:
         for schedule in ("per_ray", "refill", "auto"):
             hcc.hcc_set_trace_schedule(ctx, schedule)
-            for bvh in (sc.bvh, sc.bvh_exact):
+            for bvh in (sc.bvh, sc.bvh_exact, sc.bvh_wide):
                 hits = torch.zeros((sc.n, 4), dtype=torch.int32, device=DEV)
                 hcc.hcc_trace(ctx, bvh, sc.org, sc.dir, hits)
                 hcc.hcc_sync(ctx)

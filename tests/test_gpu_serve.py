@@ -26,7 +26,7 @@ def scenes():
           gen.tiny_workload(7, ntris=8000, nrays=6000)]
     ctx = hcc.hcc_create(0)
     up = {}
-    for layout in ("exact", "quantised"):
+    for layout in ("exact", "quantised", "wide"):
         bvhs = [hcc.hcc_bvh_upload(ctx, w.bvh, layout=layout) for w in ws]
         cuts = [hcc.hcc_select_cut(ctx, b, 32, 0.125) for b in bvhs]
         up[layout] = (bvhs, cuts)
@@ -114,7 +114,7 @@ def _oracle(ws, reqs):
 
 @pytest.mark.parametrize("method,k,layout", [("hcc", 32, "exact"), ("hcc", 48, "quantised"),
                                              ("twopoint", 30, "exact"), ("nosort", 32, "quantised"),
-                                             ("origin_dir", 24, "exact")])
+                                             ("origin_dir", 24, "exact"), ("hcc", 32, "wide")])
 def test_each_result_is_the_same_alone_and_in_the_mix(scenes, method, k, layout):
     ws, up = scenes
     bvhs, cuts = up[layout]
