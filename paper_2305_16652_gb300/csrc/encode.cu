@@ -44,9 +44,11 @@ __device__ __forceinline__ bool meets(const float4 &o, const float4 &d, float ix
 // whose boxes all have lo <= hi, the per-axis min / max of the slab test is
 // known from the sign of the reciprocal: with inv > 0, (lo - o) * inv <=
 // (hi - o) * inv (rounding is monotonic), and the order flips for inv < 0.
-// Those rays read each bound they need by a per-lane index instead of
-// computing both and taking min and max -- the same comparisons with six
-// fewer min/max operations per node.  Other rays (a zero or denormal
+// Those rays read the (near, far) bounds of each axis as one pair by a
+// per-lane index and take both distances with one packed add and one packed
+// multiply instead of computing both and taking min and max -- the same
+// comparisons with six fewer min/max operations per node and half the
+// arithmetic instructions.  Other rays (a zero or denormal
 // direction component, where 0 * inf makes a NaN that fminf / fmaxf skip) take
 // the general test.
 template <typename K>
@@ -55,19 +57,21 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_hcc(const float4 *__restri
                                                           const float4 *__restrict__ cut, uint32_t used,
                                                           uint32_t key_bits, K *__restrict__ keys) {
     __shared__ float4 s_lo[MAX_CUT_BITS], s_hi[MAX_CUT_BITS];
-    __shared__ float s_b[MAX_CUT_BITS * 6];  // per node: lo.x hi.x lo.y hi.y lo.z hi.z
+    // per node and axis the two orders of its bounds, (lo, hi) and (hi, lo):
+    // a ray reads (near, far) of an axis as one pair, by its direction sign
+    __shared__ float2 s_p[MAX_CUT_BITS * 6];
     bool ordered = true;
     for (uint32_t r = threadIdx.x; r < used; r += blockDim.x) {
         const float4 lo = cut[2 * r], hi = cut[2 * r + 1];
         s_lo[r] = lo;
         s_hi[r] = hi;
-        float *b = s_b + 6 * r;
-        b[0] = lo.x;
-        b[1] = hi.x;
-        b[2] = lo.y;
-        b[3] = hi.y;
-        b[4] = lo.z;
-        b[5] = hi.z;
+        float2 *b = s_p + 6 * r;
+        b[0] = make_float2(lo.x, hi.x);
+        b[1] = make_float2(hi.x, lo.x);
+        b[2] = make_float2(lo.y, hi.y);
+        b[3] = make_float2(hi.y, lo.y);
+        b[4] = make_float2(lo.z, hi.z);
+        b[5] = make_float2(hi.z, lo.z);
         ordered = ordered && lo.x <= hi.x && lo.y <= hi.y && lo.z <= hi.z;
     }
     ordered = __syncthreads_and(ordered);
@@ -77,26 +81,26 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_hcc(const float4 *__restri
         const float4 d = __ldcs(dir + i);
         const float ix = __frcp_rn(d.x), iy = __frcp_rn(d.y), iz = __frcp_rn(d.z);
         K key = 0;
-        K bit = (K)1 << (key_bits - 1);
         if (ordered && isfinite(ix) && isfinite(iy) && isfinite(iz)) {
-            const uint32_t nx = ix < 0.0f, ny = 2u + (iy < 0.0f), nz = 4u + (iz < 0.0f);  // near-bound slots
-            const uint32_t fx = 1u - nx, fy = 5u - ny, fz = 9u - nz;                      // far-bound slots
-            for (uint32_t r = 0; r < used; ++r, bit >>= 1) {
-                const float *b = s_b + 6 * r;
-                const float tnx = __fmul_rn(__fsub_rn(b[nx], o.x), ix);
-                const float tny = __fmul_rn(__fsub_rn(b[ny], o.y), iy);
-                const float tnz = __fmul_rn(__fsub_rn(b[nz], o.z), iz);
-                const float tfx = __fmul_rn(__fsub_rn(b[fx], o.x), ix);
-                const float tfy = __fmul_rn(__fsub_rn(b[fy], o.y), iy);
-                const float tfz = __fmul_rn(__fsub_rn(b[fz], o.z), iz);
-                const float tnear = fmax3(tnx, tny, fmaxf(tnz, o.w));
-                const float tfar = fmin3(tfx, tfy, fminf(tfz, d.w));
-                if (tnear <= tfar) key |= bit;
+            // (bound + (-o)) * inv for the near and far bound of an axis in one
+            // packed add and one packed multiply: the same round-to-nearest
+            // results as (bound - o) * inv one at a time
+            const float2 *px = s_p + (ix < 0.0f), *py = s_p + 2 + (iy < 0.0f), *pz = s_p + 4 + (iz < 0.0f);
+            const float2 nox = make_float2(-o.x, -o.x), noy = make_float2(-o.y, -o.y), noz = make_float2(-o.z, -o.z);
+            const float2 ixx = make_float2(ix, ix), iyy = make_float2(iy, iy), izz = make_float2(iz, iz);
+#pragma unroll 4
+            for (uint32_t r = 0; r < used; ++r) {
+                const float2 tx = __fmul2_rn(__fadd2_rn(px[6 * r], nox), ixx);
+                const float2 ty = __fmul2_rn(__fadd2_rn(py[6 * r], noy), iyy);
+                const float2 tz = __fmul2_rn(__fadd2_rn(pz[6 * r], noz), izz);
+                const float tnear = fmax3(tx.x, ty.x, fmaxf(tz.x, o.w));
+                const float tfar = fmin3(tx.y, ty.y, fminf(tz.y, d.w));
+                key = (key << 1) | (K)(tnear <= tfar);
             }
         } else {
-            for (uint32_t r = 0; r < used; ++r, bit >>= 1)
-                if (meets(o, d, ix, iy, iz, s_lo[r], s_hi[r])) key |= bit;
+            for (uint32_t r = 0; r < used; ++r) key = (key << 1) | (K)meets(o, d, ix, iy, iz, s_lo[r], s_hi[r]);
         }
+        if (used && key_bits > used) key <<= (key_bits - used);  // node r drives bit key_bits - 1 - r
         __stcs(keys + i, key);
     }
 }
@@ -495,14 +499,14 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_ppc(const float4 *__restri
             const uint4 n3 = __ldg(reinterpret_cast<const uint4 *>(f + 3));
             float4 lo, hi;
             uint32_t child;
-            if (!right) {
-                lo = make_float4(n0.x, n0.y, n0.z, 0.f);
-                hi = make_float4(n0.w, n1.x, n1.y, 0.f);
+            if (!right) {  // exact node: per child (lo.x, lo.y), (hi.x, hi.y), (lo.z, hi.z)
+                lo = make_float4(n0.x, n0.y, n1.x, 0.f);
+                hi = make_float4(n0.z, n0.w, n1.y, 0.f);
                 child = n3.x;
                 stack[sp++] = cur;  // its right child follows the left subtree
             } else {
-                lo = make_float4(n1.z, n1.w, n2.x, 0.f);
-                hi = make_float4(n2.y, n2.z, n2.w, 0.f);
+                lo = make_float4(n1.z, n1.w, n2.z, 0.f);
+                hi = make_float4(n2.x, n2.y, n2.w, 0.f);
                 child = n3.y;
             }
             const bool met = meets(o, d, ix, iy, iz, lo, hi);

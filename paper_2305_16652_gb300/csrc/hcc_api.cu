@@ -603,9 +603,11 @@ hcc_status hcc_bvh_upload_layout(hcc_ctx *ctx, const hcc_bvh_desc *d, hcc_bvh_la
         if (layout == HCC_BVH_QUANTISED) {
             quantise_node(&blo[3 * l], &bhi[3 * l], &blo[3 * r], &bhi[3 * r], ref_of(l), ref_of(r), w);
         } else {
-            const float f[12] = {blo[3 * l], blo[3 * l + 1], blo[3 * l + 2], bhi[3 * l],
-                                 bhi[3 * l + 1], bhi[3 * l + 2], blo[3 * r], blo[3 * r + 1],
-                                 blo[3 * r + 2], bhi[3 * r], bhi[3 * r + 1], bhi[3 * r + 2]};
+            // per child (lo.x, lo.y), (hi.x, hi.y), (lo.z, hi.z): the pairs the
+            // traversal's packed slab arithmetic takes
+            const float f[12] = {blo[3 * l], blo[3 * l + 1], bhi[3 * l], bhi[3 * l + 1],
+                                 blo[3 * l + 2], bhi[3 * l + 2], blo[3 * r], blo[3 * r + 1],
+                                 bhi[3 * r], bhi[3 * r + 1], blo[3 * r + 2], bhi[3 * r + 2]};
             std::memcpy(w, f, sizeof f);
             w[12] = ref_of(l);
             w[13] = ref_of(r);

@@ -31,8 +31,8 @@ constexpr uint32_t REF_LEAF = 0x80000000u;
 constexpr uint32_t REF_TRI_MASK = 0x1FFFFFFFu;
 
 // Exact layout: one internal node = 64 bytes = four uint4: the children's
-// FP32 boxes c0.lo.xyz c0.hi.x | c0.hi.yz c1.lo.xy | c1.lo.z c1.hi.xyz |
-// ref0 ref1 0 0.
+// FP32 boxes as pairs c0.lo.xy c0.hi.xy | c0.lo.z c0.hi.z c1.lo.xy |
+// c1.hi.xy c1.lo.z c1.hi.z | ref0 ref1 0 0.
 // Wide layout: one 4-ary node = 128 bytes = eight float4 rows, one entry per
 // child: lo.x, hi.x, lo.y, hi.y, lo.z, hi.z, references, zeros; an unused
 // child has ref 0xFFFFFFFF.  An internal reference indexes wide nodes.

@@ -45,8 +45,12 @@ __device__ __forceinline__ float byte_to_float(uint32_t w, uint32_t sel) {
 // selectors for byte 0..3 of w combined with bytes of 0x4B000000
 constexpr uint32_t SEL0 = 0x7540u, SEL1 = 0x7541u, SEL2 = 0x7542u, SEL3 = 0x7543u;
 
+// The origin is kept negated and paired, (-ox, -oy) and (-oz, -oz), with the
+// reciprocal direction paired alike, so one packed add and one packed
+// multiply give two slab distances (lo - o) * inv.
 struct Ray {
-    float ox, oy, oz, tmin, dx, dy, dz, tmax, ix, iy, iz;
+    float2 nxy, nzz, ixy, izz;
+    float tmin, dx, dy, dz, tmax;
     float lx, ly, lz, ux, uy, uz;  // o * (1/d) rounded down and up, per axis
 };
 
@@ -66,22 +70,29 @@ __device__ __forceinline__ float safe_inv(float d) {
 // rounded up, the far plane's from above by one fma rounded up against
 // o * inv rounded down, so the only error left is the relative one of the
 // rounded reciprocal.  Both widen the far distance by 1 + 2*gamma(3).
+// A child box as pairs: (lo.x, lo.y), (hi.x, hi.y), (lo.z, hi.z).
+struct Box2 {
+    float2 lxy, hxy, zz;
+};
+
 template <bool DIRECTED>
-__device__ __forceinline__ void slab(const Ray &r, float lox, float loy, float loz, float hix, float hiy, float hiz,
-                                     float tcap, float &tn, float &tf) {
+__device__ __forceinline__ void slab(const Ray &r, const Box2 &b, float tcap, float &tn, float &tf) {
     if (DIRECTED) {
-        const bool sx = r.ix < 0.0f, sy = r.iy < 0.0f, sz = r.iz < 0.0f;
-        const float ax = __fmaf_rd(sx ? hix : lox, r.ix, -r.ux), bx = __fmaf_ru(sx ? lox : hix, r.ix, -r.lx);
-        const float ay = __fmaf_rd(sy ? hiy : loy, r.iy, -r.uy), by = __fmaf_ru(sy ? loy : hiy, r.iy, -r.ly);
-        const float az = __fmaf_rd(sz ? hiz : loz, r.iz, -r.uz), bz = __fmaf_ru(sz ? loz : hiz, r.iz, -r.lz);
+        const float ix = r.ixy.x, iy = r.ixy.y, iz = r.izz.x;
+        const bool sx = ix < 0.0f, sy = iy < 0.0f, sz = iz < 0.0f;
+        const float ax = __fmaf_rd(sx ? b.hxy.x : b.lxy.x, ix, -r.ux), bx = __fmaf_ru(sx ? b.lxy.x : b.hxy.x, ix, -r.lx);
+        const float ay = __fmaf_rd(sy ? b.hxy.y : b.lxy.y, iy, -r.uy), by = __fmaf_ru(sy ? b.lxy.y : b.hxy.y, iy, -r.ly);
+        const float az = __fmaf_rd(sz ? b.zz.y : b.zz.x, iz, -r.uz), bz = __fmaf_ru(sz ? b.zz.x : b.zz.y, iz, -r.lz);
         tn = fmax3(ax, ay, fmaxf(az, r.tmin));
         tf = fminf(__fmul_rn(fmin3(bx, by, bz), ROBUST_FAR), tcap);
     } else {
-        const float ax = __fmul_rn(__fsub_rn(lox, r.ox), r.ix), bx = __fmul_rn(__fsub_rn(hix, r.ox), r.ix);
-        const float ay = __fmul_rn(__fsub_rn(loy, r.oy), r.iy), by = __fmul_rn(__fsub_rn(hiy, r.oy), r.iy);
-        const float az = __fmul_rn(__fsub_rn(loz, r.oz), r.iz), bz = __fmul_rn(__fsub_rn(hiz, r.oz), r.iz);
-        tn = fmax3(fminf(ax, bx), fminf(ay, by), fmaxf(fminf(az, bz), r.tmin));
-        const float f = fmin3(fmaxf(ax, bx), fmaxf(ay, by), fmaxf(az, bz));
+        // (bound + (-o)) * inv, two axes per packed operation: the same
+        // round-to-nearest results as (bound - o) * inv one at a time
+        const float2 a = __fmul2_rn(__fadd2_rn(b.lxy, r.nxy), r.ixy);
+        const float2 c = __fmul2_rn(__fadd2_rn(b.hxy, r.nxy), r.ixy);
+        const float2 z = __fmul2_rn(__fadd2_rn(b.zz, r.nzz), r.izz);
+        tn = fmax3(fminf(a.x, c.x), fminf(a.y, c.y), fmaxf(fminf(z.x, z.y), r.tmin));
+        const float f = fmin3(fmaxf(a.x, c.x), fmaxf(a.y, c.y), fmaxf(z.x, z.y));
         tf = fminf(__fmul_rn(f, ROBUST_FAR), tcap);
     }
 }
@@ -99,7 +110,7 @@ __device__ __forceinline__ bool intersect(const Ray &r, const float4 &A, const f
     const float det = __fmaf_rn(E1.z, pz, __fmaf_rn(E1.y, py, __fmul_rn(E1.x, px)));
     if (det == 0.0f) return false;
     const float inv = __frcp_rn(det);
-    const float sx = __fsub_rn(r.ox, A.x), sy = __fsub_rn(r.oy, A.y), sz = __fsub_rn(r.oz, A.z);
+    const float sx = __fsub_rn(-r.nxy.x, A.x), sy = __fsub_rn(-r.nxy.y, A.y), sz = __fsub_rn(-r.nzz.x, A.z);
     u = __fmul_rn(__fmaf_rn(sz, pz, __fmaf_rn(sy, py, __fmul_rn(sx, px))), inv);
     if (u < 0.0f || u > 1.0f) return false;
     const float qx = __fmaf_rn(sy, E1.z, -__fmul_rn(sz, E1.y));
@@ -115,7 +126,7 @@ constexpr uint32_t REF_NONE = 0xFFFFFFFFu;  // no node (empty stack, no postpone
 
 // Both children's boxes of an internal node, decoded for the slab test.
 struct ChildBoxes {
-    float lo0x, lo0y, lo0z, hi0x, hi0y, hi0z, lo1x, lo1y, lo1z, hi1x, hi1y, hi1z;
+    Box2 b0, b1;
     uint32_t ref0, ref1;
 };
 
@@ -125,6 +136,8 @@ __device__ __forceinline__ void ldg256(const void *p, uint4 &a, uint4 &b) {
         : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
         : "l"(p));
 }
+
+__device__ __forceinline__ float2 f2(uint32_t a, uint32_t b) { return make_float2(__uint_as_float(a), __uint_as_float(b)); }
 
 // 32-byte quantised node: bounds are origin + q * 2^E rounded outward.
 __device__ __forceinline__ void fetch_quant8(const uint4 *nodes, uint32_t ref, ChildBoxes &c) {
@@ -136,45 +149,30 @@ __device__ __forceinline__ void fetch_quant8(const uint4 *nodes, uint32_t ref, C
     const float sx = __uint_as_float((A.x & 0xFFu) << 23);
     const float sy = __uint_as_float((A.y & 0xFFu) << 23);
     const float sz = __uint_as_float((A.z & 0xFFu) << 23);
-    c.lo0x = __fmaf_rd(byte_to_float(A.w, SEL0), sx, ox);
-    c.lo0y = __fmaf_rd(byte_to_float(A.w, SEL1), sy, oy);
-    c.lo0z = __fmaf_rd(byte_to_float(A.w, SEL2), sz, oz);
-    c.hi0x = __fmaf_ru(byte_to_float(A.w, SEL3), sx, ox);
-    c.hi0y = __fmaf_ru(byte_to_float(B.x, SEL0), sy, oy);
-    c.hi0z = __fmaf_ru(byte_to_float(B.x, SEL1), sz, oz);
-    c.lo1x = __fmaf_rd(byte_to_float(B.x, SEL2), sx, ox);
-    c.lo1y = __fmaf_rd(byte_to_float(B.x, SEL3), sy, oy);
-    c.lo1z = __fmaf_rd(byte_to_float(B.y, SEL0), sz, oz);
-    c.hi1x = __fmaf_ru(byte_to_float(B.y, SEL1), sx, ox);
-    c.hi1y = __fmaf_ru(byte_to_float(B.y, SEL2), sy, oy);
-    c.hi1z = __fmaf_ru(byte_to_float(B.y, SEL3), sz, oz);
+    c.b0.lxy = make_float2(__fmaf_rd(byte_to_float(A.w, SEL0), sx, ox), __fmaf_rd(byte_to_float(A.w, SEL1), sy, oy));
+    c.b0.zz.x = __fmaf_rd(byte_to_float(A.w, SEL2), sz, oz);
+    c.b0.hxy = make_float2(__fmaf_ru(byte_to_float(A.w, SEL3), sx, ox), __fmaf_ru(byte_to_float(B.x, SEL0), sy, oy));
+    c.b0.zz.y = __fmaf_ru(byte_to_float(B.x, SEL1), sz, oz);
+    c.b1.lxy = make_float2(__fmaf_rd(byte_to_float(B.x, SEL2), sx, ox), __fmaf_rd(byte_to_float(B.x, SEL3), sy, oy));
+    c.b1.zz.x = __fmaf_rd(byte_to_float(B.y, SEL0), sz, oz);
+    c.b1.hxy = make_float2(__fmaf_ru(byte_to_float(B.y, SEL1), sx, ox), __fmaf_ru(byte_to_float(B.y, SEL2), sy, oy));
+    c.b1.zz.y = __fmaf_ru(byte_to_float(B.y, SEL3), sz, oz);
     c.ref0 = B.z;
     c.ref1 = B.w;
 }
 
-// 64-byte exact node: the children's FP32 boxes as stored in the input BVH.
+// 64-byte exact node: per child (lo.x, lo.y), (hi.x, hi.y), (lo.z, hi.z) as
+// stored in the input BVH, then the two references.
 __device__ __forceinline__ void fetch_exact(const uint4 *nodes, uint32_t ref, ChildBoxes &c) {
     uint4 w0, w1, w2, n3;
     ldg256(nodes + 4 * (size_t)ref, w0, w1);
     ldg256(nodes + 4 * (size_t)ref + 2, w2, n3);
-    const float4 n0 = make_float4(__uint_as_float(w0.x), __uint_as_float(w0.y), __uint_as_float(w0.z),
-                                  __uint_as_float(w0.w));
-    const float4 n1 = make_float4(__uint_as_float(w1.x), __uint_as_float(w1.y), __uint_as_float(w1.z),
-                                  __uint_as_float(w1.w));
-    const float4 n2 = make_float4(__uint_as_float(w2.x), __uint_as_float(w2.y), __uint_as_float(w2.z),
-                                  __uint_as_float(w2.w));
-    c.lo0x = n0.x;
-    c.lo0y = n0.y;
-    c.lo0z = n0.z;
-    c.hi0x = n0.w;
-    c.hi0y = n1.x;
-    c.hi0z = n1.y;
-    c.lo1x = n1.z;
-    c.lo1y = n1.w;
-    c.lo1z = n2.x;
-    c.hi1x = n2.y;
-    c.hi1y = n2.z;
-    c.hi1z = n2.w;
+    c.b0.lxy = f2(w0.x, w0.y);
+    c.b0.hxy = f2(w0.z, w0.w);
+    c.b0.zz = f2(w1.x, w1.y);
+    c.b1.lxy = f2(w1.z, w1.w);
+    c.b1.hxy = f2(w2.x, w2.y);
+    c.b1.zz = f2(w2.z, w2.w);
     c.ref0 = n3.x;
     c.ref1 = n3.y;
 }
@@ -186,8 +184,9 @@ __device__ __forceinline__ void fetch_exact(const uint4 *nodes, uint32_t ref, Ch
 // marks only unused and missed slots), else +inf.
 __device__ __forceinline__ float wide_child(const Ray &r, float nx, float ny, float nz, float fx, float fy, float fz,
                                             uint32_t ref, float tcap) {
-    const float tn = fmax3(__fmaf_rd(nx, r.ix, -r.ux), __fmaf_rd(ny, r.iy, -r.uy), fmaxf(__fmaf_rd(nz, r.iz, -r.uz), r.tmin));
-    const float f = fmin3(__fmaf_ru(fx, r.ix, -r.lx), __fmaf_ru(fy, r.iy, -r.ly), __fmaf_ru(fz, r.iz, -r.lz));
+    const float ix = r.ixy.x, iy = r.ixy.y, iz = r.izz.x;
+    const float tn = fmax3(__fmaf_rd(nx, ix, -r.ux), __fmaf_rd(ny, iy, -r.uy), fmaxf(__fmaf_rd(nz, iz, -r.uz), r.tmin));
+    const float f = fmin3(__fmaf_ru(fx, ix, -r.lx), __fmaf_ru(fy, iy, -r.ly), __fmaf_ru(fz, iz, -r.lz));
     const float tf = fminf(__fmul_rn(f, ROBUST_FAR), tcap);
     return (tn <= tf && ref != 0xFFFFFFFFu) ? fminf(tn, 3.40282347e38f) : __int_as_float(0x7F800000);
 }
@@ -220,23 +219,22 @@ struct RayState {
 };
 
 __device__ __forceinline__ void ray_init(RayState &s, const float4 o4, const float4 d4, uint32_t root_ref) {
-    s.r.ox = o4.x;
-    s.r.oy = o4.y;
-    s.r.oz = o4.z;
+    s.r.nxy = make_float2(-o4.x, -o4.y);
+    s.r.nzz = make_float2(-o4.z, -o4.z);
     s.r.tmin = o4.w;
     s.r.dx = d4.x;
     s.r.dy = d4.y;
     s.r.dz = d4.z;
     s.r.tmax = d4.w;
-    s.r.ix = safe_inv(d4.x);
-    s.r.iy = safe_inv(d4.y);
-    s.r.iz = safe_inv(d4.z);
-    s.r.lx = __fmul_rd(o4.x, s.r.ix);
-    s.r.ly = __fmul_rd(o4.y, s.r.iy);
-    s.r.lz = __fmul_rd(o4.z, s.r.iz);
-    s.r.ux = __fmul_ru(o4.x, s.r.ix);
-    s.r.uy = __fmul_ru(o4.y, s.r.iy);
-    s.r.uz = __fmul_ru(o4.z, s.r.iz);
+    const float ix = safe_inv(d4.x), iy = safe_inv(d4.y), iz = safe_inv(d4.z);
+    s.r.ixy = make_float2(ix, iy);
+    s.r.izz = make_float2(iz, iz);
+    s.r.lx = __fmul_rd(o4.x, ix);
+    s.r.ly = __fmul_rd(o4.y, iy);
+    s.r.lz = __fmul_rd(o4.z, iz);
+    s.r.ux = __fmul_ru(o4.x, ix);
+    s.r.uy = __fmul_ru(o4.y, iy);
+    s.r.uz = __fmul_ru(o4.z, iz);
     s.best_t = s.r.tmax;
     s.best_u = s.best_v = 0.0f;
     s.best_prim = -1;
@@ -283,7 +281,7 @@ __device__ __forceinline__ void ray_round(RayState &s, uint2 *stack, const uint4
             if (lane == (uint32_t)(__ffs(__activemask()) - 1)) ++cn.warp_nodes;
         }
         // the near row of an axis is lo for a positive reciprocal direction
-        const uint32_t sx = s.r.ix < 0.0f, sy = s.r.iy < 0.0f, sz = s.r.iz < 0.0f;
+        const uint32_t sx = s.r.ixy.x < 0.0f, sy = s.r.ixy.y < 0.0f, sz = s.r.izz.x < 0.0f;
         const float4 nx = __ldg(nd + sx), fx = __ldg(nd + 1 - sx);
         const float4 ny = __ldg(nd + 2 + sy), fy = __ldg(nd + 3 - sy);
         const float4 nz = __ldg(nd + 4 + sz), fz = __ldg(nd + 5 - sz);
@@ -331,8 +329,8 @@ __device__ __forceinline__ void ray_round(RayState &s, uint2 *stack, const uint4
             if (lane == (uint32_t)(__ffs(__activemask()) - 1)) ++cn.warp_nodes;
         }
         float tn0, tf0, tn1, tf1;
-        slab<ANY>(s.r, c.lo0x, c.lo0y, c.lo0z, c.hi0x, c.hi0y, c.hi0z, s.tcap, tn0, tf0);
-        slab<ANY>(s.r, c.lo1x, c.lo1y, c.lo1z, c.hi1x, c.hi1y, c.hi1z, s.tcap, tn1, tf1);
+        slab<ANY>(s.r, c.b0, s.tcap, tn0, tf0);
+        slab<ANY>(s.r, c.b1, s.tcap, tn1, tf1);
         const bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
         if (h0 && h1) {
             const bool first0 = tn0 <= tn1;
