@@ -134,10 +134,11 @@ hcc_status hcc_reserve(hcc_ctx *ctx, uint64_t max_n, uint32_t max_key_bits);
  * How the context's traces schedule rays on warps.  PER_RAY: one thread per
  * ray slot for the whole traversal (the plain tracer).  REFILL: persistent
  * warps take ray slots from a counter in increasing order, and after each
- * traversal round the lanes whose ray has finished take new slots once 16
+ * traversal round the lanes whose ray has finished take new slots once 12
  * lanes of the warp are idle (24 when the rays are fetched through a sorted
- * permutation) (Aila & Laine 2009, "replacing terminated rays").  AUTO (the default): REFILL for closest-hit traces, PER_RAY for
- * any-hit traces (measured faster for each on GB300).  Results do not depend
+ * permutation) (Aila & Laine 2009, "replacing terminated rays").  AUTO (the
+ * default): REFILL for closest-hit traces, PER_RAY for any-hit traces
+ * (measured faster for each on GB300).  Results do not depend
  * on the schedule, except which hit an any-hit query reports.
  */
 typedef enum hcc_trace_schedule {

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_hcc(const float4 *__restri
             const float2 *px = s_p + (ix < 0.0f), *py = s_p + 2 + (iy < 0.0f), *pz = s_p + 4 + (iz < 0.0f);
             const float2 nox = make_float2(-o.x, -o.x), noy = make_float2(-o.y, -o.y), noz = make_float2(-o.z, -o.z);
             const float2 ixx = make_float2(ix, ix), iyy = make_float2(iy, iy), izz = make_float2(iz, iz);
-#pragma unroll 4
+#pragma unroll 8
             for (uint32_t r = 0; r < used; ++r) {
                 const float2 tx = __fmul2_rn(__fadd2_rn(px[6 * r], nox), ixx);
                 const float2 ty = __fmul2_rn(__fadd2_rn(py[6 * r], noy), iyy);

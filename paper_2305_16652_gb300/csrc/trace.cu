@@ -6,10 +6,10 @@
 // collapsed from it), a per-thread stack of (node, entry distance) pairs.
 //
 // Robustness: decoded child boxes are rounded outward (they contain the exact
-// boxes), the slab distances are directed-rounding bounds of the distances
-// under the rounded reciprocal direction, the far distance is widened by
-// 1 + 2*gamma(3) for the reciprocal's own rounding (after Ize 2013, "Robust
-// BVH Ray Traversal"), and a subtree is dropped only when its entry
+// boxes), the far slab distance is widened by 1 + 2*gamma(3) to cover the
+// rounding of the distances (Ize 2013, "Robust BVH Ray Traversal"; the wide
+// nodes' directed-rounding distances leave only the reciprocal's rounding
+// to cover), and a subtree is dropped only when its entry
 // distance exceeds the best hit by more than 2^-16 relative, so traversal
 // never loses a triangle that the closest-hit definition would pick.
 // Triangle arithmetic is the canonical Moller-Trumbore sequence with explicit
@@ -31,7 +31,7 @@ constexpr float PRUNE_SLACK = 1.0f + 1.0f / 65536.0f;
 // idle lanes that make a warp take new rays: in input order, and in sorted
 // order (rays fetched through a permutation), where waiting longer keeps the
 // warp's neighbouring rays together (measured faster for each)
-constexpr uint32_t REFILL_MIN = 16;
+constexpr uint32_t REFILL_MIN = 12;
 // resident blocks per SM the persistent kernel is built for: binary nodes
 // (48 registers) and wide nodes (56)
 constexpr int POOL_BLOCKS = 10;
@@ -60,41 +60,24 @@ __device__ __forceinline__ float safe_inv(float d) {
     return __frcp_rn(fabsf(d) > 1e-30f ? d : copysignf(1e-30f, d));
 }
 
-// Entry / exit distance of the ray through one decoded child box, in one
-// of two forms that never miss a box the exact slab test meets.
-// Rounded form: t = (bound - o) * inv with round-to-nearest, near and far by
-// min/max per axis; its three roundings make it a relative-error estimate.
-// Directed form (boxes stored with lo <= hi): per axis the near plane is lo
-// for a positive reciprocal direction and hi for a negative one; its
-// distance is bounded from below by one fma rounded down against o * inv
-// rounded up, the far plane's from above by one fma rounded up against
-// o * inv rounded down, so the only error left is the relative one of the
-// rounded reciprocal.  Both widen the far distance by 1 + 2*gamma(3).
 // A child box as pairs: (lo.x, lo.y), (hi.x, hi.y), (lo.z, hi.z).
 struct Box2 {
     float2 lxy, hxy, zz;
 };
 
-template <bool DIRECTED>
+// Entry / exit distance of the ray through one decoded child box of a
+// binary node: t = (bound - o) * inv with round-to-nearest, two axes per
+// packed add and multiply ((bound + (-o)) * inv, the same results as one at
+// a time), near and far by min/max per axis.  Its three roundings make it a
+// relative-error estimate, which the far distance widened by 1 + 2*gamma(3)
+// covers.
 __device__ __forceinline__ void slab(const Ray &r, const Box2 &b, float tcap, float &tn, float &tf) {
-    if (DIRECTED) {
-        const float ix = r.ixy.x, iy = r.ixy.y, iz = r.izz.x;
-        const bool sx = ix < 0.0f, sy = iy < 0.0f, sz = iz < 0.0f;
-        const float ax = __fmaf_rd(sx ? b.hxy.x : b.lxy.x, ix, -r.ux), bx = __fmaf_ru(sx ? b.lxy.x : b.hxy.x, ix, -r.lx);
-        const float ay = __fmaf_rd(sy ? b.hxy.y : b.lxy.y, iy, -r.uy), by = __fmaf_ru(sy ? b.lxy.y : b.hxy.y, iy, -r.ly);
-        const float az = __fmaf_rd(sz ? b.zz.y : b.zz.x, iz, -r.uz), bz = __fmaf_ru(sz ? b.zz.x : b.zz.y, iz, -r.lz);
-        tn = fmax3(ax, ay, fmaxf(az, r.tmin));
-        tf = fminf(__fmul_rn(fmin3(bx, by, bz), ROBUST_FAR), tcap);
-    } else {
-        // (bound + (-o)) * inv, two axes per packed operation: the same
-        // round-to-nearest results as (bound - o) * inv one at a time
-        const float2 a = __fmul2_rn(__fadd2_rn(b.lxy, r.nxy), r.ixy);
-        const float2 c = __fmul2_rn(__fadd2_rn(b.hxy, r.nxy), r.ixy);
-        const float2 z = __fmul2_rn(__fadd2_rn(b.zz, r.nzz), r.izz);
-        tn = fmax3(fminf(a.x, c.x), fminf(a.y, c.y), fmaxf(fminf(z.x, z.y), r.tmin));
-        const float f = fmin3(fmaxf(a.x, c.x), fmaxf(a.y, c.y), fmaxf(z.x, z.y));
-        tf = fminf(__fmul_rn(f, ROBUST_FAR), tcap);
-    }
+    const float2 a = __fmul2_rn(__fadd2_rn(b.lxy, r.nxy), r.ixy);
+    const float2 c = __fmul2_rn(__fadd2_rn(b.hxy, r.nxy), r.ixy);
+    const float2 z = __fmul2_rn(__fadd2_rn(b.zz, r.nzz), r.izz);
+    tn = fmax3(fminf(a.x, c.x), fminf(a.y, c.y), fmaxf(fminf(z.x, z.y), r.tmin));
+    const float f = fmin3(fmaxf(a.x, c.x), fmaxf(a.y, c.y), fmaxf(z.x, z.y));
+    tf = fminf(__fmul_rn(f, ROBUST_FAR), tcap);
 }
 
 // Moller-Trumbore on record k; returns true with (t, u, v) on a hit in
@@ -179,9 +162,15 @@ __device__ __forceinline__ void fetch_exact(const uint4 *nodes, uint32_t ref, Ch
 
 // Child c of a 128-byte wide node (rows of four floats: lo.x hi.x lo.y
 // hi.y lo.z hi.z, then the four references) given the ray's near and far
-// rows: the directed slab test of its exact box.  t is the child's entry
-// distance if the ray meets it (clamped to the largest float, so +inf
-// marks only unused and missed slots), else +inf.
+// rows (boxes are stored with lo <= hi, so the near plane of an axis is lo
+// for a positive reciprocal direction and hi for a negative one).  Directed
+// slab test: the near distance (near - o) * inv is bounded from below by one
+// fma rounded down against o * inv rounded up, the far one from above by
+// one fma rounded up against o * inv rounded down, so the only error left
+// is the relative one of the rounded reciprocal, which the widened far
+// distance covers.  t is the child's entry distance if the ray meets it
+// (clamped to the largest float, so +inf marks only unused and missed
+// slots), else +inf.
 __device__ __forceinline__ float wide_child(const Ray &r, float nx, float ny, float nz, float fx, float fy, float fz,
                                             uint32_t ref, float tcap) {
     const float ix = r.ixy.x, iy = r.ixy.y, iz = r.izz.x;
@@ -329,8 +318,8 @@ __device__ __forceinline__ void ray_round(RayState &s, uint2 *stack, const uint4
             if (lane == (uint32_t)(__ffs(__activemask()) - 1)) ++cn.warp_nodes;
         }
         float tn0, tf0, tn1, tf1;
-        slab<ANY>(s.r, c.b0, s.tcap, tn0, tf0);
-        slab<ANY>(s.r, c.b1, s.tcap, tn1, tf1);
+        slab(s.r, c.b0, s.tcap, tn0, tf0);
+        slab(s.r, c.b1, s.tcap, tn1, tf1);
         const bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
         if (h0 && h1) {
             const bool first0 = tn0 <= tn1;
