@@ -298,19 +298,20 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_multi(const float4 *__rest
             const float ix = __frcp_rn(d.x), iy = __frcp_rn(d.y), iz = __frcp_rn(d.z);
             K bit = (K)1 << (key_bits - 1);
             if (sc.cut_ordered && isfinite(ix) && isfinite(iy) && isfinite(iz)) {
-                // bounds selected by the direction signs, as in k_encode_hcc
-                const float *cf = reinterpret_cast<const float *>(sc.cut);  // per node: lo.xyzw hi.xyzw
-                const uint32_t nx = ix < 0.0f ? 4u : 0u, ny = iy < 0.0f ? 5u : 1u, nz = iz < 0.0f ? 6u : 2u;
-                const uint32_t fx = 4u - nx, fy = 6u - ny, fz = 8u - nz;
+                // (near, far) pairs selected by the direction signs and packed
+                // arithmetic, as in k_encode_hcc
+                const bool sx = ix < 0.0f, sy = iy < 0.0f, sz = iz < 0.0f;
+                const float2 nox = make_float2(-o.x, -o.x), noy = make_float2(-o.y, -o.y), noz = make_float2(-o.z, -o.z);
+                const float2 ixx = make_float2(ix, ix), iyy = make_float2(iy, iy), izz = make_float2(iz, iz);
                 for (uint32_t r = 0; r < sc.used; ++r, bit >>= 1) {
-                    const float *b = cf + 8 * r;
-                    const float tnear = fmax3(__fmul_rn(__fsub_rn(__ldg(b + nx), o.x), ix),
-                                              __fmul_rn(__fsub_rn(__ldg(b + ny), o.y), iy),
-                                              fmaxf(__fmul_rn(__fsub_rn(__ldg(b + nz), o.z), iz), o.w));
-                    const float tfar = fmin3(__fmul_rn(__fsub_rn(__ldg(b + fx), o.x), ix),
-                                             __fmul_rn(__fsub_rn(__ldg(b + fy), o.y), iy),
-                                             fminf(__fmul_rn(__fsub_rn(__ldg(b + fz), o.z), iz), d.w));
-                    if (tnear <= tfar) key |= bit;
+                    const float4 lo = __ldg(sc.cut + 2 * r), hi = __ldg(sc.cut + 2 * r + 1);
+                    const float2 px = sx ? make_float2(hi.x, lo.x) : make_float2(lo.x, hi.x);
+                    const float2 py = sy ? make_float2(hi.y, lo.y) : make_float2(lo.y, hi.y);
+                    const float2 pz = sz ? make_float2(hi.z, lo.z) : make_float2(lo.z, hi.z);
+                    const float2 tx = __fmul2_rn(__fadd2_rn(px, nox), ixx);
+                    const float2 ty = __fmul2_rn(__fadd2_rn(py, noy), iyy);
+                    const float2 tz = __fmul2_rn(__fadd2_rn(pz, noz), izz);
+                    if (fmax3(tx.x, ty.x, fmaxf(tz.x, o.w)) <= fmin3(tx.y, ty.y, fminf(tz.y, d.w))) key |= bit;
                 }
             } else {
                 for (uint32_t r = 0; r < sc.used; ++r, bit >>= 1)
@@ -410,19 +411,21 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_mlhcc(const float4 *__rest
                                                             uint32_t top_field, const float4 *__restrict__ low,
                                                             uint32_t low_field, uint32_t key_bits,
                                                             K *__restrict__ keys) {
-    extern __shared__ float s_box[];  // per box: lo.x hi.x lo.y hi.y lo.z hi.z; top boxes, then low rows
+    // per box and axis the two orders of its bounds, (lo, hi) and (hi, lo),
+    // as in k_encode_hcc; top boxes, then the low rows
+    extern __shared__ float2 s_pair[];
     const uint32_t nbox = ntop + ntop * low_field;
     bool ordered = true;
     for (uint32_t q = threadIdx.x; q < nbox; q += blockDim.x) {
         const float4 lo = q < ntop ? top[2 * q] : low[2 * (q - ntop)];
         const float4 hi = q < ntop ? top[2 * q + 1] : low[2 * (q - ntop) + 1];
-        float *b = s_box + 6 * q;
-        b[0] = lo.x;
-        b[1] = hi.x;
-        b[2] = lo.y;
-        b[3] = hi.y;
-        b[4] = lo.z;
-        b[5] = hi.z;
+        float2 *b = s_pair + 6 * q;
+        b[0] = make_float2(lo.x, hi.x);
+        b[1] = make_float2(hi.x, lo.x);
+        b[2] = make_float2(lo.y, hi.y);
+        b[3] = make_float2(hi.y, lo.y);
+        b[4] = make_float2(lo.z, hi.z);
+        b[5] = make_float2(hi.z, lo.z);
         ordered = ordered && lo.x <= hi.x && lo.y <= hi.y && lo.z <= hi.z;
     }
     ordered = __syncthreads_and(ordered);
@@ -431,21 +434,23 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_mlhcc(const float4 *__rest
         const float4 o = __ldcs(org + i);
         const float4 d = __ldcs(dir + i);
         const float ix = __frcp_rn(d.x), iy = __frcp_rn(d.y), iz = __frcp_rn(d.z);
-        // the slab test of box q: bounds selected by the direction signs when
-        // that is exact (see k_encode_hcc), the general test otherwise
+        // the slab test of box q: (near, far) pairs selected by the direction
+        // signs and packed arithmetic when that is exact (see k_encode_hcc),
+        // the general test otherwise
         const bool fast = ordered && isfinite(ix) && isfinite(iy) && isfinite(iz);
-        const uint32_t nx = ix < 0.0f, ny = 2u + (iy < 0.0f), nz = 4u + (iz < 0.0f);
-        const uint32_t fx = 1u - nx, fy = 5u - ny, fz = 9u - nz;
+        const uint32_t sx = ix < 0.0f, sy = 2u + (iy < 0.0f), sz = 4u + (iz < 0.0f);
+        const float2 nox = make_float2(-o.x, -o.x), noy = make_float2(-o.y, -o.y), noz = make_float2(-o.z, -o.z);
+        const float2 ixx = make_float2(ix, ix), iyy = make_float2(iy, iy), izz = make_float2(iz, iz);
         auto hit = [&](uint32_t q) {
-            const float *b = s_box + 6 * q;
+            const float2 *b = s_pair + 6 * q;
             if (fast) {
-                const float tnear = fmax3(__fmul_rn(__fsub_rn(b[nx], o.x), ix), __fmul_rn(__fsub_rn(b[ny], o.y), iy),
-                                          fmaxf(__fmul_rn(__fsub_rn(b[nz], o.z), iz), o.w));
-                const float tfar = fmin3(__fmul_rn(__fsub_rn(b[fx], o.x), ix), __fmul_rn(__fsub_rn(b[fy], o.y), iy),
-                                         fminf(__fmul_rn(__fsub_rn(b[fz], o.z), iz), d.w));
-                return tnear <= tfar;
+                const float2 tx = __fmul2_rn(__fadd2_rn(b[sx], nox), ixx);
+                const float2 ty = __fmul2_rn(__fadd2_rn(b[sy], noy), iyy);
+                const float2 tz = __fmul2_rn(__fadd2_rn(b[sz], noz), izz);
+                return fmax3(tx.x, ty.x, fmaxf(tz.x, o.w)) <= fmin3(tx.y, ty.y, fminf(tz.y, d.w));
             }
-            return meets(o, d, ix, iy, iz, make_float4(b[0], b[2], b[4], 0.f), make_float4(b[1], b[3], b[5], 0.f));
+            return meets(o, d, ix, iy, iz, make_float4(b[0].x, b[2].x, b[4].x, 0.f),
+                         make_float4(b[0].y, b[2].y, b[4].y, 0.f));
         };
         K key = 0;
         K bit = (K)1 << (key_bits - 1);
@@ -534,14 +539,20 @@ cudaError_t launch_encode_mlhcc(cudaStream_t s, const float4 *org, const float4 
     if (n == 0) return cudaSuccess;
     if (ntop > top_field || top_field + low_field > MAX_CUT_BITS || top_field + low_field > key_bits)
         return cudaErrorInvalidValue;
-    const size_t smem = sizeof(float) * 6 * ((size_t)ntop + (size_t)ntop * low_field);
+    // six float2 per box: at most (32 + 32 * 32) * 48 bytes = 50,688 bytes
+    const size_t smem = sizeof(float2) * 6 * ((size_t)ntop + (size_t)ntop * low_field);
     const int grid = encode_grid(n, ENC_BLOCK, 8);
-    if (key_bits <= 32)
+    if (key_bits <= 32) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_encode_mlhcc<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_encode_mlhcc<uint32_t><<<grid, ENC_BLOCK, smem, s>>>(org, dir, n, top, ntop, top_field, low, low_field,
                                                               key_bits, (uint32_t *)keys);
-    else
+    } else {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_encode_mlhcc<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_encode_mlhcc<uint64_t><<<grid, ENC_BLOCK, smem, s>>>(org, dir, n, top, ntop, top_field, low, low_field,
                                                               key_bits, (uint64_t *)keys);
+    }
     return cudaGetLastError();
 }
 

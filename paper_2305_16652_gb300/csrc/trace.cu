@@ -33,7 +33,7 @@ constexpr float PRUNE_SLACK = 1.0f + 1.0f / 65536.0f;
 // warp's neighbouring rays together (measured faster for each)
 constexpr uint32_t REFILL_MIN = 12;
 // resident blocks per SM the persistent kernel is built for: binary nodes
-// (48 registers) and wide nodes (56)
+// (48 registers), and wide nodes or a batch of scenes (56)
 constexpr int POOL_BLOCKS = 10;
 constexpr int POOL_BLOCKS_WIDE = 9;
 constexpr uint32_t REFILL_MIN_SORTED = 24;
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
 // traversal does not depend on which rays share its warp, except for which
 // of several hits an any-hit query returns first.
 template <bool ANY, bool COUNT, int LAYOUT, bool MULTI>
-__global__ void __launch_bounds__(TRACE_BLOCK, LAYOUT == 2 ? POOL_BLOCKS_WIDE : POOL_BLOCKS) k_trace_pool(TraceArgs a) {
+__global__ void __launch_bounds__(TRACE_BLOCK, (LAYOUT == 2 || MULTI) ? POOL_BLOCKS_WIDE : POOL_BLOCKS) k_trace_pool(TraceArgs a) {
     constexpr uint32_t FULL = 0xFFFFFFFFu;
     const uint32_t lane = threadIdx.x & 31;
     uint32_t lt;
@@ -528,20 +528,21 @@ cudaError_t launch_trace(cudaStream_t s, const TraceArgs &a, int any_hit) {
     if (pool) {
         // persistent grid: every block resident at once (the residency is
         // queried once per device; all pool variants share the launch bounds)
+        // (kernels with the same launch bounds share an entry)
         static std::atomic<int> resident[64][2];
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int wide = a.layout == 2 ? 1 : 0;
-        int per_sm = (dev >= 0 && dev < 64) ? resident[dev][wide].load() : 0;
+        const int roomy = (a.layout == 2 || multi) ? 1 : 0;
+        int per_sm = (dev >= 0 && dev < 64) ? resident[dev][roomy].load() : 0;
         if (per_sm <= 0) {
-            if (wide)
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_pool<false, false, 2, false>,
+            if (roomy)
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_pool<false, false, 1, true>,
                                                               TRACE_BLOCK, 0);
             else
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_pool<false, false, 1, false>,
                                                               TRACE_BLOCK, 0);
-            if (dev >= 0 && dev < 64 && per_sm > 0) resident[dev][wide].store(per_sm);
+            if (dev >= 0 && dev < 64 && per_sm > 0) resident[dev][roomy].store(per_sm);
         }
         const unsigned cap = (unsigned)std::max(1, sms) * (unsigned)std::max(1, per_sm);
         blocks = std::min(blocks, cap);
