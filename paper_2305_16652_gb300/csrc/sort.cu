@@ -261,12 +261,13 @@ __device__ __forceinline__ void load_tile_async(T *dst, const T *src, uint32_t c
     }
 }
 
-// One digit pass.  Persistent blocks (two per SM) take tiles of 4096 keys in
-// launch order from an atomic counter; while a tile is ranked and written,
-// the next tile's keys and values stream into the other shared-memory
-// buffer (cp.async), so the DRAM latency of a tile overlaps the work on the
-// previous one.  Per tile: warp-level stable ranking (ballot bit-split, the
-// group leader's atomic returns the group's base), the tile's digit counts
+// One digit pass.  Persistent blocks (three per SM for 32-bit keys, two for
+// 64-bit keys) take tiles of 4096 keys in launch order from an atomic
+// counter; while a tile is ranked and written, the next tile's keys and
+// values stream into the other shared-memory buffer (cp.async), so the DRAM
+// latency of a tile overlaps the work on the previous one.  Per tile:
+// warp-level stable ranking (match.any or the ballot bit-split, the group
+// leader's atomic returns the group's base), the tile's digit counts
 // published at once to the decoupled look-back chain, the tile reordered by
 // digit in shared memory, the look-back for the global offsets (bounded
 // waits with back-off), and runs of equal digits written out coalesced.
