@@ -507,10 +507,11 @@ hcc_status hcc_run(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const hc
  * n records, all in host memory (page-locked memory gives asynchronous,
  * full-speed copies).  Copies the rays to device scratch, runs the
  * pipeline, copies the hits back and waits, so the hits are valid on return.
- * Above 2^22 rays, the rays go through in chunks of 2^22 that alternate
- * between two internal streams (each chunk encoded, sorted and traced on
- * its own), so that the copies of one chunk overlap the kernels of the
- * other; the hits are the same as hcc_run's.  Errors: as hcc_run, plus those
+ * Above 2^22 rays, the rays go through in chunks of 2^22 (the first one
+ * 2^21, so the first kernels start sooner) that alternate between two
+ * internal streams (each chunk encoded, sorted and traced on its own), so
+ * that the copies of one chunk overlap the kernels of the other; the hits
+ * are the same as hcc_run's.  Errors: as hcc_run, plus those
  * of hcc_sync.
  */
 hcc_status hcc_run_host(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const hcc_cut *cut,

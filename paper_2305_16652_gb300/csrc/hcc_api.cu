@@ -1479,11 +1479,12 @@ hcc_status hcc_run_host(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, con
         }
     }
     hcc_status result = HCC_OK;
-    for (uint64_t c0 = 0, c = 0; c0 < n && result == HCC_OK; c0 += HOST_CHUNK, ++c) {
+    for (uint64_t c0 = 0, c = 0, m = 0; c0 < n && result == HCC_OK; c0 += m, ++c) {
         hcc_ctx *L = ctx->lane[c % HOST_LANES];
         L->schedule = ctx->schedule;
         L->twopoint_fraction = ctx->twopoint_fraction;
-        const uint64_t m = std::min<uint64_t>(HOST_CHUNK, n - c0);
+        // the first chunk is half as large, so the first kernels start sooner
+        m = std::min<uint64_t>(c == 0 ? HOST_CHUNK / 2 : HOST_CHUNK, n - c0);
         if ((st = ensure(L, L->in_org, HOST_CHUNK * 16, "input rays")) != HCC_OK ||
             (st = ensure(L, L->in_dir, HOST_CHUNK * 16, "input rays")) != HCC_OK ||
             (st = ensure(L, L->hits, HOST_CHUNK * sizeof(hcc_hit), "hits")) != HCC_OK) {
