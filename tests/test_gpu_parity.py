@@ -533,17 +533,31 @@ def test_trace_schedules_give_the_same_records(ctx, which, request):
         hcc.hcc_cut_destroy(cut)
 
 
-def test_run_host_pipeline_over_chunks(ctx):
-    """4.7M rays go through the two-stream chunked host pipeline: every hit equals
-    the device pipeline's, and a sample equals the oracle's."""
+@pytest.fixture(scope="module")
+def chunk_room():
     w = gen.room_workload(2, target_tris=60_000, W=1024, H=576, spp=8, shadow=False)
-    n = w.rays.n
-    assert n >= 1 << 22
+    assert w.rays.n >= 1 << 22
+    return w
+
+
+# the whole wavefront (a 2^21 chunk, then 2^22 and the rest), one ray more
+# than a single pass (2^21 + 2^21 + 1), and three chunks with a 5-ray tail
+@pytest.mark.parametrize("n_rays", [None, (1 << 22) + 1, (1 << 21) + (1 << 22) + 5])
+def test_run_host_pipeline_over_chunks(ctx, chunk_room, n_rays):
+    """Rays above 2^22 go through the two-stream chunked host pipeline: every
+    hit equals the device pipeline's, and a sample equals the oracle's."""
+    w = chunk_room
+    org_np, dir_np = w.rays.org, w.rays.dir
+    if n_rays is not None:  # repeat the wavefront's rays to reach n_rays
+        reps = -(-n_rays // w.rays.n)
+        org_np = np.ascontiguousarray(np.concatenate([org_np] * reps)[:n_rays])
+        dir_np = np.ascontiguousarray(np.concatenate([dir_np] * reps)[:n_rays])
+    n = org_np.shape[0]
     bvh = hcc.hcc_bvh_upload(ctx, w.bvh, layout="exact")
     cut = hcc.hcc_select_cut(ctx, bvh, 32, 0.125)
     try:
-        org = torch.from_numpy(w.rays.org).pin_memory()
-        dir_ = torch.from_numpy(w.rays.dir).pin_memory()
+        org = torch.from_numpy(org_np).pin_memory()
+        dir_ = torch.from_numpy(dir_np).pin_memory()
         for method in ("hcc", "nosort"):
             h_host = torch.zeros((n, 4), dtype=torch.int32).pin_memory()
             hcc.hcc_run_host(ctx, method, bvh, cut, org, dir_, 32, h_host)
@@ -552,7 +566,8 @@ def test_run_host_pipeline_over_chunks(ctx):
             hcc.hcc_sync(ctx)
             assert torch.equal(h_host, d_hits.cpu()), method
         idx = np.random.default_rng(5).choice(n, 3000, replace=False)
-        ref = oracle.trace_bvh(w.bvh, w.rays.org[idx], w.rays.dir[idx])
+        idx = np.concatenate([idx, np.arange(n - 5, n)])  # the last chunk's rays
+        ref = oracle.trace_bvh(w.bvh, org_np[idx], dir_np[idx])
         assert hcc.hits_to_numpy(h_host)[idx].tobytes() == ref.tobytes()
         # the chunked path reports errors like the one-pass path
         with pytest.raises(hcc.HccError):
