@@ -932,6 +932,9 @@ def profile_case(name: str):
     trace-small: 480x270x8spp room, 200k triangles, exact nodes: HCC encode,
                  sort, trace through the sorted ids, then the NoSort trace.
     sort-16m:    two sorts of 16,588,800 seeded uniform 32-bit keys.
+    trace-orders: the 1920x1080x8spp room (16,588,800 rays), exact nodes: the
+                 closest-hit trace in NoSort, TwoPoint and HCC order (32-bit
+                 keys, cut 32), one launch each, in that order.
     """
     import torch
     from paper_2305_16652_gb300 import build, hcc
@@ -957,6 +960,21 @@ def profile_case(name: str):
         hcc.hcc_sort(ctx, keys, 32, n, perm)
         hcc.hcc_trace_sorted(ctx, bvh, org, dir_, perm, hits)
         hcc.hcc_trace(ctx, bvh, org, dir_, hits)
+    elif name == "trace-orders":
+        w = make_workload(1, False)
+        n = w.rays.n
+        bvh = hcc.hcc_bvh_upload(ctx, w.bvh, layout="exact")
+        cut = hcc.hcc_select_cut(ctx, bvh, 32, 0.125)
+        org, dir_ = torch.from_numpy(w.rays.org).cuda(), torch.from_numpy(w.rays.dir).cuda()
+        keys = torch.empty(n, dtype=torch.int32, device="cuda")
+        perm = torch.empty(n, dtype=torch.int32, device="cuda")
+        hits = torch.empty((n, 4), dtype=torch.int32, device="cuda")
+        hcc.hcc_reserve(ctx, n, 32)
+        hcc.hcc_trace(ctx, bvh, org, dir_, hits)
+        for method in ("twopoint", "hcc"):
+            hcc.hcc_encode(ctx, method, bvh, cut if method == "hcc" else None, org, dir_, 32, keys)
+            hcc.hcc_sort(ctx, keys, 32, n, perm)
+            hcc.hcc_trace_sorted(ctx, bvh, org, dir_, perm, hits)
     else:
         raise SystemExit(f"unknown case {name}")
     hcc.hcc_sync(ctx)
@@ -977,7 +995,7 @@ def main(argv=None):
     ap.add_argument("--cpu-sample", type=int, default=1_500_000)
     ap.add_argument("--ref-sample", type=int, default=300_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["trace-small", "sort-16m"], help="run a small profiling case and exit")
+    ap.add_argument("--case", choices=["trace-small", "sort-16m", "trace-orders"], help="run a profiling case and exit")
     ap.add_argument("--sweep", choices=["keylen", "batch", "serve", "methods", "hyper"],
                     help="run a study instead of the headline benchmark")
     ap.add_argument("--slots", type=int, default=4, help="serving: requests on the GPU at once")
