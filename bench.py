@@ -584,8 +584,9 @@ def run_methods_sweep(args):
 def run_hyper_sweep(args):
     """Hyperparameter study (App. B): the HAD weight lambda of Eq. 1 for HCC (cut 32,
     32-bit keys) and the TwoPoint estimated ray length as a fraction of the largest
-    scene extent, each from 0.1 to 1.0, on the 1080p wavefront; per point the stage
-    times, end-to-end Mrays/s, trace speedup over NoSort and ANC."""
+    scene extent, each from 0.1 to 1.0, and the HCC cut size from 32 to 4096 nodes at
+    32-bit keys, on the 1080p wavefront; per point the stage times, end-to-end
+    Mrays/s, trace speedup over NoSort and ANC."""
     import torch
     from paper_2305_16652_gb300 import build, hcc
     build()
@@ -634,10 +635,18 @@ def run_hyper_sweep(args):
         hcc.hcc_set_twopoint_distance(ctx, f)
         tp_rows.append({"fraction": f, **point("twopoint", None)})
     hcc.hcc_set_twopoint_distance(ctx, 0.25)
-    out = {"metric": "hyperparameter study: HCC lambda and TwoPoint length fraction", "unit": "Mrays/s",
+    # cut size at 32-bit keys: Algorithm 2 run to C nodes, the key built from
+    # the 32 of highest HAD (a larger C reaches deeper, smaller nodes)
+    cut_rows = []
+    for c in (32, 64, 128, 256, 512, 1024, 2048, 4096):
+        cut = hcc.hcc_select_cut(ctx, bvh, c, 0.125)
+        cut_rows.append({"cut_size": c, **point("hcc", cut)})
+        hcc.hcc_cut_destroy(cut)
+    out = {"metric": "hyperparameter study: HCC lambda and cut size, TwoPoint length fraction", "unit": "Mrays/s",
            "config": {"workload": w.name + f" ({n} secondary rays)", "bvh_layout": args.layout, "cut_size": 32,
                       "key_bits": 32},
-           "nosort_trace_ms": round(t0, 4), "hcc_lambda": lam_rows, "twopoint_fraction": tp_rows}
+           "nosort_trace_ms": round(t0, 4), "hcc_lambda": lam_rows, "twopoint_fraction": tp_rows,
+           "hcc_cut_size": cut_rows}
     hcc.hcc_bvh_destroy(bvh)
     hcc.hcc_destroy(ctx)
     print(json.dumps(out), flush=True)
