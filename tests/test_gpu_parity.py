@@ -163,6 +163,30 @@ def test_encode_hcc_matches_oracle(ctx, which, C, k, request):
         assert len(np.unique(g)) > 1
 
 
+@pytest.mark.parametrize("k", [16, 32, 64])
+@pytest.mark.parametrize("C", [256, 4096])
+def test_encode_hcc_large_cuts_use_the_highest_had_nodes(ctx, room, C, k):
+    """A cut larger than the key: the key's bits come from the min(C, k) cut
+    nodes of highest HAD, in the oracle's order."""
+    cut = hcc.hcc_select_cut(ctx, room.bvh, C, 0.125)
+    ids = hcc.hcc_cut_info(cut)
+    try:
+        assert len(ids) == C
+        g = gpu_encode(ctx, room, "hcc", k, cut=cut)
+    finally:
+        hcc.hcc_cut_destroy(cut)
+    lo, hi = room.w.bvh.lo[ids], room.w.bvh.hi[ids]
+    o = oracle.encode_hcc(room.w.rays.org, room.w.rays.dir, lo, hi, k)
+    o_first = oracle.encode_hcc(room.w.rays.org, room.w.rays.dir, lo[:k], hi[:k], k)
+    assert np.array_equal(o, o_first)  # the oracle reads only the first k nodes
+    bad = np.nonzero(g != o)[0]
+    if len(bad):
+        m = oracle.key_margin(room.w.rays.org[bad], room.w.rays.dir[bad], lo, hi, k)
+        assert np.all(m < 1e-6), f"{len(bad)} key mismatches on non-marginal rays"
+    assert len(bad) <= max(1, room.n // 1000)
+    assert len(np.unique(g)) > 1
+
+
 @pytest.mark.parametrize("k", [1, 5, 6, 16, 30, 32, 33, 60, 64])
 def test_encode_twopoint_matches_oracle(ctx, room, k):
     g = gpu_encode(ctx, room, "twopoint", k)
