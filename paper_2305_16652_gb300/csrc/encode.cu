@@ -453,18 +453,35 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_mlhcc(const float4 *__rest
                          make_float4(b[0].y, b[2].y, b[4].y, 0.f));
         };
         K key = 0;
-        K bit = (K)1 << (key_bits - 1);
-        uint32_t rep = ntop;
-        for (uint32_t r = 0; r < ntop; ++r, bit >>= 1)
-            if (hit(r)) {
-                key |= bit;
-                rep = min(rep, r);
+        if (fast) {
+            // top bits first (node r at bit ntop - 1 - r of tb), then the low
+            // row of the first met top node (the highest set bit of tb)
+            uint64_t tb = 0;
+#pragma unroll 8
+            for (uint32_t r = 0; r < ntop; ++r) tb = (tb << 1) | (uint64_t)hit(r);
+            key = ntop ? (K)(tb << (key_bits - ntop)) : (K)0;
+            if (tb) {
+                const uint32_t rep = ntop - 64u + (uint32_t)__clzll((long long)tb);
+                const uint32_t row = ntop + rep * low_field;
+                uint64_t lb = 0;
+#pragma unroll 8
+                for (uint32_t j = 0; j < low_field; ++j) lb = (lb << 1) | (uint64_t)hit(row + j);
+                if (low_field) key |= (K)(lb << (key_bits - top_field - low_field));
             }
-        if (rep < ntop) {
-            const uint32_t row = ntop + rep * low_field;
-            K lbit = (K)1 << (key_bits - 1 - top_field);
-            for (uint32_t j = 0; j < low_field; ++j, lbit >>= 1)
-                if (hit(row + j)) key |= lbit;
+        } else {
+            K bit = (K)1 << (key_bits - 1);
+            uint32_t rep = ntop;
+            for (uint32_t r = 0; r < ntop; ++r, bit >>= 1)
+                if (hit(r)) {
+                    key |= bit;
+                    rep = min(rep, r);
+                }
+            if (rep < ntop) {
+                const uint32_t row = ntop + rep * low_field;
+                K lbit = (K)1 << (key_bits - 1 - top_field);
+                for (uint32_t j = 0; j < low_field; ++j, lbit >>= 1)
+                    if (hit(row + j)) key |= lbit;
+            }
         }
         __stcs(keys + i, key);
     }
