@@ -202,9 +202,9 @@ def test_ppc_deep_and_degenerate_trees(ctx, tiny):
 
 # ------------------------------------------------------------ pipelines
 
-@pytest.mark.parametrize("layout", ["exact", "quantised"])
+@pytest.mark.parametrize("layout", ["exact", "quantised", "wide"])
 def test_variant_pipelines_give_the_nosort_hits(ctx, room, layout):
-    bvh = room.bvh_exact if layout == "exact" else room.bvh
+    bvh = {"exact": room.bvh_exact, "quantised": room.bvh, "wide": room.bvh_wide}[layout]
     hits0 = torch.zeros((room.n, 4), dtype=torch.int32, device=DEV)
     hcc.hcc_run(ctx, "nosort", bvh, None, room.org, room.dir, 32, hits0)
     ml = hcc.hcc_select_cut_ml(ctx, bvh, 16, 16, 0.125)
@@ -212,6 +212,11 @@ def test_variant_pipelines_give_the_nosort_hits(ctx, room, layout):
     cases = [("mlhcc", ml, 32), ("mlhcc", ml, 48), ("hcc", grid, 32)]
     if layout == "exact":
         cases += [("ppc", None, 32), ("ppc", None, 64)]
+    else:  # the prefix path code walks exact BVH2 nodes only
+        keys = torch.zeros(room.n, dtype=torch.int32, device=DEV)
+        with pytest.raises(hcc.HccError) as ei:
+            hcc.hcc_encode(ctx, "ppc", bvh, None, room.org, room.dir, 32, keys)
+        assert ei.value.status == 4
     try:
         for method, cut, k in cases:
             hits = torch.zeros_like(hits0)
