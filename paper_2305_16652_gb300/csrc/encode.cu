@@ -3,8 +3,10 @@
 // TwoPoint, Origin and Origin-Direction baselines (Sec. 3.2, Sec. 5).
 //
 // Floating point: every rounding step is an explicit round-to-nearest
-// intrinsic and the library is built with --fmad=false, so each key is the
-// same bit pattern the arithmetic defines, whatever the compiler schedules.
+// intrinsic (scalar, or Blackwell's packed FP32x2 add and multiply, which
+// round each half the same way) and the library is built with
+// --fmad=false, so each key is the same bit pattern the arithmetic defines,
+// whatever the compiler schedules.
 #include "hcc_internal.cuh"
 
 namespace hcc {

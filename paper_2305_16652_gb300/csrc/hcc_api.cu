@@ -1,7 +1,9 @@
 // C ABI of the hcc library: argument checking, device memory, the BVH
-// upload (quantised node layout), host-side cut selection (Sec. 4.2.2) and
-// the per-bounce pipeline (Sec. 5).  Kernels live in encode.cu, sort.cu,
-// gather.cu and trace.cu.
+// upload (quantised and exact BVH2 node layouts, 4-ary nodes collapsed from
+// the BVH2), host-side cut selection (Sec. 4.2.2), the per-bounce pipeline
+// (Sec. 5), batches of wavefronts and CUDA graphs.  Kernels live in
+// encode.cu, sort.cu, gather.cu, trace.cu and spawn.cu; the serving loop in
+// serve.cu.
 #include <algorithm>
 #include <array>
 #include <cmath>
