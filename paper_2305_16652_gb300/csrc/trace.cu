@@ -429,6 +429,10 @@ __device__ __forceinline__ bool fetch_ray(const TraceArgs &a, uint64_t i, float4
 
 // Writes the record of ray slot i to hits[scatter[i]] (or i).
 __device__ __forceinline__ void store_hit(const TraceArgs &a, uint64_t i, const RayState &s) {
+    if (i >= a.n) {  // not a ray slot: report, never index the permutation out of bounds
+        atomicOr(a.err, ERR_INDEX);
+        return;
+    }
     if (s.overflow) atomicOr(a.err, ERR_STACK);
     const uint64_t dst = a.scatter ? (uint64_t)a.scatter[i] : i;
     if (dst < a.n)
