@@ -941,6 +941,8 @@ def profile_case(name: str):
     trace-small: 480x270x8spp room, 200k triangles, exact nodes: HCC encode,
                  sort, trace through the sorted ids, then the NoSort trace.
     sort-16m:    two sorts of 16,588,800 seeded uniform 32-bit keys.
+    sort-hcc:    two sorts of the 16,588,800 HCC keys (cut 32, 32-bit keys) of
+                 the 1920x1080x8spp room wavefront.
     trace-orders: the 1920x1080x8spp room (16,588,800 rays), exact nodes: the
                  closest-hit trace in NoSort, TwoPoint and HCC order (32-bit
                  keys, cut 32), one launch each, in that order.
@@ -956,6 +958,18 @@ def profile_case(name: str):
         perm = torch.empty(n, dtype=torch.int32, device="cuda")
         for _ in range(2):
             hcc.hcc_sort(ctx, kt, 32, n, perm)
+    elif name == "sort-hcc":
+        w = make_workload(1, False)
+        n = w.rays.n
+        bvh = hcc.hcc_bvh_upload(ctx, w.bvh, layout="exact")
+        cut = hcc.hcc_select_cut(ctx, bvh, 32, 0.125)
+        org, dir_ = torch.from_numpy(w.rays.org).cuda(), torch.from_numpy(w.rays.dir).cuda()
+        keys = torch.empty(n, dtype=torch.int32, device="cuda")
+        perm = torch.empty(n, dtype=torch.int32, device="cuda")
+        hcc.hcc_reserve(ctx, n, 32)
+        hcc.hcc_encode(ctx, "hcc", bvh, cut, org, dir_, 32, keys)
+        for _ in range(2):
+            hcc.hcc_sort(ctx, keys, 32, n, perm)
     elif name == "trace-small":
         w = make_workload(1, True)
         n = w.rays.n
@@ -1004,7 +1018,7 @@ def main(argv=None):
     ap.add_argument("--cpu-sample", type=int, default=1_500_000)
     ap.add_argument("--ref-sample", type=int, default=300_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["trace-small", "sort-16m", "trace-orders"], help="run a profiling case and exit")
+    ap.add_argument("--case", choices=["trace-small", "sort-16m", "sort-hcc", "trace-orders"], help="run a profiling case and exit")
     ap.add_argument("--sweep", choices=["keylen", "batch", "serve", "methods", "hyper"],
                     help="run a study instead of the headline benchmark")
     ap.add_argument("--slots", type=int, default=4, help="serving: requests on the GPU at once")

@@ -26,3 +26,17 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+def pytest_terminal_summary(terminalreporter):
+    # the exception counts of the parity comparisons (keys on marginal rays,
+    # near-edge hit ties), per test and in total
+    try:
+        import parity
+    except ImportError:  # pragma: no cover
+        return
+    lines = parity.summary_lines()
+    if lines:
+        terminalreporter.write_sep("-", "parity exceptions")
+        for line in lines:
+            terminalreporter.write_line(line)

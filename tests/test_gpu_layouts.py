@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 from paper_2305_16652_gb300 import gen, hcc
-from test_gpu_parity import compare_hits
+from parity import compare_hits
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu

@@ -3,15 +3,17 @@
 Every check goes through the C ABI (libhcc.so via the ctypes binding).
 Integer results (cut ids, keys, permutations, gathered bytes) must be equal
 bit for bit.  Keys may differ only on rays within 1e-6 (relative) of a cut
-box boundary; hit records must be bit-identical except where two triangles
-tie in t within 1e-5 relative or the hit sits within 1e-6 of a triangle edge
-in barycentric terms.  Such exceptions are counted and bounded.
+box boundary; hit records must be bit-identical except on near-edge ties
+(the oracle's hit within 1e-6 of a triangle edge in barycentric terms, and t
+within 1e-5 relative); the rules are in parity.py.  Such exceptions are
+counted, bounded and printed at the end of the run.
 """
 import numpy as np
 import pytest
 
 import oracle
 from paper_2305_16652_gb300 import gen, hcc
+from parity import compare_hits, compare_keys
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -99,30 +101,6 @@ def gpu_trace(ctx, sc, org, dir_, any_hit=False, scatter=None, layout="quantised
     return hcc.hits_to_numpy(hits)
 
 
-def compare_hits(g, o, tol_t=1e-5, tol_b=1e-6, max_frac=1e-3):
-    """Bit-exact except counted near ties; returns the number of exceptions."""
-    gi32 = np.ascontiguousarray(g).view(np.int32).reshape(-1, 4)
-    oi32 = np.ascontiguousarray(o).view(np.int32).reshape(-1, 4)
-    bad = np.nonzero(np.any(gi32 != oi32, axis=1))[0]
-    exceptions = 0
-    for i in bad:
-        gi, oi = g[i], o[i]
-        if gi["prim"] >= 0 and oi["prim"] >= 0 and gi["prim"] == oi["prim"]:
-            raise AssertionError(f"ray {i}: same triangle, different numbers {gi} vs {oi}")
-        both = gi["prim"] >= 0 and oi["prim"] >= 0
-        if both and abs(float(gi["t"]) - float(oi["t"])) <= tol_t * max(1.0, abs(float(oi["t"]))):
-            exceptions += 1
-            continue
-        ref = oi if oi["prim"] >= 0 else gi
-        margin = min(float(ref["u"]), float(ref["v"]), 1.0 - float(ref["u"]) - float(ref["v"]))
-        if margin < tol_b:
-            exceptions += 1
-            continue
-        raise AssertionError(f"ray {i}: GPU {gi} vs oracle {oi}")
-    assert exceptions <= max(1, max_frac * len(g)), exceptions
-    return exceptions
-
-
 # --------------------------------------------------------------------- cut
 
 @pytest.mark.parametrize("which", ["tiny", "room"])
@@ -153,11 +131,7 @@ def test_encode_hcc_matches_oracle(ctx, which, C, k, request):
         hcc.hcc_cut_destroy(cut)
     lo, hi = sc.w.bvh.lo[ids], sc.w.bvh.hi[ids]
     o = oracle.encode_hcc(sc.w.rays.org, sc.w.rays.dir, lo, hi, k)
-    bad = np.nonzero(g != o)[0]
-    if len(bad):
-        m = oracle.key_margin(sc.w.rays.org[bad], sc.w.rays.dir[bad], lo, hi, k)
-        assert np.all(m < 1e-6), f"{len(bad)} key mismatches on non-marginal rays"
-    assert len(bad) <= max(1, sc.n // 1000)
+    compare_keys(g, o, lambda b: oracle.key_margin(sc.w.rays.org[b], sc.w.rays.dir[b], lo, hi, k))
     assert np.all(g < (np.uint64(1) << np.uint64(k)) if k < 64 else True)
     if k >= 16:
         assert len(np.unique(g)) > 1
@@ -179,11 +153,7 @@ def test_encode_hcc_large_cuts_use_the_highest_had_nodes(ctx, room, C, k):
     o = oracle.encode_hcc(room.w.rays.org, room.w.rays.dir, lo, hi, k)
     o_first = oracle.encode_hcc(room.w.rays.org, room.w.rays.dir, lo[:k], hi[:k], k)
     assert np.array_equal(o, o_first)  # the oracle reads only the first k nodes
-    bad = np.nonzero(g != o)[0]
-    if len(bad):
-        m = oracle.key_margin(room.w.rays.org[bad], room.w.rays.dir[bad], lo, hi, k)
-        assert np.all(m < 1e-6), f"{len(bad)} key mismatches on non-marginal rays"
-    assert len(bad) <= max(1, room.n // 1000)
+    compare_keys(g, o, lambda b: oracle.key_margin(room.w.rays.org[b], room.w.rays.dir[b], lo, hi, k))
     assert len(np.unique(g)) > 1
 
 
@@ -657,10 +627,8 @@ def test_full_size_headline_configuration():
         rng = np.random.default_rng(11)
         idx = rng.choice(n, 20_000, replace=False)
         ref_k = oracle.encode_hcc(w.rays.org[idx], w.rays.dir[idx], w.bvh.lo[ids], w.bvh.hi[ids], 32)
-        bad = np.nonzero(k[idx] != ref_k)[0]
-        if len(bad):
-            m = oracle.key_margin(w.rays.org[idx[bad]], w.rays.dir[idx[bad]], w.bvh.lo[ids], w.bvh.hi[ids], 32)
-            assert np.all(m < 1e-6)
+        compare_keys(k[idx], ref_k, lambda b: oracle.key_margin(w.rays.org[idx[b]], w.rays.dir[idx[b]],
+                                                                 w.bvh.lo[ids], w.bvh.hi[ids], 32))
         # the permutation: every id once, keys non-decreasing, equal keys in id order
         assert np.array_equal(np.sort(p), np.arange(n))
         ks = k[p]
@@ -669,7 +637,7 @@ def test_full_size_headline_configuration():
         assert np.all(p[1:][same] > p[:-1][same])
         sample = idx[:3000]
         ref_h = oracle.trace_bvh(w.bvh, w.rays.org[sample], w.rays.dir[sample])
-        assert hcc.hits_to_numpy(hits)[sample].tobytes() == ref_h.tobytes()
+        compare_hits(hcc.hits_to_numpy(hits)[sample], ref_h)
     finally:
         hcc.hcc_cut_destroy(cut)
         hcc.hcc_bvh_destroy(bvh)

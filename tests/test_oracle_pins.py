@@ -132,6 +132,123 @@ def test_hcc_slab_matches_exact_clipping():
     assert checked > 0.9 * n * C
 
 
+# ------------------------------------------------------- slab-test margin
+#
+# A key bit may differ from the oracle only on a ray whose smallest relative
+# slab gap |tfar - tnear| / max(1, |tnear|, |tfar|) over the boxes that drive
+# key bits (the first min(cut size, k) in key order) is below 1e-6 (the
+# reading of Algorithm 1's intersection test at a box boundary).  Boxes the
+# ray misses through a zero direction component (an infinite distance) do
+# not count.  These pins fix that function by hand-worked rays and by exact
+# rational arithmetic.
+
+UNIT_LO = np.zeros((1, 3), np.float32)
+UNIT_HI = np.ones((1, 3), np.float32)
+
+
+def _margin1(o, d, tmin=0.0, tmax=np.inf, lo=UNIT_LO, hi=UNIT_HI, k=32):
+    org = np.array([[o[0], o[1], o[2], tmin]], np.float32)
+    dir_ = np.array([[d[0], d[1], d[2], tmax]], np.float32)
+    return float(oracle.key_margin(org, dir_, lo, hi, k)[0])
+
+
+def test_key_margin_hand_worked_unit_box():
+    # along x through the middle: the box spans t in [1, 2]: gap 1 over max(1, 1, 2) = 2
+    assert _margin1((-1, 0.5, 0.5), (1, 0, 0)) == 0.5
+    # through the corners (0,0,0) -> (1,1,1): t in [1, 2] on every axis
+    assert _margin1((-1, -1, -1), (1, 1, 1)) == 0.5
+    # touching the corner (1, 1, 1) only: x, y in [0, 1], z in [1, 2]: tnear = tfar = 1
+    assert _margin1((0, 0, 2), (1, 1, -1)) == 0.0
+    # origin inside, distances below 1: [max(-0.25, tmin 0), 0.75] -> 0.75 / max(1, 0, 0.75)
+    assert _margin1((0.25, 0.5, 0.5), (1, 0, 0)) == 0.75
+    # the interval end clips the box: [1, min(2, tmax 1.5)] -> 0.5 / 1.5
+    assert abs(_margin1((-1, 0.5, 0.5), (1, 0, 0), tmax=1.5) - 1.0 / 3.0) < 1e-7
+    # ... and so does its start: [max(1, tmin 1.75), 2] -> 0.25 / 2
+    assert _margin1((-1, 0.5, 0.5), (1, 0, 0), tmin=1.75) == 0.125
+    # a miss counts as well: the interval [1.75, 2] lies beyond tmax 1.25 -> tnear - tfar = 0.5 over 1.75
+    assert abs(_margin1((-1, 0.5, 0.5), (1, 0, 0), tmin=1.75, tmax=1.25) - 0.5 / 1.75) < 1e-7
+    # parallel to the x faces, outside the slab: an infinite distance, so no box counts
+    assert _margin1((-1, 2, 0.5), (1, 0, 0)) == np.inf
+    assert _margin1((-1, 0.5, -3), (1, 0, -0.0)) == np.inf
+
+
+def test_key_margin_grazing_a_face():
+    # o = (-1, 0.5, 1 - a), d = (1, 0, b) enters through x = 0 at t = 1 and leaves
+    # through z = 1 at t = a / b; for a / b slightly above 1 the gap is a / b - 1
+    for a, b in ((0.5, 0.49), (0.25, 0.2499), (0.5, 0.5 - 2.0 ** -20)):
+        a32, b32 = float(np.float32(a)), float(np.float32(b))
+        o, d = (-1.0, 0.5, float(np.float32(1.0 - a32))), (1.0, 0.0, b32)
+        exact = _exact_gap(o, d, 0.0, np.inf, UNIT_LO[0], UNIT_HI[0])
+        m = _margin1(o, d)
+        assert exact is not None and abs(m - float(exact)) <= 4e-7 * (1 + float(exact)), (a, b, m, float(exact))
+        assert 0 < m < 0.05
+    # the last one is within 1e-6 of the edge: a marginal ray
+    assert _margin1((-1.0, 0.5, 0.5), (1.0, 0.0, 0.5 - 2.0 ** -22)) < 1e-6
+
+
+def test_key_margin_counts_only_the_boxes_that_drive_bits():
+    # box 0 gives gap 0.5; box 2 (touched at a corner) gives 0: it drives a bit
+    # only when the key has at least 3 bits
+    lo = np.array([[0, 0, 0], [5, 5, 5], [1, 1, 1]], np.float32)
+    hi = np.array([[1, 1, 1], [6, 6, 6], [2, 2, 2]], np.float32)
+    o, d = (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0)
+    # box 1 spans t in [6, 7] (gap 1 / 7), box 2 spans [2, 3] (gap 1 / 3)
+    assert abs(_margin1(o, d, lo=lo, hi=hi, k=1) - 0.5) < 1e-7
+    assert abs(_margin1(o, d, lo=lo, hi=hi, k=2) - 1.0 / 7.0) < 1e-7
+    assert abs(_margin1(o, d, lo=lo, hi=hi, k=3) - 1.0 / 7.0) < 1e-7
+    # a ray touching box 2's corner only: margin 0 once box 2 drives a bit
+    o2, d2 = (1.0, 1.0, 3.0), (1.0, 1.0, -1.0)  # box 2: x, y in [0, 1], z in [1, 2]; boxes 0, 1: gaps 1, 1.5
+    assert _margin1(o2, d2, lo=lo, hi=hi, k=3) == 0.0
+    assert _margin1(o2, d2, lo=lo, hi=hi, k=2) > 0.1
+
+
+def _exact_gap(o, d, tmin, tmax, lo, hi):
+    """The relative slab gap in exact rationals; None for a box missed by an infinite distance."""
+    tn, tf = [Fraction(float(np.float32(tmin)))], []
+    if np.isfinite(tmax):
+        tf.append(Fraction(float(np.float32(tmax))))
+    for a in range(3):
+        oa, da = Fraction(float(np.float32(o[a]))), Fraction(float(np.float32(d[a])))
+        la, ha = Fraction(float(lo[a])), Fraction(float(hi[a]))
+        if da == 0:
+            assert oa != la and oa != ha, "origin on a slab plane: not a case for this pin"
+            if not (la < oa < ha):
+                return None
+            continue
+        ta, tb = (la - oa) / da, (ha - oa) / da
+        tn.append(min(ta, tb))
+        tf.append(max(ta, tb))
+    if not tf:
+        return None
+    near, far = max(tn), min(tf)
+    return abs(far - near) / max(Fraction(1), abs(near), abs(far))
+
+
+def test_key_margin_matches_exact_rationals():
+    rng = np.random.default_rng(11)
+    n, C = 300, 12
+    c = rng.uniform(0, 1, (C, 3))
+    e = rng.uniform(0.02, 0.5, (C, 3))
+    lo = (c - e).astype(np.float32)
+    hi = (c + e).astype(np.float32)
+    org = np.concatenate([rng.uniform(-0.5, 1.5, (n, 3)), rng.uniform(0, 0.3, (n, 1))], 1).astype(np.float32)
+    d = rng.normal(size=(n, 3)) * rng.choice([1e-3, 1.0, 30.0], size=(n, 1))
+    d[rng.uniform(size=(n, 3)) < 0.07] = 0.0  # some zero direction components
+    tmax = np.where(rng.uniform(size=(n, 1)) < 0.5, np.inf, rng.uniform(0.2, 4.0, (n, 1)))
+    dir_ = np.concatenate([d, tmax], 1).astype(np.float32)
+    for k in (1, 5, 12, 32):
+        m = oracle.key_margin(org, dir_, lo, hi, k)
+        for i in range(n):
+            gaps = [g for r in range(min(C, k))
+                    if (g := _exact_gap(org[i, :3], dir_[i, :3], org[i, 3], dir_[i, 3], lo[r], hi[r])) is not None]
+            if not gaps:
+                assert m[i] == np.inf, (k, i)
+                continue
+            g = float(min(gaps))
+            # three roundings per distance (reciprocal, difference, product): 4e-7 covers them
+            assert abs(m[i] - g) <= 4e-7 * (1 + g), (k, i, m[i], g)
+
+
 # ----------------------------------------------------------- HAD and the cut
 
 @dataclass
