@@ -155,6 +155,23 @@ hcc_status hcc_set_trace_schedule(hcc_ctx *ctx, hcc_trace_schedule schedule);
  * Errors: INVALID_ARG (negative or not finite). */
 hcc_status hcc_set_twopoint_distance(hcc_ctx *ctx, float fraction);
 
+/* Bound on the decoupled look-back wait of this context's sorts (Sec. 4.2.3
+ * sort; the bound is this library's failure detection): a tile that has
+ * read its predecessors' status words status_reads times without finding
+ * their counts gives up, marks the sort aborted (so no other tile waits
+ * long) and hcc_sync reports HCC_ERR_TIMEOUT; the permutation is then
+ * unspecified and the next sort starts afresh.  0 restores the default of
+ * 2^22 reads (with back-off, about a quarter of a second), which a sort
+ * whose blocks all make progress never reaches. */
+hcc_status hcc_set_sort_wait_limit(hcc_ctx *ctx, uint32_t status_reads);
+
+/* Test hook for the bounded wait above (no counterpart in the paper): while
+ * set, tile number `tile` (4096 keys each) of every digit pass of this
+ * context's sorts never publishes its counts, so the tile after it waits
+ * until its limit and the sort reports HCC_ERR_TIMEOUT.  0xFFFFFFFF (the
+ * default) withholds nothing.  Never needed outside tests. */
+hcc_status hcc_test_sort_withhold_tile(hcc_ctx *ctx, uint32_t tile);
+
 /* Wait for all work queued on the context's stream, then read and clear the
  * device error word: STACK_OVERFLOW or TIMEOUT if a kernel reported one
  * since the last hcc_sync, INVALID_ARG if a gather or scatter met an index
@@ -344,15 +361,17 @@ hcc_status hcc_sort(hcc_ctx *ctx, const void *keys, uint32_t key_bits, uint64_t 
  * may imply.  The paper has no counterpart; this is a service of this
  * library.  Same result as hcc_sort (stable ascending sort of ids by the low
  * key_bits bits).  Scratch is a fixed device array owned by the library,
- * sized for n <= HCC_SORT_NOALLOC_MAX_N keys of up to 64 bits (about 11 MiB
- * on every device that loads the library, for the life of the process).
+ * sized for n <= HCC_SORT_NOALLOC_MAX_N keys of up to 64 bits (12 MiB on
+ * every device that loads the library, for the life of the process).
  * Runs on the calling thread's current device; stream (a cudaStream_t,
  * NULL = legacy default stream) must belong to it.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress); make
  * that first call before any stream capture.  All calls share the array:
  * calls whose work overlaps on the GPU race and give wrong results.
  * err_word: optional device uint32 into which bounded-wait failures are
- * OR-ed (HCC_ERR_TIMEOUT's bit 2); it is never cleared by the library.
+ * OR-ed (bit value 2); it is never cleared by the library.  With NULL such
+ * a failure is not reported anywhere (the permutation is then unspecified),
+ * so callers that need to detect it pass a word and read it.
  * Errors (synchronous): INVALID_ARG (n above the maximum, key_bits outside
  * 1..64, NULL/misaligned/overlapping buffers), CUDA.
  */

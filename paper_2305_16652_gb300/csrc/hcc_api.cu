@@ -37,6 +37,7 @@ struct hcc_ctx {
     unsigned long long *d_work = nullptr;      // ... whose second half is the trace's slot counter
     hcc_trace_schedule schedule = HCC_TRACE_AUTO;
     float twopoint_fraction = 0.25f;            // TwoPoint length estimate / largest extent
+    hcc::SortOptions sort_opt;                  // bounded-wait settings of this context's sorts
     std::string last_error;
     DevBuf sort_scratch;
     DevBuf keys, perm;                          // hcc_run
@@ -391,6 +392,22 @@ hcc_status hcc_set_twopoint_distance(hcc_ctx *ctx, float fraction) {
     ctx->twopoint_fraction = fraction;
     for (hcc_ctx *l : ctx->lane)
         if (l) l->twopoint_fraction = fraction;
+    return HCC_OK;
+}
+
+hcc_status hcc_set_sort_wait_limit(hcc_ctx *ctx, uint32_t status_reads) {
+    if (!ctx) return HCC_ERR_INVALID_ARG;
+    ctx->sort_opt.wait_limit = status_reads ? status_reads : hcc::SortOptions().wait_limit;
+    for (hcc_ctx *l : ctx->lane)
+        if (l) l->sort_opt.wait_limit = ctx->sort_opt.wait_limit;
+    return HCC_OK;
+}
+
+hcc_status hcc_test_sort_withhold_tile(hcc_ctx *ctx, uint32_t tile) {
+    if (!ctx) return HCC_ERR_INVALID_ARG;
+    ctx->sort_opt.withhold_tile = tile;
+    for (hcc_ctx *l : ctx->lane)
+        if (l) l->sort_opt.withhold_tile = tile;
     return HCC_OK;
 }
 
@@ -1032,7 +1049,7 @@ hcc_status hcc_sort(hcc_ctx *ctx, const void *keys, uint32_t key_bits, uint64_t 
     DeviceGuard g(ctx->device);
     hcc_status st = ensure(ctx, ctx->sort_scratch, sort_scratch_bytes(n, key_bits), "sort scratch");
     if (st != HCC_OK) return st;
-    cudaError_t e = launch_sort(ctx->stream, keys, key_bits, n, perm, ctx->sort_scratch.p, ctx->d_err);
+    cudaError_t e = launch_sort(ctx->stream, keys, key_bits, n, perm, ctx->sort_scratch.p, ctx->d_err, ctx->sort_opt);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sort launch");
     return HCC_OK;
 }
@@ -1479,6 +1496,11 @@ hcc_status hcc_run_host(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, con
             cudaStreamDestroy(s);
             return fail(ctx, st, "pipeline context");
         }
+    }
+    for (hcc_ctx *l : ctx->lane) {  // the lanes follow the context's settings
+        l->schedule = ctx->schedule;
+        l->twopoint_fraction = ctx->twopoint_fraction;
+        l->sort_opt = ctx->sort_opt;
     }
     hcc_status result = HCC_OK;
     for (uint64_t c0 = 0, c = 0, m = 0; c0 < n && result == HCC_OK; c0 += m, ++c) {

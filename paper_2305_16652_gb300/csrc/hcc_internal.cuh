@@ -126,8 +126,14 @@ cudaError_t launch_key_stats(cudaStream_t s, const void *keys, uint32_t key_bits
 // Radix sort scratch bytes for n keys of key_bits bits.
 size_t sort_scratch_bytes(uint64_t n, uint32_t key_bits);
 
+// Bounded-wait settings of one sort.
+struct SortOptions {
+    uint32_t wait_limit = 1u << 22;        // status reads a tile may wait in the look-back before giving up
+    uint32_t withhold_tile = 0xFFFFFFFFu;  // test hook: this tile never publishes its counts (none by default)
+};
+
 cudaError_t launch_sort(cudaStream_t s, const void *keys, uint32_t key_bits, uint64_t n, uint32_t *perm,
-                        void *scratch, uint32_t *err_word);
+                        void *scratch, uint32_t *err_word, const SortOptions &opt = SortOptions());
 
 cudaError_t launch_gather(cudaStream_t s, const float4 *in_org, const float4 *in_dir, uint64_t in_n,
                           const uint32_t *perm, float4 *out_org, float4 *out_dir, uint64_t n, uint32_t *err);

@@ -8,8 +8,8 @@
 // may imply is not acceptable.  This entry point needs no context and no
 // allocation: its scratch is one fixed-size array in device memory that
 // belongs to this file, sized for HCC_SORT_NOALLOC_MAX_N keys of up to 64
-// bits (about 11 MiB, held by every device that loads the library for as long
-// as the process lives).
+// bits (12 MiB, held by every device that loads the library for as long as
+// the process lives).
 //
 // The array is a __device__ symbol, so host code only knows a stand-in for
 // it; the real device address is looked up with cudaGetSymbolAddress once
@@ -29,7 +29,7 @@ constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)12 << 20;  // >= sort scratch o
 constexpr int MAX_DEVICES = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
-static __device__ uint32_t g_noalloc_err;  // error bits when the caller passes no error word
+static __device__ uint32_t g_noalloc_err;  // sink for error bits when the caller passes no error word (never read)
 
 std::mutex g_mu;
 void *g_scratch_ptr[MAX_DEVICES] = {};

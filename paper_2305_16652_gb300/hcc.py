@@ -79,6 +79,8 @@ def load(path: str = LIB_PATH):
         "hcc_set_stream": [P, P],
         "hcc_set_trace_schedule": [P, i32],
         "hcc_set_twopoint_distance": [P, ctypes.c_float],
+        "hcc_set_sort_wait_limit": [P, u32],
+        "hcc_test_sort_withhold_tile": [P, u32],
         "hcc_reserve": [P, u64, u32],
         "hcc_sync": [P],
         "hcc_bvh_upload": [P, ctypes.POINTER(_BvhDesc), PP],
@@ -238,6 +240,16 @@ def hcc_set_trace_schedule(ctx, schedule="auto"):
 def hcc_set_twopoint_distance(ctx, fraction: float = 0.25):
     """TwoPoint ray-length estimate as a fraction of the largest scene extent."""
     _check(load().hcc_set_twopoint_distance(ctx, fraction), ctx)
+
+
+def hcc_set_sort_wait_limit(ctx, status_reads: int = 0):
+    """Look-back wait bound of the context's sorts (0 = the default 2^22 reads)."""
+    _check(load().hcc_set_sort_wait_limit(ctx, status_reads), ctx)
+
+
+def hcc_test_sort_withhold_tile(ctx, tile: int = 0xFFFFFFFF):
+    """Test hook: tile `tile` of each digit pass never publishes its counts."""
+    _check(load().hcc_test_sort_withhold_tile(ctx, tile), ctx)
 
 
 def hcc_select_cut(ctx, bvh, cut_size: int, lam: float = 0.125):

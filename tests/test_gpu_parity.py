@@ -250,7 +250,7 @@ def _keys(kind, n, k, rng):
     raise ValueError(kind)
 
 
-@pytest.mark.parametrize("n", [0, 1, 2, 31, 32, 33, 4095, 4096, 4097, 65537, 300_001])
+@pytest.mark.parametrize("n", [0, 1, 2, 31, 32, 33, 4095, 4096, 4097, 8193, 12288, 65537, 300_001])
 def test_sort_sizes(ctx, n):
     rng = np.random.default_rng(n)
     for k in (32, 17):
@@ -282,6 +282,28 @@ def test_sort_hcc_keys(ctx, room):
     finally:
         hcc.hcc_cut_destroy(cut)
     assert np.array_equal(gpu_sort(ctx, g, 32), oracle.stable_sort(g))
+
+
+@pytest.mark.parametrize("k", [32, 64])
+@pytest.mark.parametrize("tile", [0, 5])
+def test_sort_bounded_wait_runs_out_and_the_context_recovers(ctx, tile, k):
+    """A tile that never publishes its counts (test hook) makes the next
+    tile's look-back wait run out: hcc_sync reports HCC_ERR_TIMEOUT, every
+    tile returns (the sort ends), and the next sort on the same context is
+    the oracle's stable sort again."""
+    rng = np.random.default_rng(77 + tile + k)
+    n = 300_001  # 74 tiles of 4096 keys
+    keys = _keys("uniform", n, k, rng)
+    try:
+        hcc.hcc_set_sort_wait_limit(ctx, 256)
+        hcc.hcc_test_sort_withhold_tile(ctx, tile)
+        with pytest.raises(hcc.HccError) as ei:
+            gpu_sort(ctx, keys, k)
+        assert ei.value.status == 6  # HCC_ERR_TIMEOUT
+    finally:
+        hcc.hcc_test_sort_withhold_tile(ctx)
+        hcc.hcc_set_sort_wait_limit(ctx, 0)
+    assert np.array_equal(gpu_sort(ctx, keys, k), oracle.stable_sort(keys))
 
 
 # ------------------------------------------------------------------ gather
