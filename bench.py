@@ -52,6 +52,12 @@ OPS_PER_TRI = 45
 # HBM bytes each stage must move per ray (32-bit keys; see the design notes)
 BYTES_ENCODE = 32 + 4
 BYTES_GATHER = 4 + 32 + 32
+# FP32/INT lane operations of the HCC encode: about 20 per cut node that
+# drives a bit (6 bound differences and products, 6 min/max to order and
+# combine the slab ends, the tmin/tmax clamp, the compare and the bit) and
+# about 10 per ray (reciprocal directions, key store): 650 at 32 nodes
+ENCODE_OPS_PER_NODE, ENCODE_OPS_PER_RAY = 20, 10
+LATENCY_STEPS = 200  # step latencies for p50/p99 are taken over at least this many timed steps
 
 
 def sort_bytes_per_key(passes: int, key_bytes: int = 4) -> int:
@@ -216,10 +222,13 @@ def run_ours(args, rank, world, local_rank):
     hits = torch.empty((n, 4), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
+    shapes = {"nosort": (128, hcc.HCC_TRACE_STACK), "sorted": (128, hcc.HCC_TRACE_STACK)}
+
     def step(method, ev=None, fused=True, bvh_h=None, schedule="auto"):
         """One wavefront through the C ABI; ev = 5 events around encode/sort/gather/trace."""
         b = bvh_h or bvh
         hcc.hcc_set_trace_schedule(ctx, schedule)
+        hcc.hcc_set_trace_shape(ctx, *shapes["nosort" if method == "nosort" else "sorted"])
         if ev:
             ev[0].record(stream)
         if method == "nosort":
@@ -267,6 +276,12 @@ def run_ours(args, rank, world, local_rank):
         total_ms = evs[0][0].elapsed_time(evs[-1][4])
         return dict(per=per, stages=stages, total_ms=total_ms, wall_s=wall)
 
+    # the trace shape (threads per block, stack entries) picked by the
+    # autotuner, separately for the unsorted and the HCC-order trace
+    shape_ms = tune_shapes(ctx, bvh, args.layout, org, dir_, keys, perm, hits, cut, K)
+    shapes["nosort"] = min(shape_ms["nosort"], key=shape_ms["nosort"].get)
+    shapes["sorted"] = min(shape_ms["hcc"], key=shape_ms["hcc"].get)
+
     # context for the headline: NoSort, TwoPoint, the split-gather HCC path and
     # the quantised node layout; then the HCC headline
     others = {}
@@ -282,13 +297,17 @@ def run_ours(args, rank, world, local_rank):
                             ms_per_step=round(t_max / len(r["per"]), 3),
                             stages_ms=dict(zip(("encode", "sort", "gather", "trace"),
                                                [round(statistics.mean(x), 4) for x in r["stages"]])))
+    lat_steps = max(LATENCY_STEPS, args.steps)
     with ClockSampler(local_rank) as clk:
         r = timed("hcc", args.steps, args.warmup)
+        # step latency: events around each of at least 200 back-to-back steps
+        # (no host synchronisation inside), after the warm-up above
+        lat = timed("hcc", lat_steps, 0)
     clocks = clk.summary()
     t_max = reduce_max(r["total_ms"], world)
     ms_step = t_max / args.steps
     value = n * world * args.steps / (t_max * 1e3)  # Mrays/s over all ranks
-    per = sorted(r["per"])
+    per = sorted(lat["per"])
     p50 = statistics.median(per)
     p99 = per[min(len(per) - 1, int(round(0.99 * (len(per) - 1))))]
     st = [statistics.mean(x) for x in r["stages"]]
@@ -311,13 +330,20 @@ def run_ours(args, rank, world, local_rank):
     e2e_s = reduce_max(time.perf_counter() - t0, world)
     e2e_value = n * world * e2e_steps / (e2e_s * 1e6)
 
-    # parity of the timed path on a sample (sorted vs unsorted bit-identical)
+    # a short serving leg on the same scene: Poisson arrivals at half the
+    # 4-slot saturation, continuous admission against the unbatched path
+    serving = (serve_leg(local_rank, bvh, cut, h_org, h_dir, K, args.serve_requests_bench)
+               if args.serve_requests_bench else None)
+
+    # parity of the timed path (sorted vs unsorted bit-identical)
     step("hcc")
     hcc.hcc_sync(ctx)
     h_hcc = hits.clone()
+    gpu_keys = keys.cpu().numpy().view(np.uint32).astype(np.uint64)
     step("nosort")
     hcc.hcc_sync(ctx)
     identical = bool(torch.equal(h_hcc, hits))
+    gpu_hits = hcc.hits_to_numpy(h_hcc)
 
     # work counts of the trace (order-independent per ray) for the ALU roofline
     counts = hcc.hcc_trace_counts(ctx, bvh, org, dir_, perm=perm)
@@ -331,9 +357,13 @@ def run_ours(args, rank, world, local_rank):
     achieved = work / (trace_ms * 1e-3) / 1e12
     sort_passes = active_digit_passes(keys, K)
     sb = sort_bytes_per_key(sort_passes)
+    enc_ops = (ENCODE_OPS_PER_NODE * min(C, K) + ENCODE_OPS_PER_RAY) * n
+    enc_tops = enc_ops / (st[0] * 1e-3) / 1e12
     stages = {
-        "encode": dict(ms=round(st[0], 4), bound="hbm", achieved_gbs=round(BYTES_ENCODE * n / (st[0] * 1e6), 1),
-                       frac=round(BYTES_ENCODE * n / (st[0] * 1e6) / hbm, 3)),
+        "encode": dict(ms=round(st[0], 4), bound="alu", ops_per_ray=ENCODE_OPS_PER_NODE * min(C, K) + ENCODE_OPS_PER_RAY,
+                       achieved_tops=round(enc_tops, 3), frac=round(enc_tops / alu_peak, 3),
+                       achieved_gbs=round(BYTES_ENCODE * n / (st[0] * 1e6), 1),
+                       hbm_frac=round(BYTES_ENCODE * n / (st[0] * 1e6) / hbm, 3)),
         "sort": dict(ms=round(st[1], 4), bound="hbm", active_passes=sort_passes, bytes_per_key=sb,
                      achieved_gbs=round(sb * n / (st[1] * 1e6), 1), frac=round(sb * n / (st[1] * 1e6) / hbm, 3)),
         "gather": dict(ms=0.0, fused_into_trace=True, split_kernel_ms=round(g_split, 4), bound="hbm",
@@ -353,10 +383,13 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": w.name + f" ({n} secondary rays), HCC cut {C}, {K}-bit keys, {args.layout} BVH nodes",
                    "bvh_layout": args.layout, "gather": "fused into the trace (rays fetched through the sorted ids)",
                    "trace_schedule": "auto (closest hit: persistent warps with ray replacement)",
+                   "trace_shape": {"hcc": list(shapes["sorted"]), "nosort": list(shapes["nosort"]),
+                                   "searched_ms": {o: {f"{b}x{st}": round(v, 4) for (b, st), v in t.items()}
+                                                   for o, t in shape_ms.items()}},
                    "rays": n, "triangles": int(w.tris.shape[0]), "cut_size": C, "key_bits": K, "lambda": 0.125,
                    "l2": f"inputs larger than L2 ({n * 32 / 1e6:.0f} MB of rays per step)",
                    "parallelism": f"replica per GPU x{world}"},
-        "p50_ms": round(p50, 4), "p99_ms": round(p99, 4),
+        "p50_ms": round(p50, 4), "p99_ms": round(p99, 4), "latency_steps": len(per),
         "stages_ms": {"encode": round(st[0], 4), "sort": round(st[1], 4), "gather": round(st[2], 4),
                       "trace": round(st[3], 4)},
         "methods": {"hcc": {"mrays_s": round(value, 2), "ms_per_step": round(ms_step, 3)}, **others},
@@ -375,38 +408,107 @@ def run_ours(args, rank, world, local_rank):
         "hbm_peak_gbs": hbm, "hbm_peak_source": peak_kind,
         "clocks": clocks,
     }
+    if serving is not None:
+        out["serving"] = serving
     hcc.hcc_cut_destroy(cut)
     hcc.hcc_bvh_destroy(bvh)
     hcc.hcc_destroy(ctx)
-    return out, w
+    return out, w, {"keys": gpu_keys, "hits": gpu_hits}
+
+
+def tune_shapes(ctx, bvh, layout, org, dir_, keys, perm, hits, cut, key_bits, reps=3):
+    """Trace time (ms, median of reps) of every trace shape the autotuner may
+    pick for this BVH, for the unsorted wavefront and in HCC order."""
+    import torch
+    from paper_2305_16652_gb300 import hcc, tune
+    hcc.hcc_encode(ctx, "hcc", bvh, cut, org, dir_, key_bits, keys)
+    hcc.hcc_sort(ctx, keys, key_bits, int(org.shape[0]), perm)
+    hcc.hcc_set_trace_schedule(ctx, "auto")
+    out = {"nosort": {}, "hcc": {}}
+    for shape in tune.shape_candidates([bvh], layout):
+        hcc.hcc_set_trace_shape(ctx, *shape)
+        for name, f in (("nosort", lambda: hcc.hcc_trace(ctx, bvh, org, dir_, hits)),
+                        ("hcc", lambda: hcc.hcc_trace_sorted(ctx, bvh, org, dir_, perm, hits))):
+            ts = []
+            for _ in range(reps + 1):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                f()
+                b.record()
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            out[name][shape] = statistics.median(ts[1:])
+    hcc.hcc_sync(ctx)
+    hcc.hcc_set_trace_shape(ctx, 0, 0)
+    return out
 
 
 # ------------------------------------------------------- oracle (CPU) leg
 
-def oracle_sample(w, sample_n: int, seed: int = 7):
+def oracle_indices(w, sample_n: int, seed: int = 7):
     rng = np.random.default_rng(seed)
-    idx = np.sort(rng.choice(w.rays.n, size=min(sample_n, w.rays.n), replace=False))
+    return np.sort(rng.choice(w.rays.n, size=min(sample_n, w.rays.n), replace=False))
+
+
+def oracle_sample(w, sample_n: int, seed: int = 7):
+    idx = oracle_indices(w, sample_n, seed)
     return w.rays.org[idx].copy(), w.rays.dir[idx].copy()
 
 
 def oracle_step(w, cut_ids, org, dir_, key_bits):
+    """The whole path on the CPU oracle; returns the keys and the hits in input order."""
     import oracle
     keys = oracle.encode_hcc(org, dir_, w.bvh.lo[cut_ids], w.bvh.hi[cut_ids], key_bits)
     perm = oracle.stable_sort(keys)
     so, sd = oracle.gather(org, dir_, perm)
-    oracle.trace_bvh(w.bvh, so, sd)
+    hs = oracle.trace_bvh(w.bvh, so, sd)
+    hits = np.empty_like(hs)
+    hits[perm] = hs
+    return keys, hits
 
 
-def cpu_baseline(w, key_bits, cut_size, sample_n):
+def parity_counts(w, cut_ids, org, dir_, idx, keys_o, hits_o, gpu, key_bits):
+    """GPU keys and hits of the sampled rays against the oracle's, with the
+    tolerances of the parity tests: a key may differ only on a ray whose slab
+    margin is below 1e-6; a hit only on a near-edge tie (the oracle's hit
+    within 1e-6 of an edge, t within 1e-5 relative)."""
+    import oracle
+    lo, hi = w.bvh.lo[cut_ids], w.bvh.hi[cut_ids]
+    kg = gpu["keys"][idx]
+    kbad = np.nonzero(kg != keys_o)[0]
+    kmarg = oracle.key_margin(org[kbad], dir_[kbad], lo, hi, key_bits) if len(kbad) else np.zeros(0)
+    marginal_rays = int(np.sum(oracle.key_margin(org, dir_, lo, hi, key_bits) < 1e-6))
+    hg = gpu["hits"][idx]
+    gi, oi = hg.view(np.int32).reshape(-1, 4), hits_o.view(np.int32).reshape(-1, 4)
+    hbad = np.nonzero(np.any(gi != oi, axis=1))[0]
+    ties = 0
+    for i in hbad:
+        g, o = hg[i], hits_o[i]
+        gh, oh = int(g["prim"]) >= 0, int(o["prim"]) >= 0
+        ref = o if oh else g
+        margin = min(float(ref["u"]), float(ref["v"]), 1.0 - float(ref["u"]) - float(ref["v"]))
+        same_prim = gh and oh and int(g["prim"]) == int(o["prim"])
+        t_ok = (not (gh and oh)) or abs(float(g["t"]) - float(o["t"])) <= 1e-5 * abs(float(o["t"]))
+        ties += int(not same_prim and margin < 1e-6 and t_ok)
+    return {"rays": int(len(idx)), "key_mismatches": int(len(kbad)),
+            "key_mismatches_not_marginal": int(np.sum(kmarg >= 1e-6)), "marginal_rays": marginal_rays,
+            "hit_mismatches": int(len(hbad)), "near_edge_ties": int(ties),
+            "hit_mismatches_not_tolerated": int(len(hbad) - ties)}
+
+
+def cpu_baseline(w, key_bits, cut_size, sample_n, gpu=None):
     import oracle
     cut_ids = oracle.select_cut(w.bvh, cut_size)
-    org, dir_ = oracle_sample(w, sample_n)
+    idx = oracle_indices(w, sample_n)
+    org, dir_ = w.rays.org[idx].copy(), w.rays.dir[idx].copy()
     t0 = time.perf_counter()
-    oracle_step(w, cut_ids, org, dir_, key_bits)
+    keys_o, hits_o = oracle_step(w, cut_ids, org, dir_, key_bits)
     dt = time.perf_counter() - t0
-    return {"value": round(org.shape[0] / dt / 1e6, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{org.shape[0]} seeded random rays of the same wavefront, encode+sort+gather+trace, "
-                      f"single-threaded C++ oracle, {dt:.1f} s"}
+    out = {"value": round(org.shape[0] / dt / 1e6, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{org.shape[0]} seeded random rays of the same wavefront, encode+sort+gather+trace, "
+                     f"single-threaded C++ oracle, {dt:.1f} s"}
+    parity = parity_counts(w, cut_ids, org, dir_, idx, keys_o, hits_o, gpu, key_bits) if gpu else None
+    return out, parity
 
 
 def run_reference(args, rank, world):
@@ -824,6 +926,64 @@ def _serve_run(server, ring, pools, reqs, count, rate=None, outstanding=None):
     return rays / (last - first) / 1e6, lat, hcc.hcc_server_stats_get(server)
 
 
+def _warm_server(srv, reqs, pools, ring, slots, count):
+    """Grow a server's memory pool to the largest request on every slot (so
+    that no timed request waits for the driver to map memory), then run a few
+    requests through it."""
+    import torch
+    from paper_2305_16652_gb300 import hcc
+    big = int(np.argmax(reqs["n"][:count]))
+    s, n, off = int(reqs["scene"][big]), int(reqs["n"][big]), int(reqs["offset"][big])
+    hits_w = [torch.empty((n, 4), dtype=torch.int32).pin_memory() for _ in range(slots)]
+    tickets = [hcc.hcc_server_submit(srv, s, pools[s][0][off:off + n], pools[s][1][off:off + n], h) for h in hits_w]
+    for t in tickets:
+        hcc.hcc_server_wait(srv, t)
+    _serve_run(srv, ring, pools, reqs, min(24, count), outstanding=2 * slots)
+
+
+def _serve_summary(mrays, lat, st, ring):
+    return {"mrays_s": round(mrays, 1), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(float(np.percentile(lat, 99)), 3), "mean_ms": round(float(lat.mean()), 3),
+            "max_in_flight": st["max_in_flight"], "ring_stalls": ring.stalls}
+
+
+def serve_leg(device, bvh, cut, h_org, h_dir, key_bits, count, slots=4, load=0.5, seed=3):
+    """Serving on the headline scene: `count` ray-query requests (64k-4M rays,
+    log-uniform, windows of the wavefront in page-locked host memory) with
+    Poisson arrivals at `load` of the continuous server's closed-loop
+    saturation; p50/p99 latency and Mrays/s of continuous admission (`slots`
+    requests on the GPU) and of the unbatched path (one at a time)."""
+    import torch
+    from paper_2305_16652_gb300 import gen, hcc
+    pools = [(h_org, h_dir)]
+    reqs = gen.serve_requests(seed, count, [int(h_org.shape[0])])
+    ring = _HitRing(torch, 24 << 20)
+
+    def server(k):
+        srv = hcc.hcc_server_create(device, [bvh], [cut], slots=k, method="hcc", key_bits=key_bits)
+        _warm_server(srv, reqs, pools, ring, k, count)
+        return srv
+
+    srv = server(slots)
+    try:
+        sat, lat, st = _serve_run(srv, ring, pools, reqs, count, outstanding=2 * slots)
+    finally:
+        hcc.hcc_server_destroy(srv)
+    mean_rays = float(reqs["n"][:count].mean())
+    rate = load * sat * 1e6 / mean_rays
+    out = {"requests": count, "rays_per_request": f"64k-4M log-uniform (mean {int(mean_rays)})",
+           "saturation": {"slots": slots, **_serve_summary(sat, lat, st, ring)},
+           "load": load, "offered_req_s": round(rate, 1), "offered_mrays_s": round(load * sat, 1)}
+    for name, k in (("continuous", slots), ("unbatched", 1)):
+        srv = server(k)
+        try:
+            m, lat, st = _serve_run(srv, ring, pools, reqs, count, rate=rate)
+        finally:
+            hcc.hcc_server_destroy(srv)
+        out[name] = _serve_summary(m, lat, st, ring)
+    return out
+
+
 def run_serve_sweep(args):
     """Serving loop: Poisson arrivals of ray queries (64k-4M rays, log-uniform)
     against 8 resident rooms of 0.2-4M triangles; per-request HCC encode, sort
@@ -847,25 +1007,13 @@ def run_serve_sweep(args):
     ring = _HitRing(torch, 64 << 20 if not args.quick else 8 << 20)
     key_bits = args.key_bits
 
-    big = int(np.argmax(reqs["n"]))
-
     def server(slots):
         srv = hcc.hcc_server_create(0, bvhs, cuts, slots=slots, method="hcc", key_bits=key_bits)
-        # grow the server's memory pool to the largest request on every slot, so
-        # that no timed request waits for the driver to map new memory
-        s, n, off = int(reqs["scene"][big]), int(reqs["n"][big]), int(reqs["offset"][big])
-        hits_w = [torch.empty((n, 4), dtype=torch.int32).pin_memory() for _ in range(slots)]
-        tickets = [hcc.hcc_server_submit(srv, s, pools[s][0][off:off + n], pools[s][1][off:off + n], h)
-                   for h in hits_w]
-        for t in tickets:
-            hcc.hcc_server_wait(srv, t)
-        _serve_run(srv, ring, pools, reqs, min(24, count), outstanding=2 * slots)
+        _warm_server(srv, reqs, pools, ring, slots, count)
         return srv
 
     def summary(mrays, lat, st):
-        return {"mrays_s": round(mrays, 1), "p50_ms": round(float(np.percentile(lat, 50)), 3),
-                "p99_ms": round(float(np.percentile(lat, 99)), 3), "mean_ms": round(float(lat.mean()), 3),
-                "max_in_flight": st["max_in_flight"], "ring_stalls": ring.stalls}
+        return _serve_summary(mrays, lat, st, ring)
 
     out = {"metric": "serving: ray-query Mrays/s and p50/p99 latency under Poisson load, continuous admission "
                      "vs the unbatched per-request path", "unit": "Mrays/s",
@@ -1025,6 +1173,8 @@ def main(argv=None):
     ap.add_argument("--viewport", choices=["full", "limited"], default="full",
                     help="method study: the 60-degree room view or a 10-degree view of the floor (Sec. 6.3)")
     ap.add_argument("--serve-requests", type=int, default=1000, help="serving: requests per run")
+    ap.add_argument("--serve-requests-bench", type=int, default=300,
+                    help="headline run: requests of its short serving leg (0 = skip)")
     args = ap.parse_args(argv)
     if args.case:
         return profile_case(args.case)
@@ -1053,9 +1203,10 @@ def main(argv=None):
         else:
             from paper_2305_16652_gb300 import build
             build()
-            out, w = run_ours(args, rank, world, local_rank)
+            out, w, gpu = run_ours(args, rank, world, local_rank)
             if rank == 0 and not args.no_cpu_baseline:
-                out["cpu_baseline"] = cpu_baseline(w, args.key_bits, args.cut_size, args.cpu_sample)
+                out["cpu_baseline"], out["parity_sample"] = cpu_baseline(w, args.key_bits, args.cut_size,
+                                                                         args.cpu_sample, gpu)
         if rank == 0 and out is not None:
             print(json.dumps(out), flush=True)
     finally:

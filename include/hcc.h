@@ -88,15 +88,23 @@ typedef struct hcc_bvh_desc {
 } hcc_bvh_desc;
 
 /*
- * n rays on the device as two float4 streams (structure of arrays), each
- * 16-byte aligned: org_tmin[i] = (ox, oy, oz, tmin), dir_tmax[i] =
- * (dx, dy, dz, tmax).  A ray covers the parameter interval [tmin, tmax];
- * tmax = +inf for an unbounded ray.  Directions need not be normalised.
+ * n rays on the device as two float4 streams, each 16-byte aligned:
+ * org_tmin[i] = (ox, oy, oz, tmin), dir_tmax[i] = (dx, dy, dz, tmax).  A ray
+ * covers the parameter interval [tmin, tmax]; tmax = +inf for an unbounded
+ * ray.  Directions need not be normalised.
+ * stride: bytes from ray i to ray i + 1 in each stream, a multiple of 16
+ * (0 means 16).  16 = two packed float4 arrays (structure of arrays); 32
+ * with dir_tmax = org_tmin + 4 = one 32-byte record per ray (origin, then
+ * direction), which a fetch through a permutation reads as one 32-byte
+ * access instead of two 16-byte ones.  Every call that takes rays accepts
+ * any stride; outputs of hcc_gather and hcc_batch_spawn are written with
+ * their own descriptor's stride.
  */
 typedef struct hcc_rays {
     float *org_tmin;
     float *dir_tmax;
     uint64_t n;
+    uint64_t stride;
 } hcc_rays;
 
 /* One hit record (16 bytes): prim = triangle id or -1 for a miss (then t =
@@ -148,6 +156,21 @@ typedef enum hcc_trace_schedule {
 } hcc_trace_schedule;
 
 hcc_status hcc_set_trace_schedule(hcc_ctx *ctx, hcc_trace_schedule schedule);
+
+/*
+ * Shape of the context's closest-hit traces that use ray replacement
+ * (REFILL, and AUTO for closest hit), single wavefronts and batches: threads
+ * per block (64, 128 or 256) and traversal-stack entries per ray (32, 48 or
+ * 64).  The paper fixes neither (its tracer follows Aila & Laine 2009); the
+ * autotuner picks them by measurement.  A ray whose traversal needs more
+ * stack entries than the shape has is reported as HCC_ERR_STACK_OVERFLOW by
+ * hcc_sync (its record is a miss): a binary layout needs at most the BVH's
+ * depth (hcc_bvh_info), the 4-ary layout up to three entries per 4-ary
+ * level.  Results do not depend on the shape otherwise.  (0, 0) restores
+ * the default (128, HCC_TRACE_STACK).  Errors: INVALID_ARG for any other
+ * pair.
+ */
+hcc_status hcc_set_trace_shape(hcc_ctx *ctx, uint32_t block_threads, uint32_t stack_entries);
 
 /* The TwoPoint key's estimated ray length as a fraction of the root box's
  * largest extent (App. B sweeps it; Sec. 5 and the default use 0.25), for

@@ -55,7 +55,7 @@ __device__ __forceinline__ bool meets(const float4 &o, const float4 &d, float ix
 // the general test.
 template <typename K>
 __global__ void __launch_bounds__(ENC_BLOCK) k_encode_hcc(const float4 *__restrict__ org,
-                                                          const float4 *__restrict__ dir, uint64_t n,
+                                                          const float4 *__restrict__ dir, uint64_t n, uint32_t rs,
                                                           const float4 *__restrict__ cut, uint32_t used,
                                                           uint32_t key_bits, K *__restrict__ keys) {
     __shared__ float4 s_lo[MAX_CUT_BITS], s_hi[MAX_CUT_BITS];
@@ -79,8 +79,8 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_hcc(const float4 *__restri
     ordered = __syncthreads_and(ordered);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float4 o = __ldcs(org + i);
-        const float4 d = __ldcs(dir + i);
+        const float4 o = __ldcs(org + i * rs);
+        const float4 d = __ldcs(dir + i * rs);
         const float ix = __frcp_rn(d.x), iy = __frcp_rn(d.y), iz = __frcp_rn(d.z);
         K key = 0;
         if (ordered && isfinite(ix) && isfinite(iy) && isfinite(iz)) {
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_hcc(const float4 *__restri
 // level first in the order o.x o.y o.z t.x t.y t.z, left-justified in k bits.
 template <typename K>
 __global__ void __launch_bounds__(ENC_BLOCK) k_encode_twopoint(const float4 *__restrict__ org,
-                                                               const float4 *__restrict__ dir, uint64_t n,
+                                                               const float4 *__restrict__ dir, uint64_t n, uint32_t rs,
                                                                float lox, float loy, float loz, float ex, float ey,
                                                                float ez, float L, uint32_t key_bits,
                                                                K *__restrict__ keys) {
@@ -122,8 +122,8 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_twopoint(const float4 *__r
     const uint32_t pad = key_bits - 6 * b;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float4 o = __ldcs(org + i);
-        const float4 d = __ldcs(dir + i);
+        const float4 o = __ldcs(org + i * rs);
+        const float4 d = __ldcs(dir + i * rs);
         const float p[6] = {o.x, o.y, o.z, __fmaf_rn(L, d.x, o.x), __fmaf_rn(L, d.y, o.y), __fmaf_rn(L, d.z, o.z)};
         const float lo[3] = {lox, loy, loz}, ext[3] = {ex, ey, ez};
         uint32_t q[6];
@@ -187,13 +187,13 @@ __device__ __forceinline__ void octahedral(const float4 &d, float &u, float &v) 
 // Origin key: 3D Morton code of the origin, floor(k/3) bits per axis,
 // left-justified in k bits.
 template <typename K>
-__global__ void __launch_bounds__(ENC_BLOCK) k_encode_origin(const float4 *__restrict__ org, uint64_t n, float lox,
+__global__ void __launch_bounds__(ENC_BLOCK) k_encode_origin(const float4 *__restrict__ org, uint64_t n, uint32_t rs, float lox,
                                                              float loy, float loz, float ex, float ey, float ez,
                                                              uint32_t key_bits, K *__restrict__ keys) {
     const uint32_t b = key_bits / 3, pad = key_bits - 3 * b;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float4 o = __ldcs(org + i);
+        const float4 o = __ldcs(org + i * rs);
         const uint32_t q[3] = {quantise(o.x, lox, ex, b), quantise(o.y, loy, ey, b), quantise(o.z, loz, ez, b)};
         K key = interleave<K, 3>(q, b);
         if (pad) key <<= pad;
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_origin(const float4 *__res
 // bd = floor(k/6), bo = floor((k - 2 bd)/3), left-justified in k bits.
 template <typename K>
 __global__ void __launch_bounds__(ENC_BLOCK) k_encode_origin_dir(const float4 *__restrict__ org,
-                                                                 const float4 *__restrict__ dir, uint64_t n,
+                                                                 const float4 *__restrict__ dir, uint64_t n, uint32_t rs,
                                                                  float lox, float loy, float loz, float ex,
                                                                  float ey, float ez, uint32_t key_bits,
                                                                  K *__restrict__ keys) {
@@ -214,8 +214,8 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_origin_dir(const float4 *_
     const uint32_t pad = key_bits - (3 * bo + 2 * bd);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float4 o = __ldcs(org + i);
-        const float4 d = __ldcs(dir + i);
+        const float4 o = __ldcs(org + i * rs);
+        const float4 d = __ldcs(dir + i * rs);
         float u, v;
         octahedral(d, u, v);
         const uint32_t qo[3] = {quantise(o.x, lox, ex, bo), quantise(o.y, loy, ey, bo), quantise(o.z, loz, ez, bo)};
@@ -285,7 +285,7 @@ __device__ __forceinline__ K origin_dir_key(const float4 &o, const float4 &d, co
 // sort groups rays by scene, then by key.
 template <typename K, int METHOD>
 __global__ void __launch_bounds__(ENC_BLOCK) k_encode_multi(const float4 *__restrict__ org,
-                                                            const float4 *__restrict__ dir, uint64_t n,
+                                                            const float4 *__restrict__ dir, uint64_t n, uint32_t rs,
                                                             const SceneDesc *__restrict__ scenes,
                                                             const uint64_t *__restrict__ offsets, uint32_t num_scenes,
                                                             uint32_t key_bits, K *__restrict__ keys) {
@@ -293,8 +293,8 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_multi(const float4 *__rest
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const uint32_t s = scene_of(offsets, num_scenes, i);
         const SceneDesc &sc = scenes[s];
-        const float4 o = __ldcs(org + i);
-        const float4 d = __ldcs(dir + i);
+        const float4 o = __ldcs(org + i * rs);
+        const float4 d = __ldcs(dir + i * rs);
         K key = 0;
         if (METHOD == HCC_METHOD_HCC) {
             const float ix = __frcp_rn(d.x), iy = __frcp_rn(d.y), iz = __frcp_rn(d.z);
@@ -333,13 +333,13 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_multi(const float4 *__rest
 
 }  // namespace
 
-cudaError_t launch_encode_multi(cudaStream_t s, int method, const float4 *org, const float4 *dir, uint64_t n,
+cudaError_t launch_encode_multi(cudaStream_t s, int method, const float4 *org, const float4 *dir, uint64_t n, uint32_t rs,
                                 const SceneDesc *scenes, const uint64_t *offsets, uint32_t num_scenes,
                                 uint32_t key_bits, uint32_t total_bits, void *keys) {
     if (n == 0) return cudaSuccess;
     const int grid = encode_grid(n, ENC_BLOCK, 8);
 #define HCC_ENC_MULTI(K, M) \
-    k_encode_multi<K, M><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, scenes, offsets, num_scenes, key_bits, (K *)keys)
+    k_encode_multi<K, M><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, rs, scenes, offsets, num_scenes, key_bits, (K *)keys)
 #define HCC_ENC_MULTI_K(K)                                                      \
     do {                                                                        \
         if (method == HCC_METHOD_HCC)                                           \
@@ -374,28 +374,28 @@ cudaError_t launch_key_stats(cudaStream_t s, const void *keys, uint32_t key_bits
     return cudaGetLastError();
 }
 
-cudaError_t launch_encode_origin(cudaStream_t s, const float4 *org, uint64_t n, const float lo[3], const float ext[3],
+cudaError_t launch_encode_origin(cudaStream_t s, const float4 *org, uint64_t n, uint32_t rs, const float lo[3], const float ext[3],
                                  uint32_t key_bits, void *keys) {
     if (n == 0) return cudaSuccess;
     const int grid = encode_grid(n, ENC_BLOCK, 8);
     if (key_bits <= 32)
-        k_encode_origin<uint32_t><<<grid, ENC_BLOCK, 0, s>>>(org, n, lo[0], lo[1], lo[2], ext[0], ext[1], ext[2],
+        k_encode_origin<uint32_t><<<grid, ENC_BLOCK, 0, s>>>(org, n, rs, lo[0], lo[1], lo[2], ext[0], ext[1], ext[2],
                                                              key_bits, (uint32_t *)keys);
     else
-        k_encode_origin<uint64_t><<<grid, ENC_BLOCK, 0, s>>>(org, n, lo[0], lo[1], lo[2], ext[0], ext[1], ext[2],
+        k_encode_origin<uint64_t><<<grid, ENC_BLOCK, 0, s>>>(org, n, rs, lo[0], lo[1], lo[2], ext[0], ext[1], ext[2],
                                                              key_bits, (uint64_t *)keys);
     return cudaGetLastError();
 }
 
-cudaError_t launch_encode_origin_dir(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n,
+cudaError_t launch_encode_origin_dir(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n, uint32_t rs,
                                      const float lo[3], const float ext[3], uint32_t key_bits, void *keys) {
     if (n == 0) return cudaSuccess;
     const int grid = encode_grid(n, ENC_BLOCK, 8);
     if (key_bits <= 32)
-        k_encode_origin_dir<uint32_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, lo[0], lo[1], lo[2], ext[0], ext[1],
+        k_encode_origin_dir<uint32_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, rs, lo[0], lo[1], lo[2], ext[0], ext[1],
                                                                  ext[2], key_bits, (uint32_t *)keys);
     else
-        k_encode_origin_dir<uint64_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, lo[0], lo[1], lo[2], ext[0], ext[1],
+        k_encode_origin_dir<uint64_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, rs, lo[0], lo[1], lo[2], ext[0], ext[1],
                                                                  ext[2], key_bits, (uint64_t *)keys);
     return cudaGetLastError();
 }
@@ -408,7 +408,7 @@ namespace {
 // top boxes first, then the low boxes row by row.
 template <typename K>
 __global__ void __launch_bounds__(ENC_BLOCK) k_encode_mlhcc(const float4 *__restrict__ org,
-                                                            const float4 *__restrict__ dir, uint64_t n,
+                                                            const float4 *__restrict__ dir, uint64_t n, uint32_t rs,
                                                             const float4 *__restrict__ top, uint32_t ntop,
                                                             uint32_t top_field, const float4 *__restrict__ low,
                                                             uint32_t low_field, uint32_t key_bits,
@@ -433,8 +433,8 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_mlhcc(const float4 *__rest
     ordered = __syncthreads_and(ordered);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float4 o = __ldcs(org + i);
-        const float4 d = __ldcs(dir + i);
+        const float4 o = __ldcs(org + i * rs);
+        const float4 d = __ldcs(dir + i * rs);
         const float ix = __frcp_rn(d.x), iy = __frcp_rn(d.y), iz = __frcp_rn(d.z);
         // the slab test of box q: (near, far) pairs selected by the direction
         // signs and packed arithmetic when that is exact (see k_encode_hcc),
@@ -498,14 +498,14 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_mlhcc(const float4 *__rest
 // suffice).
 template <typename K>
 __global__ void __launch_bounds__(ENC_BLOCK) k_encode_ppc(const float4 *__restrict__ org,
-                                                          const float4 *__restrict__ dir, uint64_t n,
+                                                          const float4 *__restrict__ dir, uint64_t n, uint32_t rs,
                                                           const float4 *__restrict__ nodes, uint32_t root_ref,
                                                           float4 root_lo, float4 root_hi, uint32_t key_bits,
                                                           K *__restrict__ keys) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float4 o = __ldcs(org + i);
-        const float4 d = __ldcs(dir + i);
+        const float4 o = __ldcs(org + i * rs);
+        const float4 d = __ldcs(dir + i * rs);
         const float ix = __frcp_rn(d.x), iy = __frcp_rn(d.y), iz = __frcp_rn(d.z);
         K key = 0;
         uint32_t m = 0;  // tests made
@@ -552,7 +552,7 @@ __global__ void __launch_bounds__(ENC_BLOCK) k_encode_ppc(const float4 *__restri
 
 }  // namespace
 
-cudaError_t launch_encode_mlhcc(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n,
+cudaError_t launch_encode_mlhcc(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n, uint32_t rs,
                                 const float4 *top, uint32_t ntop, uint32_t top_field, const float4 *low,
                                 uint32_t low_field, uint32_t key_bits, void *keys) {
     if (n == 0) return cudaSuccess;
@@ -564,18 +564,18 @@ cudaError_t launch_encode_mlhcc(cudaStream_t s, const float4 *org, const float4 
     if (key_bits <= 32) {
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(k_encode_mlhcc<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_encode_mlhcc<uint32_t><<<grid, ENC_BLOCK, smem, s>>>(org, dir, n, top, ntop, top_field, low, low_field,
+        k_encode_mlhcc<uint32_t><<<grid, ENC_BLOCK, smem, s>>>(org, dir, n, rs, top, ntop, top_field, low, low_field,
                                                               key_bits, (uint32_t *)keys);
     } else {
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(k_encode_mlhcc<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_encode_mlhcc<uint64_t><<<grid, ENC_BLOCK, smem, s>>>(org, dir, n, top, ntop, top_field, low, low_field,
+        k_encode_mlhcc<uint64_t><<<grid, ENC_BLOCK, smem, s>>>(org, dir, n, rs, top, ntop, top_field, low, low_field,
                                                               key_bits, (uint64_t *)keys);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_encode_ppc(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n, const uint4 *nodes,
+cudaError_t launch_encode_ppc(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n, uint32_t rs, const uint4 *nodes,
                               uint32_t root_ref, const float root_lo[3], const float root_hi[3], uint32_t key_bits,
                               void *keys) {
     if (n == 0) return cudaSuccess;
@@ -585,35 +585,35 @@ cudaError_t launch_encode_ppc(cudaStream_t s, const float4 *org, const float4 *d
     const float4 *f = reinterpret_cast<const float4 *>(nodes);
     const int grid = encode_grid(n, ENC_BLOCK, 8);
     if (key_bits <= 32)
-        k_encode_ppc<uint32_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, f, root_ref, lo, hi, key_bits,
+        k_encode_ppc<uint32_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, rs, f, root_ref, lo, hi, key_bits,
                                                           (uint32_t *)keys);
     else
-        k_encode_ppc<uint64_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, f, root_ref, lo, hi, key_bits,
+        k_encode_ppc<uint64_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, rs, f, root_ref, lo, hi, key_bits,
                                                           (uint64_t *)keys);
     return cudaGetLastError();
 }
 
-cudaError_t launch_encode_hcc(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n,
+cudaError_t launch_encode_hcc(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n, uint32_t rs,
                               const float4 *cut_boxes, uint32_t used, uint32_t key_bits, void *keys) {
     if (n == 0) return cudaSuccess;
     if (used > MAX_CUT_BITS) used = MAX_CUT_BITS;
     const int grid = encode_grid(n, ENC_BLOCK, 8);
     if (key_bits <= 32)
-        k_encode_hcc<uint32_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, cut_boxes, used, key_bits, (uint32_t *)keys);
+        k_encode_hcc<uint32_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, rs, cut_boxes, used, key_bits, (uint32_t *)keys);
     else
-        k_encode_hcc<uint64_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, cut_boxes, used, key_bits, (uint64_t *)keys);
+        k_encode_hcc<uint64_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, rs, cut_boxes, used, key_bits, (uint64_t *)keys);
     return cudaGetLastError();
 }
 
-cudaError_t launch_encode_twopoint(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n,
+cudaError_t launch_encode_twopoint(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n, uint32_t rs,
                                    const float lo[3], const float ext[3], float L, uint32_t key_bits, void *keys) {
     if (n == 0) return cudaSuccess;
     const int grid = encode_grid(n, ENC_BLOCK, 8);
     if (key_bits <= 32)
-        k_encode_twopoint<uint32_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, lo[0], lo[1], lo[2], ext[0], ext[1],
+        k_encode_twopoint<uint32_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, rs, lo[0], lo[1], lo[2], ext[0], ext[1],
                                                                ext[2], L, key_bits, (uint32_t *)keys);
     else
-        k_encode_twopoint<uint64_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, lo[0], lo[1], lo[2], ext[0], ext[1],
+        k_encode_twopoint<uint64_t><<<grid, ENC_BLOCK, 0, s>>>(org, dir, n, rs, lo[0], lo[1], lo[2], ext[0], ext[1],
                                                                ext[2], L, key_bits, (uint64_t *)keys);
     return cudaGetLastError();
 }

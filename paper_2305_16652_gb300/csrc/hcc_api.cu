@@ -38,6 +38,7 @@ struct hcc_ctx {
     hcc_trace_schedule schedule = HCC_TRACE_AUTO;
     float twopoint_fraction = 0.25f;            // TwoPoint length estimate / largest extent
     hcc::SortOptions sort_opt;                  // bounded-wait settings of this context's sorts
+    uint32_t trace_block = 128, trace_stack = HCC_TRACE_STACK;  // shape of the closest-hit persistent trace
     std::string last_error;
     DevBuf sort_scratch;
     DevBuf keys, perm;                          // hcc_run
@@ -153,12 +154,21 @@ bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) %
 
 hcc_status check_rays(hcc_ctx *ctx, const hcc_rays *r, const char *name) {
     if (!r) return fail(ctx, HCC_ERR_INVALID_ARG, "%s is NULL", name);
+    if (r->stride % 16 != 0 || r->stride > (1u << 20))
+        return fail(ctx, HCC_ERR_INVALID_ARG, "%s: the stride must be a multiple of 16 bytes (at most 2^20)", name);
     if (r->n == 0) return HCC_OK;
     if (!r->org_tmin || !r->dir_tmax) return fail(ctx, HCC_ERR_INVALID_ARG, "%s has a NULL stream", name);
     if (!aligned(r->org_tmin, 16) || !aligned(r->dir_tmax, 16))
         return fail(ctx, HCC_ERR_INVALID_ARG, "%s streams must be 16-byte aligned", name);
     if (r->n > (uint64_t)0xFFFFFFFFu) return fail(ctx, HCC_ERR_INVALID_ARG, "%s: n above 2^32-1", name);
     return HCC_OK;
+}
+
+// Stride of a ray descriptor in float4 units (0 bytes: packed arrays).
+uint32_t ray_rs(const hcc_rays *r) { return r->stride ? (uint32_t)(r->stride / 16) : 1u; }
+// One 32-byte record per ray: direction right after the origin, 32-byte aligned.
+bool ray_rec(const hcc_rays *r) {
+    return ray_rs(r) == 2 && r->dir_tmax == r->org_tmin + 4 && aligned(r->org_tmin, 32);
 }
 
 // ------------------------------------------------------ node quantisation
@@ -392,6 +402,25 @@ hcc_status hcc_set_twopoint_distance(hcc_ctx *ctx, float fraction) {
     ctx->twopoint_fraction = fraction;
     for (hcc_ctx *l : ctx->lane)
         if (l) l->twopoint_fraction = fraction;
+    return HCC_OK;
+}
+
+hcc_status hcc_set_trace_shape(hcc_ctx *ctx, uint32_t block_threads, uint32_t stack_entries) {
+    if (!ctx) return HCC_ERR_INVALID_ARG;
+    if (block_threads == 0 && stack_entries == 0) {
+        block_threads = 128;
+        stack_entries = HCC_TRACE_STACK;
+    }
+    if (!hcc::trace_shape_supported(block_threads, stack_entries))
+        return fail(ctx, HCC_ERR_INVALID_ARG, "unsupported trace shape %u threads x %u stack entries", block_threads,
+                    stack_entries);
+    ctx->trace_block = block_threads;
+    ctx->trace_stack = stack_entries;
+    for (hcc_ctx *l : ctx->lane)
+        if (l) {
+            l->trace_block = block_threads;
+            l->trace_stack = stack_entries;
+        }
     return HCC_OK;
 }
 
@@ -977,15 +1006,16 @@ hcc_status hcc_encode(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const
     DeviceGuard g(ctx->device);
     const float4 *o = reinterpret_cast<const float4 *>(rays->org_tmin);
     const float4 *d = reinterpret_cast<const float4 *>(rays->dir_tmax);
+    const uint32_t rs = ray_rs(rays);
     cudaError_t e;
     if (method == HCC_METHOD_HCC) {
         const uint32_t used = std::min<uint32_t>(cut->on_device, key_bits);
-        e = launch_encode_hcc(ctx->stream, o, d, rays->n, cut->d_boxes, used, key_bits, keys);
+        e = launch_encode_hcc(ctx->stream, o, d, rays->n, rs, cut->d_boxes, used, key_bits, keys);
     } else if (method == HCC_METHOD_MLHCC) {
-        e = launch_encode_mlhcc(ctx->stream, o, d, rays->n, cut->d_boxes, cut->on_device, cut->top_field, cut->d_low,
+        e = launch_encode_mlhcc(ctx->stream, o, d, rays->n, rs, cut->d_boxes, cut->on_device, cut->top_field, cut->d_low,
                                 cut->low_field, key_bits, keys);
     } else if (method == HCC_METHOD_PPC) {
-        e = launch_encode_ppc(ctx->stream, o, d, rays->n, bvh->d_nodes, bvh->root_ref, &bvh->lo[0], &bvh->hi[0],
+        e = launch_encode_ppc(ctx->stream, o, d, rays->n, rs, bvh->d_nodes, bvh->root_ref, &bvh->lo[0], &bvh->hi[0],
                               key_bits, keys);
     } else {
         float lo[3], ext[3];
@@ -995,11 +1025,11 @@ hcc_status hcc_encode(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, const
         }
         if (method == HCC_METHOD_TWOPOINT) {
             const float L = ctx->twopoint_fraction * std::max(ext[0], std::max(ext[1], ext[2]));
-            e = launch_encode_twopoint(ctx->stream, o, d, rays->n, lo, ext, L, key_bits, keys);
+            e = launch_encode_twopoint(ctx->stream, o, d, rays->n, rs, lo, ext, L, key_bits, keys);
         } else if (method == HCC_METHOD_ORIGIN) {
-            e = launch_encode_origin(ctx->stream, o, rays->n, lo, ext, key_bits, keys);
+            e = launch_encode_origin(ctx->stream, o, rays->n, rs, lo, ext, key_bits, keys);
         } else {
-            e = launch_encode_origin_dir(ctx->stream, o, d, rays->n, lo, ext, key_bits, keys);
+            e = launch_encode_origin_dir(ctx->stream, o, d, rays->n, rs, lo, ext, key_bits, keys);
         }
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "encode launch");
@@ -1066,9 +1096,9 @@ hcc_status hcc_gather(hcc_ctx *ctx, const hcc_rays *in, const uint32_t *perm, co
     if (in->n == 0) return fail(ctx, HCC_ERR_INVALID_ARG, "gather from an empty ray set");
     DeviceGuard g(ctx->device);
     cudaError_t e = launch_gather(ctx->stream, reinterpret_cast<const float4 *>(in->org_tmin),
-                                  reinterpret_cast<const float4 *>(in->dir_tmax), in->n, perm,
+                                  reinterpret_cast<const float4 *>(in->dir_tmax), ray_rs(in), in->n, perm,
                                   reinterpret_cast<float4 *>(out->org_tmin), reinterpret_cast<float4 *>(out->dir_tmax),
-                                  out->n, ctx->d_err);
+                                  ray_rs(out), out->n, ctx->d_err);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "gather launch");
     return HCC_OK;
 }
@@ -1092,12 +1122,16 @@ hcc_status hcc_trace(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *rays, int
     a.root_ref = bvh->root_ref;
     a.org = reinterpret_cast<const float4 *>(rays->org_tmin);
     a.dir = reinterpret_cast<const float4 *>(rays->dir_tmax);
+    a.rs = ray_rs(rays);
+    a.rec = ray_rec(rays);
     a.n = rays->n;
     a.gather = nullptr;
     a.scatter = scatter;
     a.hits = reinterpret_cast<int4 *>(hits);
     a.err = ctx->d_err;
     a.work = trace_work(ctx, any_hit);
+    a.block = (int)ctx->trace_block;
+    a.stack = (int)ctx->trace_stack;
     a.counts = nullptr;
     a.scenes = nullptr;
     a.offsets = nullptr;
@@ -1124,12 +1158,16 @@ hcc_status hcc_trace_sorted(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *ra
     a.root_ref = bvh->root_ref;
     a.org = reinterpret_cast<const float4 *>(rays->org_tmin);
     a.dir = reinterpret_cast<const float4 *>(rays->dir_tmax);
+    a.rs = ray_rs(rays);
+    a.rec = ray_rec(rays);
     a.n = rays->n;
     a.gather = perm;
     a.scatter = perm;
     a.hits = reinterpret_cast<int4 *>(hits);
     a.err = ctx->d_err;
     a.work = trace_work(ctx, any_hit);
+    a.block = (int)ctx->trace_block;
+    a.stack = (int)ctx->trace_stack;
     a.counts = nullptr;
     a.scenes = nullptr;
     a.offsets = nullptr;
@@ -1161,12 +1199,16 @@ hcc_status hcc_trace_counts(hcc_ctx *ctx, const hcc_bvh *bvh, const hcc_rays *ra
     a.root_ref = bvh->root_ref;
     a.org = reinterpret_cast<const float4 *>(rays->org_tmin);
     a.dir = reinterpret_cast<const float4 *>(rays->dir_tmax);
+    a.rs = ray_rs(rays);
+    a.rec = ray_rec(rays);
     a.n = rays->n;
     a.gather = perm;
     a.scatter = perm;
     a.hits = reinterpret_cast<int4 *>(tmp.p);
     a.err = ctx->d_err;
     a.work = trace_work(ctx, any_hit);
+    a.block = (int)ctx->trace_block;
+    a.stack = (int)ctx->trace_stack;
     a.counts = cnt;
     a.scenes = nullptr;
     a.offsets = nullptr;
@@ -1275,10 +1317,14 @@ hcc_status hcc_batch_run(hcc_ctx *ctx, const hcc_batch *b, hcc_method method, co
     a.layout = b->layout;
     a.org = reinterpret_cast<const float4 *>(rays->org_tmin);
     a.dir = reinterpret_cast<const float4 *>(rays->dir_tmax);
+    a.rs = ray_rs(rays);
+    a.rec = ray_rec(rays);
     a.n = n;
     a.hits = reinterpret_cast<int4 *>(hits);
     a.err = ctx->d_err;
     a.work = trace_work(ctx, any_hit);
+    a.block = (int)ctx->trace_block;
+    a.stack = (int)ctx->trace_stack;
     a.scenes = b->d_scenes;
     a.offsets = b->d_offsets;
     a.num_scenes = b->num_scenes;
@@ -1287,8 +1333,8 @@ hcc_status hcc_batch_run(hcc_ctx *ctx, const hcc_batch *b, hcc_method method, co
         const size_t ksz = total_bits > 32 ? 8 : 4;
         if ((st = ensure(ctx, ctx->keys, n * ksz, "keys")) != HCC_OK) return st;
         if ((st = ensure(ctx, ctx->perm, n * 4, "perm")) != HCC_OK) return st;
-        e = launch_encode_multi(ctx->stream, (int)method, a.org, a.dir, n, b->d_scenes, b->d_offsets, b->num_scenes,
-                                key_bits, total_bits, ctx->keys.p);
+        e = launch_encode_multi(ctx->stream, (int)method, a.org, a.dir, n, a.rs, b->d_scenes, b->d_offsets,
+                                b->num_scenes, key_bits, total_bits, ctx->keys.p);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "batch encode launch");
         uint32_t *perm = static_cast<uint32_t *>(ctx->perm.p);
         if ((st = hcc_sort(ctx, ctx->keys.p, total_bits, n, perm)) != HCC_OK) return st;
@@ -1314,10 +1360,10 @@ hcc_status hcc_batch_spawn(hcc_ctx *ctx, const hcc_batch *b, const hcc_rays *in,
         return fail(ctx, HCC_ERR_INVALID_ARG, "in and out must be different buffers");
     DeviceGuard g(ctx->device);
     cudaError_t e = launch_spawn(ctx->stream, reinterpret_cast<const float4 *>(in->org_tmin),
-                                 reinterpret_cast<const float4 *>(in->dir_tmax), reinterpret_cast<const int4 *>(hits),
-                                 n, b->d_scenes, b->d_offsets, b->num_scenes, seed, tmin,
-                                 reinterpret_cast<float4 *>(out->org_tmin), reinterpret_cast<float4 *>(out->dir_tmax),
-                                 ctx->d_err);
+                                 reinterpret_cast<const float4 *>(in->dir_tmax), ray_rs(in),
+                                 reinterpret_cast<const int4 *>(hits), n, b->d_scenes, b->d_offsets, b->num_scenes,
+                                 seed, tmin, reinterpret_cast<float4 *>(out->org_tmin),
+                                 reinterpret_cast<float4 *>(out->dir_tmax), ray_rs(out), ctx->d_err);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "spawn launch");
     return HCC_OK;
 }
@@ -1499,6 +1545,8 @@ hcc_status hcc_run_host(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, con
     }
     for (hcc_ctx *l : ctx->lane) {  // the lanes follow the context's settings
         l->schedule = ctx->schedule;
+        l->trace_block = ctx->trace_block;
+        l->trace_stack = ctx->trace_stack;
         l->twopoint_fraction = ctx->twopoint_fraction;
         l->sort_opt = ctx->sort_opt;
     }

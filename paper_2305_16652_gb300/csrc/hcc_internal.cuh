@@ -85,38 +85,38 @@ __device__ __forceinline__ float fmin3(float a, float b, float c) {
 // ------------------------------------------------------------------ launchers
 // All return the launch error (cudaSuccess when queued).
 
-cudaError_t launch_encode_hcc(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n,
+cudaError_t launch_encode_hcc(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n, uint32_t rs,
                               const float4 *cut_boxes, uint32_t used, uint32_t key_bits, void *keys);
 
-cudaError_t launch_encode_twopoint(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n,
+cudaError_t launch_encode_twopoint(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n, uint32_t rs,
                                    const float lo[3], const float ext[3], float L, uint32_t key_bits, void *keys);
 
-cudaError_t launch_encode_origin(cudaStream_t s, const float4 *org, uint64_t n, const float lo[3], const float ext[3],
+cudaError_t launch_encode_origin(cudaStream_t s, const float4 *org, uint64_t n, uint32_t rs, const float lo[3], const float ext[3],
                                  uint32_t key_bits, void *keys);
 
-cudaError_t launch_encode_origin_dir(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n,
+cudaError_t launch_encode_origin_dir(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n, uint32_t rs,
                                      const float lo[3], const float ext[3], uint32_t key_bits, void *keys);
 
 // Multi-level HCC: ntop top boxes (at most top_field), ntop * low_field low
 // boxes (row r = top node r), (lo, hi) float4 pairs.
-cudaError_t launch_encode_mlhcc(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n,
+cudaError_t launch_encode_mlhcc(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n, uint32_t rs,
                                 const float4 *top, uint32_t ntop, uint32_t top_field, const float4 *low,
                                 uint32_t low_field, uint32_t key_bits, void *keys);
 
 // Prefix path code over the exact-layout nodes; root box given separately.
-cudaError_t launch_encode_ppc(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n, const uint4 *nodes,
+cudaError_t launch_encode_ppc(cudaStream_t s, const float4 *org, const float4 *dir, uint64_t n, uint32_t rs, const uint4 *nodes,
                               uint32_t root_ref, const float root_lo[3], const float root_hi[3], uint32_t key_bits,
                               void *keys);
 
 // Batch of scenes: key of ray i = (scene << key_bits) | its key in its scene.
-cudaError_t launch_encode_multi(cudaStream_t s, int method, const float4 *org, const float4 *dir, uint64_t n,
+cudaError_t launch_encode_multi(cudaStream_t s, int method, const float4 *org, const float4 *dir, uint64_t n, uint32_t rs,
                                 const SceneDesc *scenes, const uint64_t *offsets, uint32_t num_scenes,
                                 uint32_t key_bits, uint32_t total_bits, void *keys);
 
 // Next bounce of a batch: diffuse rays from the hit points (see spawn.cu).
-cudaError_t launch_spawn(cudaStream_t s, const float4 *in_org, const float4 *in_dir, const int4 *hits, uint64_t n,
-                         const SceneDesc *scenes, const uint64_t *offsets, uint32_t num_scenes, uint64_t seed,
-                         float tmin, float4 *out_org, float4 *out_dir, uint32_t *err);
+cudaError_t launch_spawn(cudaStream_t s, const float4 *in_org, const float4 *in_dir, uint32_t in_rs, const int4 *hits,
+                         uint64_t n, const SceneDesc *scenes, const uint64_t *offsets, uint32_t num_scenes,
+                         uint64_t seed, float tmin, float4 *out_org, float4 *out_dir, uint32_t out_rs, uint32_t *err);
 
 // cnt[0] += key changes between consecutive sorted positions, cnt[1] += those
 // inside groups of 32 positions (cnt zeroed by the caller).
@@ -135,8 +135,12 @@ struct SortOptions {
 cudaError_t launch_sort(cudaStream_t s, const void *keys, uint32_t key_bits, uint64_t n, uint32_t *perm,
                         void *scratch, uint32_t *err_word, const SortOptions &opt = SortOptions());
 
-cudaError_t launch_gather(cudaStream_t s, const float4 *in_org, const float4 *in_dir, uint64_t in_n,
-                          const uint32_t *perm, float4 *out_org, float4 *out_dir, uint64_t n, uint32_t *err);
+// Ray i of a stream pair is org[i * rs], dir[i * rs] (rs: the stride in
+// float4 units; 1 = two packed float4 arrays, 2 with dir = org + 1 = 32-byte
+// records).
+cudaError_t launch_gather(cudaStream_t s, const float4 *in_org, const float4 *in_dir, uint32_t in_rs, uint64_t in_n,
+                          const uint32_t *perm, float4 *out_org, float4 *out_dir, uint32_t out_rs, uint64_t n,
+                          uint32_t *err);
 
 struct TraceArgs {
     const uint4 *nodes = nullptr;  // 2 (quantised), 4 (exact) or 8 (wide) per node
@@ -145,6 +149,8 @@ struct TraceArgs {
     uint32_t root_ref = 0;
     const float4 *org = nullptr;
     const float4 *dir = nullptr;
+    uint32_t rs = 1;     // ray i is org/dir[i * rs]
+    bool rec = false;    // 32-byte records (rs 2, dir = org + 1, 32-byte aligned): one load per ray
     uint64_t n = 0;
     const uint32_t *gather = nullptr;   // ray j is read from org/dir[gather[j]] (NULL = j)
     const uint32_t *scatter = nullptr;  // its hit goes to hits[scatter[j]] (NULL = j)
@@ -156,8 +162,13 @@ struct TraceArgs {
     const uint64_t *offsets = nullptr;     // scene s owns rays [offsets[s], offsets[s+1])
     uint32_t num_scenes = 0;
     unsigned long long *work = nullptr;    // slot counter of the persistent trace (NULL: one thread per slot)
+    int block = 128;                       // closest-hit persistent trace: threads per block ...
+    int stack = HCC_TRACE_STACK;           // ... and stack entries per ray (a supported shape)
 };
 
 cudaError_t launch_trace(cudaStream_t s, const TraceArgs &a, int any_hit);
+// The block sizes and stack depths of the closest-hit persistent trace: 64,
+// 128 or 256 threads with 32, 48 or 64 stack entries.
+bool trace_shape_supported(uint32_t block, uint32_t stack);
 
 }  // namespace hcc

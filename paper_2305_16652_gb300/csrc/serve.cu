@@ -149,17 +149,17 @@ hcc_status launch_request(hcc_server *s, const Request &r, Slot &sl) {
         uint32_t *perm = static_cast<uint32_t *>(d_perm);
         switch (s->method) {
         case HCC_METHOD_HCC:
-            e = hcc::launch_encode_hcc(st, org, dir, n, s->cut_boxes[r.scene],
+            e = hcc::launch_encode_hcc(st, org, dir, n, 1, s->cut_boxes[r.scene],
                                        std::min(s->cut_used[r.scene], s->key_bits), s->key_bits, d_keys);
             break;
         case HCC_METHOD_TWOPOINT:
-            e = hcc::launch_encode_twopoint(st, org, dir, n, sc.lo, sc.ext, sc.L, s->key_bits, d_keys);
+            e = hcc::launch_encode_twopoint(st, org, dir, n, 1, sc.lo, sc.ext, sc.L, s->key_bits, d_keys);
             break;
         case HCC_METHOD_ORIGIN:
-            e = hcc::launch_encode_origin(st, org, n, sc.lo, sc.ext, s->key_bits, d_keys);
+            e = hcc::launch_encode_origin(st, org, n, 1, sc.lo, sc.ext, s->key_bits, d_keys);
             break;
         default:
-            e = hcc::launch_encode_origin_dir(st, org, dir, n, sc.lo, sc.ext, s->key_bits, d_keys);
+            e = hcc::launch_encode_origin_dir(st, org, dir, n, 1, sc.lo, sc.ext, s->key_bits, d_keys);
             break;
         }
         if (e == cudaSuccess) e = hcc::launch_sort(st, d_keys, s->key_bits, n, perm, d_scratch, sl.d_err);

@@ -10,13 +10,13 @@
 //            ping-pong buffers are chosen so that the first active pass reads
 //            the caller's keys and synthesises ids, and the last one writes
 //            only the permutation
-//   k_pass   per 4096-key tile: warp-level stable ranking (match.any, or a
-//            ballot split when a warp's digits are spread), per-digit tile
-//            counts published to a decoupled look-back chain (bounded
-//            waits), keys reordered in shared memory and written out in runs
-//            of equal digits (coalesced); the last launch writes the
+//   k_pass   one block per 4096-key tile: warp-level stable ranking
+//            (match.any, or a ballot split when a warp's digits are spread),
+//            per-digit tile counts published to a decoupled look-back chain
+//            (bounded waits), keys reordered in shared memory and written out
+//            in runs of equal digits (coalesced); the last launch writes the
 //            identity permutation when no pass is active
-// Tiles take their position from an atomic counter in launch order, so a tile
+// Blocks take their tile from an atomic counter when they start, so a tile
 // only ever waits for tiles that are already running.
 #include <algorithm>
 #include <atomic>
@@ -35,10 +35,12 @@ constexpr int SORT_TILE = SORT_BLOCK * SORT_ITEMS;
 constexpr uint32_t ST_AGG = 1u << 30;  // tile count of this digit available
 constexpr uint32_t ST_INC = 2u << 30;  // inclusive prefix of this digit available
 constexpr uint32_t ST_VALUE = (1u << 30) - 1u;
-constexpr int LOOKBACK = 4;                // predecessors read per look-back round
+#ifndef SORT_LOOKBACK
+#define SORT_LOOKBACK 4
+#endif
+constexpr int LOOKBACK = SORT_LOOKBACK;    // predecessors read per look-back round
 constexpr int MATCH_MAX_DISTINCT = 16;     // distinct digits per warp item below which match.any ranks
 constexpr int HIST_BLOCK = 256;
-constexpr int HIST_WARPS = HIST_BLOCK / 32;
 
 enum : int { KB_USER = 0, KB_A = 1, KB_B = 2, KB_NONE = 3 };
 enum : int { VB_SYNTH = 0, VB_A = 1, VB_PERM = 2 };
@@ -66,17 +68,19 @@ struct Layout {
     size_t header, status, ka, kb, va, total;
 };
 
+// Buffers between passes: for 32-bit keys two ping-pong arrays of (key, id)
+// pairs (8 bytes each); for 64-bit keys two key arrays and one id array (the
+// permutation is the other id buffer).
 Layout layout(uint64_t n, uint32_t key_bits) {
     const uint32_t passes = (key_bits + 7) / 8;
     const uint64_t tiles = (n + SORT_TILE - 1) / SORT_TILE;
-    const size_t ksz = key_bits > 32 ? 8 : 4;
     Layout L;
     L.header = 0;
     L.status = align256(sizeof(SortHeader));
     L.ka = L.status + align256((size_t)passes * tiles * RADIX * sizeof(uint32_t));
-    L.kb = L.ka + align256(n * ksz);
-    L.va = L.kb + align256(n * ksz);
-    L.total = L.va + align256(n * sizeof(uint32_t));
+    L.kb = L.ka + align256(n * 8);
+    L.va = L.kb + align256(n * 8);
+    L.total = L.va + (key_bits > 32 ? align256(n * sizeof(uint32_t)) : 0);
     return L;
 }
 
@@ -164,52 +168,72 @@ __device__ void plan_passes(SortHeader *h, int passes, uint64_t n) {
     }
 }
 
-// One read of all keys: the digit histograms of every pass.  Each warp reads
-// runs of consecutive keys (neighbouring rays have similar keys), merges the
-// lanes with equal digits with match.any and adds each group's size to its
-// own shared-memory counters, so neither warps nor lanes contend.  The
-// block's counters then go to the global histograms, and the last block to
-// finish plans the passes.
+// One read of all keys: the digit histograms of every pass.  Keys of ray
+// batches are heavily skewed (one digit value often holds most keys), so
+// each warp first picks the most common digit of its first 32 keys for each
+// pass and counts that value in a register; every other digit goes to a
+// shared-memory atomic, where collisions are then rare.  The block's counts
+// then go to the global histograms, and the last block to finish plans the
+// passes.
 template <typename K>
 __global__ void __launch_bounds__(HIST_BLOCK) k_hist(const K *__restrict__ keys, uint64_t n, uint32_t key_bits,
                                                      int passes, SortHeader *h) {
-    extern __shared__ uint32_t hsh[];  // [HIST_WARPS][passes][RADIX]
+    __shared__ uint32_t sh[MAX_PASSES * RADIX];
     __shared__ bool s_last;
-    const int per_warp = passes * RADIX;
-    for (int i = threadIdx.x; i < HIST_WARPS * per_warp; i += blockDim.x) hsh[i] = 0;
+    for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) sh[i] = 0;
     __syncthreads();
     const K mask = key_mask<K>(key_bits);
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *wh = hsh + warp * per_warp;
-    constexpr int UNROLL = 4;  // keys per lane in flight
-    const uint64_t gwarp = (uint64_t)blockIdx.x * HIST_WARPS + warp, nwarps = (uint64_t)gridDim.x * HIST_WARPS;
-    for (uint64_t base = gwarp * (32 * UNROLL); base < n; base += nwarps * (32 * UNROLL)) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t first = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // dominant digit per pass among the warp's first keys
+    const K k0 = first < n ? (keys[first] & mask) : (K)0;
+    uint32_t dom[MAX_PASSES], cnt[MAX_PASSES];
+#pragma unroll
+    for (int p = 0; p < MAX_PASSES; ++p) {
+        cnt[p] = 0;
+        dom[p] = 0;
+        if (p < passes) {
+            const uint32_t d = digit_of(k0, (uint32_t)p);
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, first < n ? d : 256u + lane);
+            uint32_t best = ((uint32_t)__popc(peers) << 9) | d;
+            best = __reduce_max_sync(0xFFFFFFFFu, best);
+            dom[p] = best & 511u;
+        }
+    }
+    constexpr int UNROLL = 8;  // independent loads in flight per thread
+    for (uint64_t base = first; base < n; base += UNROLL * stride) {
         K kk[UNROLL];
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) {
-            const uint64_t i = base + (uint64_t)u * 32 + lane;
+            const uint64_t i = base + (uint64_t)u * stride;
             kk[u] = i < n ? (keys[i] & mask) : (K)0;
         }
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) {
-            const bool valid = base + (uint64_t)u * 32 + lane < n;
+            if (base + (uint64_t)u * stride >= n) break;
 #pragma unroll
             for (int p = 0; p < MAX_PASSES; ++p) {
                 if (p < passes) {
                     const uint32_t d = digit_of(kk[u], (uint32_t)p);
-                    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, valid ? d : 256u + lane);
-                    if (valid && (int)lane == top_lane(peers)) wh[p * RADIX + d] += (uint32_t)__popc(peers);
+                    if (d == dom[p])
+                        ++cnt[p];
+                    else
+                        atomicAdd(&sh[p * RADIX + d], 1u);
                 }
             }
         }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < per_warp; i += blockDim.x) {
-        uint32_t c = 0;
 #pragma unroll
-        for (int w = 0; w < HIST_WARPS; ++w) c += hsh[w * per_warp + i];
-        if (c) atomicAdd(&h->hist[0][0] + i, c);
+    for (int p = 0; p < MAX_PASSES; ++p) {
+        if (p < passes) {
+            const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, cnt[p]);
+            if (lane == 0 && c && dom[p] < 256u) atomicAdd(&sh[p * RADIX + dom[p]], c);
+        }
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x)
+        if (sh[i]) atomicAdd(&h->hist[0][0] + i, sh[i]);
     // the last block to finish plans the passes
     __threadfence();
     __syncthreads();
@@ -224,8 +248,9 @@ __global__ void __launch_bounds__(HIST_BLOCK) k_hist(const K *__restrict__ keys,
 template <typename K>
 struct PassArgs {
     const K *user_keys;
-    K *ka, *kb;
-    uint32_t *va, *perm;
+    void *buf_a, *buf_b;  // between passes: (key, id) pairs for 32-bit keys, keys for 64-bit keys
+    uint32_t *va;         // ids between passes (64-bit keys)
+    uint32_t *perm;
     uint32_t *status;
     SortHeader *h;
     uint64_t n;
@@ -235,40 +260,6 @@ struct PassArgs {
     uint32_t withhold_tile;  // test hook: this tile never publishes its counts
     int last_launch;         // the last pass launch writes the identity permutation if no pass is active
 };
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// Copy count elements of T from global src to shared dst with asynchronous
-// copies: 16-byte chunks when the whole tile is present and src is 16-byte
-// aligned, element by element otherwise.  Only elements below count are read.
-template <typename T>
-__device__ __forceinline__ void load_tile_async(T *dst, const T *src, uint32_t count) {
-    if (count == SORT_TILE && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
-        constexpr uint32_t per = 16 / sizeof(T), chunks = SORT_TILE / per;
-#pragma unroll
-        for (uint32_t c = threadIdx.x; c < chunks; c += SORT_BLOCK) cp_async16(dst + c * per, src + c * per);
-    } else {
-        for (uint32_t p = threadIdx.x; p < count; p += SORT_BLOCK) {
-            if (sizeof(T) == 8)
-                cp_async8(dst + p, src + p);
-            else
-                cp_async4(dst + p, src + p);
-        }
-    }
-}
 
 // Stable rank of this thread's items within their digit in the warp's
 // running count: lanes with equal digits found by match.any (or by the
@@ -305,19 +296,20 @@ __device__ __forceinline__ void rank_items(const K (&kreg)[SORT_ITEMS], uint32_t
     }
 }
 
-// One digit pass.  Persistent blocks (three per SM for 32-bit keys, two for
-// 64-bit keys) take tiles of 4096 keys in launch order from an atomic
-// counter; while a tile is ranked and written, the next tile's keys and
-// values stream into the other shared-memory buffer (cp.async), so the DRAM
-// latency of a tile overlaps the work on the previous one.  Per tile: the
-// warp-level stable ranking, the tile's digit counts published at once to
-// the decoupled look-back chain, the tile reordered by digit in shared
-// memory, the look-back for the global offsets (bounded waits with
-// back-off), and runs of equal digits written out coalesced.  A block
-// handles its tiles in increasing order, so the lowest unfinished tile is
-// always being worked on and every wait ends.
+// One digit pass, one block per tile of 4096 keys.  A block takes its tile
+// from an atomic counter when it starts, so tiles are worked on in the order
+// blocks start and a tile's predecessors are already running when it looks
+// back.  Per tile: each thread loads its 16 items (a warp reads 32
+// consecutive elements per item), the warp-level stable ranking, the tile's
+// digit counts published at once to the decoupled look-back chain, the tile
+// reordered by digit in shared memory, the look-back for the global offsets
+// (bounded waits with back-off), and runs of equal digits written out
+// coalesced.  32-bit keys travel between passes as (key, id) pairs, so an
+// element moves with one 8-byte access; 64-bit keys as separate key and id
+// arrays.
 template <typename K>
 __global__ void __launch_bounds__(SORT_BLOCK, sizeof(K) == 4 ? 3 : 2) k_pass(PassArgs<K> a, int pass) {
+    constexpr bool PAIRS = sizeof(K) == 4;
     const PassPlan pl = a.h->plan[pass];
     if (!pl.active) {
         if (a.last_launch && a.h->identity) {  // no active pass: the permutation is the identity
@@ -327,14 +319,16 @@ __global__ void __launch_bounds__(SORT_BLOCK, sizeof(K) == 4 ? 3 : 2) k_pass(Pas
         }
         return;
     }
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    K *in_keys = reinterpret_cast<K *>(smem_raw);                                  // [2][TILE]
-    uint32_t *in_vals = reinterpret_cast<uint32_t *>(in_keys + 2 * SORT_TILE);     // [2][TILE]
+    extern __shared__ __align__(16) unsigned char smem_raw[];     // the tile, reordered
+    uint2 *tp = reinterpret_cast<uint2 *>(smem_raw);              // pairs (32-bit keys), and ...
+    uint32_t *tvs = reinterpret_cast<uint32_t *>(tp + SORT_TILE);  // ... their ids in input order
+    K *tk = reinterpret_cast<K *>(smem_raw);                      // keys (64-bit keys) ...
+    uint32_t *tv = reinterpret_cast<uint32_t *>(tk + SORT_TILE);  // ... and their ids
     // per-warp digit counts of the tile, then each warp's first reorder slot per digit
     __shared__ uint32_t s_wofs[SORT_WARPS][RADIX];
     __shared__ uint32_t s_gofs[RADIX];  // global position of digit d's run minus its first tile slot
     __shared__ uint32_t s_wsum[SORT_WARPS];
-    __shared__ uint32_t s_claim, s_abort;
+    __shared__ uint32_t s_tile, s_abort;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t byte = (uint32_t)pass;
@@ -342,178 +336,168 @@ __global__ void __launch_bounds__(SORT_BLOCK, sizeof(K) == 4 ? 3 : 2) k_pass(Pas
     const bool from_user = pl.src_keys == KB_USER;
     const K mask = key_mask<K>(a.key_bits);
     const uint32_t dbits = a.key_bits - shift < 8u ? a.key_bits - shift : 8u;
-    const K *kin = from_user ? a.user_keys : (pl.src_keys == KB_A ? a.ka : a.kb);
-    const uint32_t *vin = pl.src_vals == VB_A ? a.va : a.perm;
-    const bool synth = pl.src_vals == VB_SYNTH;
-    K *kout = pl.dst_keys == KB_A ? a.ka : (pl.dst_keys == KB_B ? a.kb : nullptr);
-    uint32_t *vout = pl.dst_vals == VB_A ? a.va : a.perm;
+    const void *bin = pl.src_keys == KB_A ? a.buf_a : a.buf_b;
+    void *bout = pl.dst_keys == KB_A ? a.buf_a : (pl.dst_keys == KB_B ? a.buf_b : nullptr);
     const uint32_t wfirst = (uint32_t)warp * (SORT_ITEMS * 32) + lane;  // tile position of this lane's item 0
-    const uint32_t wait_rounds = a.wait_limit / LOOKBACK;
 
-    auto tile_count = [&](uint32_t t) -> uint32_t {
-        const uint64_t b = (uint64_t)t * SORT_TILE;
-        return (uint32_t)((a.n - b) < (uint64_t)SORT_TILE ? (a.n - b) : SORT_TILE);
-    };
-    auto issue = [&](uint32_t t, int buf) {
-        if (t < a.num_tiles) {
-            const uint64_t b = (uint64_t)t * SORT_TILE;
-            const uint32_t cnt = tile_count(t);
-            load_tile_async(in_keys + buf * SORT_TILE, kin + b, cnt);
-            if (!synth) load_tile_async(in_vals + buf * SORT_TILE, vin + b, cnt);
-        }
-        cp_async_commit();
-    };
-
-    for (int i = tid; i < SORT_WARPS * RADIX; i += SORT_BLOCK) (&s_wofs[0][0])[i] = 0;
+#pragma unroll
+    for (int w = 0; w < SORT_WARPS; ++w) s_wofs[w][tid] = 0;
     if (tid == 0) {
-        s_claim = atomicAdd(&a.h->tile_counter[pass], 1u);
+        s_tile = atomicAdd(&a.h->tile_counter[pass], 1u);
         s_abort = 0;
     }
     __syncthreads();
-    uint32_t cur = s_claim;
-    __syncthreads();
-    if (tid == 0) s_claim = atomicAdd(&a.h->tile_counter[pass], 1u);
-    int buf = 0;
-    issue(cur, buf);
-    while (cur < a.num_tiles) {
-        cp_async_wait_all();
-        __syncthreads();  // (1) the tile's data everywhere; the previous tile fully written; s_claim visible
-        const uint32_t nxt = s_claim;
-        issue(nxt, buf ^ 1);  // prefetch the next tile into the other buffer
+    const uint32_t tile = s_tile;
+    if (tile >= a.num_tiles) return;  // uniform; the grid has one block per tile, so this never happens
+    const uint64_t base = (uint64_t)tile * SORT_TILE;
+    const uint32_t tile_n = (uint32_t)((a.n - base) < (uint64_t)SORT_TILE ? (a.n - base) : SORT_TILE);
+    const bool full = tile_n == SORT_TILE;
 
-        const uint32_t tile = cur;
-        const uint64_t base = (uint64_t)tile * SORT_TILE;
-        const uint32_t tile_n = tile_count(tile);
-        K *tk = in_keys + buf * SORT_TILE;  // the tile's keys, then (reordered) its staging area
-        uint32_t *tv = in_vals + buf * SORT_TILE;
-        const bool full = tile_n == SORT_TILE;
-
-        K kreg[SORT_ITEMS];
-        uint32_t vreg[SORT_ITEMS], rank[SORT_ITEMS];
+    K kreg[SORT_ITEMS];
+    uint32_t vreg[SORT_ITEMS], rank[SORT_ITEMS];
 #pragma unroll
-        for (int i = 0; i < SORT_ITEMS; ++i) {
-            const uint32_t pos = wfirst + (uint32_t)i * 32;
-            const bool ok = full || pos < tile_n;
-            const K k = ok ? tk[pos] : (K)0;
-            kreg[i] = from_user ? (K)(k & mask) : k;
-            vreg[i] = synth ? (uint32_t)(base + pos) : (ok ? tv[pos] : 0u);
+    for (int i = 0; i < SORT_ITEMS; ++i) {
+        const uint32_t pos = wfirst + (uint32_t)i * 32;
+        const bool ok = full || pos < tile_n;
+        const uint64_t g = base + pos;
+        if (from_user) {
+            kreg[i] = ok ? (K)(a.user_keys[g] & mask) : (K)0;
+            if (!PAIRS) vreg[i] = (uint32_t)g;
+        } else if (PAIRS) {  // the id waits in shared memory, not in a register, until the reorder
+            const uint2 e = ok ? static_cast<const uint2 *>(bin)[g] : make_uint2(0u, 0u);
+            kreg[i] = (K)e.x;
+            if (ok) tvs[pos] = e.y;
+        } else {
+            kreg[i] = ok ? static_cast<const K *>(bin)[g] : (K)0;
+            vreg[i] = ok ? (pl.src_vals == VB_A ? a.va : a.perm)[g] : 0u;
         }
-        uint32_t *wh = s_wofs[warp];
-        if (full)
-            rank_items<true>(kreg, rank, wh, byte, dbits, wfirst, tile_n);
+    }
+    uint32_t *wh = s_wofs[warp];
+    if (full)
+        rank_items<true>(kreg, rank, wh, byte, dbits, wfirst, tile_n);
+    else
+        rank_items<false>(kreg, rank, wh, byte, dbits, wfirst, tile_n);
+    __syncthreads();  // (1) warp counts complete
+    // thread tid owns digit tid: warp offsets, tile count, publication
+    uint32_t total = 0;  // the counts become each warp's offset within the digit, in place
+#pragma unroll
+    for (int w = 0; w < SORT_WARPS; ++w) {
+        const uint32_t c = s_wofs[w][tid];
+        s_wofs[w][tid] = total;
+        total += c;
+    }
+    uint32_t *st = a.status + ((size_t)pass * a.num_tiles + tile) * RADIX;
+    const bool publish = tile != a.withhold_tile;
+    if (publish) {
+        if (tile == 0)
+            st_relaxed(st + tid, ST_INC | ((a.h->start[pass][tid] + total) & ST_VALUE));
         else
-            rank_items<false>(kreg, rank, wh, byte, dbits, wfirst, tile_n);
-        __syncthreads();  // (2) warp counts complete; every thread has read its items and nxt
-        if (tid == 0) s_claim = atomicAdd(&a.h->tile_counter[pass], 1u);  // the tile after nxt
-        // thread tid owns digit tid: warp offsets, tile count, publication
-        uint32_t wpref[SORT_WARPS];
-        uint32_t total = 0;
+            st_relaxed(st + tid, ST_AGG | total);
+    }
+    uint32_t incl = total;
 #pragma unroll
-        for (int w = 0; w < SORT_WARPS; ++w) {
-            wpref[w] = total;
-            total += s_wofs[w][tid];
-        }
-        uint32_t *st = a.status + ((size_t)pass * a.num_tiles + tile) * RADIX;
-        const bool publish = tile != a.withhold_tile;
-        if (publish) {
-            if (tile == 0)
-                st_relaxed(st + tid, ST_INC | ((a.h->start[pass][tid] + total) & ST_VALUE));
-            else
-                st_relaxed(st + tid, ST_AGG | total);
-        }
-        uint32_t incl = total;
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    if (lane == 31) s_wsum[warp] = incl;
+    __syncthreads();  // (2) per-warp sums of the digit totals
+    uint32_t local = incl - total;
+    for (int w = 0; w < warp; ++w) local += s_wsum[w];
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, off);
-            if (lane >= off) incl += v;
-        }
-        if (lane == 31) s_wsum[warp] = incl;
-        __syncthreads();  // (3) per-warp sums of the digit totals
-        uint32_t local = incl - total;
-        for (int w = 0; w < warp; ++w) local += s_wsum[w];
+    for (int w = 0; w < SORT_WARPS; ++w) s_wofs[w][tid] += local;
+    __syncthreads();  // (3) reorder slots ready
+    // reorder the tile by digit (stable)
 #pragma unroll
-        for (int w = 0; w < SORT_WARPS; ++w) s_wofs[w][tid] = local + wpref[w];
-        __syncthreads();  // (4) reorder slots ready
-        // reorder the tile by digit (stable) into its own buffer
-#pragma unroll
-        for (int i = 0; i < SORT_ITEMS; ++i) {
-            if (full || wfirst + (uint32_t)i * 32 < tile_n) {
-                const uint32_t o = wh[digit_of(kreg[i], byte)] + rank[i];
+    for (int i = 0; i < SORT_ITEMS; ++i) {
+        if (full || wfirst + (uint32_t)i * 32 < tile_n) {
+            const uint32_t o = wh[digit_of(kreg[i], byte)] + rank[i];
+            if (PAIRS) {
+                const uint32_t pos = wfirst + (uint32_t)i * 32;
+                tp[o] = make_uint2((uint32_t)kreg[i], from_user ? (uint32_t)(base + pos) : tvs[pos]);
+            } else {
                 tk[o] = kreg[i];
                 tv[o] = vreg[i];
             }
         }
-        // decoupled look-back for digit tid
-        uint32_t excl;
-        if (tile == 0) {
-            excl = a.h->start[pass][tid];
-        } else {
-            excl = 0;
-            int64_t j = (int64_t)tile - 1;
-            uint32_t spins = 0;
-            bool timed_out = false, done = false;
-            const uint32_t *col = a.status + (size_t)pass * a.num_tiles * RADIX + tid;
-            while (!done) {
-                uint32_t sv[LOOKBACK];
-#pragma unroll
-                for (int w = 0; w < LOOKBACK; ++w)
-                    sv[w] = (j - w >= 0) ? ld_relaxed(col + (size_t)(j - w) * RADIX) : ST_INC;
-                int used = 0;
-                bool stalled = false;
-#pragma unroll
-                for (int w = 0; w < LOOKBACK; ++w) {
-                    if (done || stalled) continue;
-                    const uint32_t flag = sv[w] & ~ST_VALUE;
-                    if (flag == 0) {
-                        stalled = true;
-                        continue;
-                    }
-                    if (j - w >= 0) excl += sv[w] & ST_VALUE;
-                    ++used;
-                    if (flag == ST_INC) done = true;
-                }
-                j -= used;
-                if (done) break;
-                if (stalled) {
-                    if (++spins > wait_rounds || ((spins & 63u) == 0 && ld_relaxed(&a.h->abort))) {
-                        timed_out = true;
-                        break;
-                    }
-                    __nanosleep(spins < 8 ? 32u * spins : 256u);
-                }
-            }
-            if (timed_out) {
-                atomicOr(a.err, ERR_TIMEOUT);
-                atomicExch(&a.h->abort, 1u);
-                s_abort = 1;
-            }
-            if (publish) st_relaxed(st + tid, ST_INC | ((excl + total) & ST_VALUE));
-        }
-        s_gofs[tid] = excl - local;
-        __syncthreads();  // (5) the tile reordered, global offsets ready
-        if (s_abort) break;
-#pragma unroll
-        for (int w = 0; w < SORT_WARPS; ++w) s_wofs[w][tid] = 0;  // counters of the next tile
-        // runs of equal digits to their global positions
-        if (kout) {
-#pragma unroll 4
-            for (uint32_t p = tid; p < tile_n; p += SORT_BLOCK) {
-                const K k = tk[p];
-                const uint32_t g = s_gofs[digit_of(k, byte)] + p;
-                kout[g] = k;
-                vout[g] = tv[p];
-            }
-        } else {
-#pragma unroll 4
-            for (uint32_t p = tid; p < tile_n; p += SORT_BLOCK) {
-                const uint32_t g = s_gofs[digit_of(tk[p], byte)] + p;
-                __stcs(vout + g, tv[p]);
-            }
-        }
-        cur = nxt;
-        buf ^= 1;
     }
-    cp_async_wait_all();
+    // decoupled look-back for digit tid
+    uint32_t excl;
+    if (tile == 0) {
+        excl = a.h->start[pass][tid];
+    } else {
+        excl = 0;
+        int64_t j = (int64_t)tile - 1;
+        uint32_t spins = 0;
+        bool timed_out = false, done = false;
+        const uint32_t wait_rounds = a.wait_limit / LOOKBACK;
+        const uint32_t *col = a.status + (size_t)pass * a.num_tiles * RADIX + tid;
+        while (!done) {
+            uint32_t sv[LOOKBACK];
+#pragma unroll
+            for (int w = 0; w < LOOKBACK; ++w)
+                sv[w] = (j - w >= 0) ? ld_relaxed(col + (size_t)(j - w) * RADIX) : ST_INC;
+            int used = 0;
+            bool stalled = false;
+#pragma unroll
+            for (int w = 0; w < LOOKBACK; ++w) {
+                if (done || stalled) continue;
+                const uint32_t flag = sv[w] & ~ST_VALUE;
+                if (flag == 0) {
+                    stalled = true;
+                    continue;
+                }
+                if (j - w >= 0) excl += sv[w] & ST_VALUE;
+                ++used;
+                if (flag == ST_INC) done = true;
+            }
+            j -= used;
+            if (done) break;
+            if (stalled) {
+                if (++spins > wait_rounds || ((spins & 63u) == 0 && ld_relaxed(&a.h->abort))) {
+                    timed_out = true;
+                    break;
+                }
+                __nanosleep(spins < 8 ? 32u * spins : 256u);
+            }
+        }
+        if (timed_out) {
+            atomicOr(a.err, ERR_TIMEOUT);
+            atomicExch(&a.h->abort, 1u);
+            s_abort = 1;
+        }
+        if (publish) st_relaxed(st + tid, ST_INC | ((excl + total) & ST_VALUE));
+    }
+    s_gofs[tid] = excl - local;
+    __syncthreads();  // (4) the tile reordered, global offsets ready
+    if (s_abort) return;
+    // runs of equal digits to their global positions
+    if (PAIRS) {
+        if (bout) {
+            uint2 *out = static_cast<uint2 *>(bout);
+#pragma unroll 4
+            for (uint32_t p = tid; p < tile_n; p += SORT_BLOCK) {
+                const uint2 e = tp[p];
+                out[s_gofs[digit_of(e.x, byte)] + p] = e;
+            }
+        } else {
+#pragma unroll 4
+            for (uint32_t p = tid; p < tile_n; p += SORT_BLOCK) {
+                const uint2 e = tp[p];
+                a.perm[s_gofs[digit_of(e.x, byte)] + p] = e.y;
+            }
+        }
+    } else {
+        K *kout = static_cast<K *>(bout);
+        uint32_t *vout = pl.dst_vals == VB_A ? a.va : a.perm;
+#pragma unroll 4
+        for (uint32_t p = tid; p < tile_n; p += SORT_BLOCK) {
+            const K k = tk[p];
+            const uint32_t g = s_gofs[digit_of(k, byte)] + p;
+            if (kout) kout[g] = k;
+            vout[g] = tv[p];
+        }
+    }
 }
 
 template <typename K>
@@ -528,28 +512,24 @@ cudaError_t run_sort(cudaStream_t s, const K *keys, uint32_t key_bits, uint64_t 
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    uint64_t hblocks = (n + HIST_BLOCK * 16 - 1) / (HIST_BLOCK * 16);
+    uint64_t hblocks = (n + HIST_BLOCK * 8 - 1) / (HIST_BLOCK * 8);
     const uint64_t hcap = (uint64_t)(sms > 0 ? sms : 1) * 4;
     if (hblocks > hcap) hblocks = hcap;
     if (hblocks == 0) hblocks = 1;
-    const size_t dyn = 2 * (sizeof(K) + sizeof(uint32_t)) * SORT_TILE;  // 2 tile buffers (prefetch, current)
+    const size_t dyn = (sizeof(K) == 4 ? sizeof(uint2) : sizeof(K)) * SORT_TILE + sizeof(uint32_t) * SORT_TILE;
     // the shared-memory opt-in is set once per device (so that a sort can be
     // captured in a CUDA graph without any non-stream call)
     static std::atomic<uint64_t> opted{0};
     if (dev >= 0 && dev < 64 && !(opted.load() & (1ull << dev))) {
         e = cudaFuncSetAttribute(k_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_hist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 HIST_WARPS * MAX_PASSES * RADIX * (int)sizeof(uint32_t));
-        if (e != cudaSuccess) return e;
         opted.fetch_or(1ull << dev);
     }
-    const size_t hdyn = (size_t)HIST_WARPS * passes * RADIX * sizeof(uint32_t);
-    k_hist<K><<<(unsigned)hblocks, HIST_BLOCK, hdyn, s>>>(keys, n, key_bits, passes, h);
+    k_hist<K><<<(unsigned)hblocks, HIST_BLOCK, 0, s>>>(keys, n, key_bits, passes, h);
     PassArgs<K> a;
     a.user_keys = keys;
-    a.ka = reinterpret_cast<K *>(scratch + L.ka);
-    a.kb = reinterpret_cast<K *>(scratch + L.kb);
+    a.buf_a = scratch + L.ka;
+    a.buf_b = scratch + L.kb;
     a.va = reinterpret_cast<uint32_t *>(scratch + L.va);
     a.perm = perm;
     a.status = reinterpret_cast<uint32_t *>(scratch + L.status);
@@ -560,12 +540,9 @@ cudaError_t run_sort(cudaStream_t s, const K *keys, uint32_t key_bits, uint64_t 
     a.err = err;
     a.wait_limit = opt.wait_limit;
     a.withhold_tile = opt.withhold_tile;
-    a.last_launch = 0;
-    const uint32_t per_sm = sizeof(K) == 4 ? 3u : 2u;  // blocks that fit the shared memory
-    const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)(sms > 0 ? sms : 1) * per_sm);
     for (int p = 0; p < passes; ++p) {
         a.last_launch = p == passes - 1;
-        k_pass<K><<<grid, SORT_BLOCK, dyn, s>>>(a, p);
+        k_pass<K><<<tiles, SORT_BLOCK, dyn, s>>>(a, p);
     }
     return cudaGetLastError();
 }

@@ -36,16 +36,16 @@ __device__ __forceinline__ float uniform24(uint64_t seed_mixed, uint64_t i, uint
 }
 
 __global__ void __launch_bounds__(SPAWN_BLOCK) k_spawn(const float4 *__restrict__ in_org,
-                                                       const float4 *__restrict__ in_dir,
+                                                       const float4 *__restrict__ in_dir, uint32_t in_rs,
                                                        const int4 *__restrict__ hits, uint64_t n,
                                                        const SceneDesc *__restrict__ scenes,
                                                        const uint64_t *__restrict__ offsets, uint32_t num_scenes,
                                                        uint64_t seed, float tmin, float4 *__restrict__ out_org,
-                                                       float4 *__restrict__ out_dir, uint32_t *err) {
+                                                       float4 *__restrict__ out_dir, uint32_t out_rs, uint32_t *err) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t sm = mix64(seed);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float4 o = in_org[i], d = in_dir[i];
+        const float4 o = in_org[i * in_rs], d = in_dir[i * in_rs];
         const int4 h = hits[i];
         const int32_t prim = h.x;
         const SceneDesc &sc = scenes[scene_of(offsets, num_scenes, i)];
@@ -53,8 +53,8 @@ __global__ void __launch_bounds__(SPAWN_BLOCK) k_spawn(const float4 *__restrict_
             atomicOr(err, ERR_INDEX);
         }
         if (prim < 0 || (uint32_t)prim >= sc.num_tris) {  // miss: an empty ray
-            out_org[i] = make_float4(o.x, o.y, o.z, 1.0f);
-            out_dir[i] = make_float4(d.x, d.y, d.z, 0.0f);
+            out_org[i * out_rs] = make_float4(o.x, o.y, o.z, 1.0f);
+            out_dir[i * out_rs] = make_float4(d.x, d.y, d.z, 0.0f);
             continue;
         }
         const uint32_t rec = __ldg(sc.prim_rec + prim);
@@ -107,16 +107,16 @@ __global__ void __launch_bounds__(SPAWN_BLOCK) k_spawn(const float4 *__restrict_
         const float wx = __fmaf_rn(z, nx, __fmaf_rn(y, b2x, __fmul_rn(x, b1x)));
         const float wy = __fmaf_rn(z, ny, __fmaf_rn(y, b2y, __fmul_rn(x, b1y)));
         const float wz = __fmaf_rn(z, nz, __fmaf_rn(y, b2z, __fmul_rn(x, b1z)));
-        out_org[i] = make_float4(px, py, pz, tmin);
-        out_dir[i] = make_float4(wx, wy, wz, __int_as_float(0x7F800000));
+        out_org[i * out_rs] = make_float4(px, py, pz, tmin);
+        out_dir[i * out_rs] = make_float4(wx, wy, wz, __int_as_float(0x7F800000));
     }
 }
 
 }  // namespace
 
-cudaError_t launch_spawn(cudaStream_t s, const float4 *in_org, const float4 *in_dir, const int4 *hits, uint64_t n,
-                         const SceneDesc *scenes, const uint64_t *offsets, uint32_t num_scenes, uint64_t seed,
-                         float tmin, float4 *out_org, float4 *out_dir, uint32_t *err) {
+cudaError_t launch_spawn(cudaStream_t s, const float4 *in_org, const float4 *in_dir, uint32_t in_rs, const int4 *hits,
+                         uint64_t n, const SceneDesc *scenes, const uint64_t *offsets, uint32_t num_scenes,
+                         uint64_t seed, float tmin, float4 *out_org, float4 *out_dir, uint32_t out_rs, uint32_t *err) {
     if (n == 0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -124,8 +124,8 @@ cudaError_t launch_spawn(cudaStream_t s, const float4 *in_org, const float4 *in_
     uint64_t blocks = (n + SPAWN_BLOCK - 1) / SPAWN_BLOCK;
     const uint64_t cap = (uint64_t)(sms > 0 ? sms : 1) * 8;
     if (blocks > cap) blocks = cap;
-    k_spawn<<<(unsigned)blocks, SPAWN_BLOCK, 0, s>>>(in_org, in_dir, hits, n, scenes, offsets, num_scenes, seed, tmin,
-                                                     out_org, out_dir, err);
+    k_spawn<<<(unsigned)blocks, SPAWN_BLOCK, 0, s>>>(in_org, in_dir, in_rs, hits, n, scenes, offsets, num_scenes, seed,
+                                                     tmin, out_org, out_dir, out_rs, err);
     return cudaGetLastError();
 }
 

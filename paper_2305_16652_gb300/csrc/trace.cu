@@ -17,6 +17,9 @@
 // a triangle are the same bit patterns on every run and in every ray order.
 #include <algorithm>
 #include <atomic>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "hcc_internal.cuh"
 
@@ -32,10 +35,11 @@ constexpr float PRUNE_SLACK = 1.0f + 1.0f / 65536.0f;
 // order (rays fetched through a permutation), where waiting longer keeps the
 // warp's neighbouring rays together (measured faster for each)
 constexpr uint32_t REFILL_MIN = 12;
-// resident blocks per SM the persistent kernel is built for: binary nodes
-// (48 registers), and wide nodes or a batch of scenes (56)
-constexpr int POOL_BLOCKS = 10;
-constexpr int POOL_BLOCKS_WIDE = 9;
+// resident threads per SM the persistent kernel is built for: binary nodes
+// (48 registers at 128-thread blocks), and wide nodes or a batch of scenes
+// (56); the register cap follows from threads x registers <= 64K
+constexpr int POOL_THREADS = 1280;
+constexpr int POOL_THREADS_WIDE = 1152;
 constexpr uint32_t REFILL_MIN_SORTED = 24;
 
 __device__ __forceinline__ float byte_to_float(uint32_t w, uint32_t sel) {
@@ -256,7 +260,7 @@ __device__ __forceinline__ uint32_t ray_pop(RayState &s, const uint2 *stack) {
 // then test the parked leaf and any leaf that is next on the stack.  The
 // nearer child is visited first and the farther one is pushed with its
 // entry distance, which lets a pop skip subtrees beyond the best hit.
-template <bool ANY, bool COUNT, int LAYOUT>
+template <bool ANY, bool COUNT, int LAYOUT, int STACKN>
 __device__ __forceinline__ void ray_round(RayState &s, uint2 *stack, const uint4 *__restrict__ nodes,
                                           const float4 *__restrict__ tris, Counters &cn) {
     const uint32_t lane = threadIdx.x & 31;
@@ -290,7 +294,7 @@ __device__ __forceinline__ void ray_round(RayState &s, uint2 *stack, const uint4
         if (met == 0) {
             s.node = ray_pop(s, stack);
         } else {
-            if (s.sp + met - 1 > STACK) {
+            if (s.sp + met - 1 > STACKN) {
                 s.overflow = true;
                 s.node = s.leaf = REF_NONE;
                 break;
@@ -323,7 +327,7 @@ __device__ __forceinline__ void ray_round(RayState &s, uint2 *stack, const uint4
         const bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
         if (h0 && h1) {
             const bool first0 = tn0 <= tn1;
-            if (s.sp == STACK) {
+            if (s.sp == STACKN) {
                 s.overflow = true;
                 s.node = s.leaf = REF_NONE;
                 break;
@@ -413,8 +417,14 @@ __device__ __forceinline__ bool fetch_ray(const TraceArgs &a, uint64_t i, float4
             return false;
         }
     }
-    o4 = __ldcs(a.org + src);
-    d4 = __ldcs(a.dir + src);
+    if (a.rec) {  // one 32-byte record: a single access per ray
+        asm volatile("ld.global.cs.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=f"(o4.x), "=f"(o4.y), "=f"(o4.z), "=f"(o4.w), "=f"(d4.x), "=f"(d4.y), "=f"(d4.z), "=f"(d4.w)
+                     : "l"(a.org + 2 * src));
+    } else {
+        o4 = __ldcs(a.org + src * a.rs);
+        d4 = __ldcs(a.dir + src * a.rs);
+    }
     nodes = a.nodes;
     tris = a.tris;
     root = a.root_ref;
@@ -457,7 +467,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
     uint2 stack[STACK];
     Counters cn;
     ray_init(s, o4, d4, root);
-    while (!ray_done(s)) ray_round<ANY, COUNT, LAYOUT>(s, stack, nodes, tris, cn);
+    while (!ray_done(s)) ray_round<ANY, COUNT, LAYOUT, STACK>(s, stack, nodes, tris, cn);
     store_hit(a, i, s);
     add_counts<COUNT>(a, cn);
 }
@@ -470,15 +480,17 @@ __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
 // so lanes of a warp trace neighbouring slots -- in sorted order, rays with
 // equal keys.  Every ray's record is the same as in k_trace: a ray's own
 // traversal does not depend on which rays share its warp, except for which
-// of several hits an any-hit query returns first.
-template <bool ANY, bool COUNT, int LAYOUT, bool MULTI>
-__global__ void __launch_bounds__(TRACE_BLOCK, (LAYOUT == 2 || MULTI) ? POOL_BLOCKS_WIDE : POOL_BLOCKS) k_trace_pool(TraceArgs a) {
+// of several hits an any-hit query returns first.  BLOCK threads per block
+// and STACKN stack entries per ray are a shape the autotuner may pick.
+template <bool ANY, bool COUNT, int LAYOUT, bool MULTI, int BLOCK, int STACKN>
+__global__ void __launch_bounds__(BLOCK, ((LAYOUT == 2 || MULTI) ? POOL_THREADS_WIDE : POOL_THREADS) / BLOCK)
+    k_trace_pool(TraceArgs a) {
     constexpr uint32_t FULL = 0xFFFFFFFFu;
     const uint32_t lane = threadIdx.x & 31;
     uint32_t lt;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
     RayState s;
-    uint2 stack[STACK];
+    uint2 stack[STACKN];
     Counters cn;
     const uint4 *nodes = a.nodes;
     const float4 *tris = a.tris;
@@ -513,7 +525,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK, (LAYOUT == 2 || MULTI) ? POOL_BLO
             continue;
         }
         if (have) {
-            ray_round<ANY, COUNT, LAYOUT>(s, stack, nodes, tris, cn);
+            ray_round<ANY, COUNT, LAYOUT, STACKN>(s, stack, nodes, tris, cn);
             if (ray_done(s)) {
                 store_hit(a, slot, s);
                 have = false;
@@ -525,70 +537,102 @@ __global__ void __launch_bounds__(TRACE_BLOCK, (LAYOUT == 2 || MULTI) ? POOL_BLO
 
 }  // namespace
 
+namespace {
+
+// Resident blocks per SM of one persistent kernel on the current device
+// (queried once per device and kernel).
+int resident_blocks(const void *kernel, int block) {
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<int, const void *>, int>> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto &e : cache)
+        if (e.first.first == dev && e.first.second == kernel) return e.second;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm <= 0) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    cache.push_back({{dev, kernel}, per_sm});
+    return per_sm;
+}
+
+// Persistent grid: every block resident at once.
+template <bool ANY, bool CNT, int LAYOUT, bool MULTI, int BLOCK, int STACKN>
+cudaError_t launch_pool(cudaStream_t s, const TraceArgs &a) {
+    const auto kernel = k_trace_pool<ANY, CNT, LAYOUT, MULTI, BLOCK, STACKN>;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned cap = (unsigned)std::max(1, sms) * (unsigned)resident_blocks((const void *)kernel, BLOCK);
+    const unsigned blocks = (unsigned)std::min<uint64_t>((a.n + BLOCK - 1) / BLOCK, cap);
+    cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    kernel<<<blocks, BLOCK, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// The closest-hit persistent trace in the shape the context asks for; the
+// any-hit and counting variants keep the default shape.
+template <bool ANY, bool CNT, int LAYOUT, bool MULTI>
+cudaError_t launch_pool_shaped(cudaStream_t s, const TraceArgs &a) {
+    if constexpr (ANY || CNT) {
+        return launch_pool<ANY, CNT, LAYOUT, MULTI, TRACE_BLOCK, STACK>(s, a);
+    } else {
+        switch (a.block * 1000 + a.stack) {
+            case 64032: return launch_pool<ANY, CNT, LAYOUT, MULTI, 64, 32>(s, a);
+            case 64048: return launch_pool<ANY, CNT, LAYOUT, MULTI, 64, 48>(s, a);
+            case 64064: return launch_pool<ANY, CNT, LAYOUT, MULTI, 64, 64>(s, a);
+            case 128032: return launch_pool<ANY, CNT, LAYOUT, MULTI, 128, 32>(s, a);
+            case 128048: return launch_pool<ANY, CNT, LAYOUT, MULTI, 128, 48>(s, a);
+            case 256032: return launch_pool<ANY, CNT, LAYOUT, MULTI, 256, 32>(s, a);
+            case 256048: return launch_pool<ANY, CNT, LAYOUT, MULTI, 256, 48>(s, a);
+            case 256064: return launch_pool<ANY, CNT, LAYOUT, MULTI, 256, 64>(s, a);
+            default: return launch_pool<ANY, CNT, LAYOUT, MULTI, TRACE_BLOCK, STACK>(s, a);
+        }
+    }
+}
+
+template <bool ANY, bool CNT, bool MULTI>
+cudaError_t launch_layout(cudaStream_t s, const TraceArgs &a, bool pool) {
+    if (pool) {
+        if (a.layout == 0) return launch_pool_shaped<ANY, CNT, 0, MULTI>(s, a);
+        if (a.layout == 1) return launch_pool_shaped<ANY, CNT, 1, MULTI>(s, a);
+        return launch_pool_shaped<ANY, CNT, 2, MULTI>(s, a);
+    }
+    const unsigned blocks = (unsigned)((a.n + TRACE_BLOCK - 1) / TRACE_BLOCK);
+    if (a.layout == 0)
+        k_trace<ANY, CNT, 0, MULTI><<<blocks, TRACE_BLOCK, 0, s>>>(a);
+    else if (a.layout == 1)
+        k_trace<ANY, CNT, 1, MULTI><<<blocks, TRACE_BLOCK, 0, s>>>(a);
+    else
+        k_trace<ANY, CNT, 2, MULTI><<<blocks, TRACE_BLOCK, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <bool ANY, bool CNT>
+cudaError_t launch_multi(cudaStream_t s, const TraceArgs &a, bool pool) {
+    return a.scenes ? launch_layout<ANY, CNT, true>(s, a, pool) : launch_layout<ANY, CNT, false>(s, a, pool);
+}
+
+}  // namespace
+
+bool trace_shape_supported(uint32_t block, uint32_t stack) {
+    const uint32_t shapes[][2] = {{64, 32}, {64, 48}, {64, 64}, {128, 32}, {128, 48}, {128, 64},
+                                  {256, 32}, {256, 48}, {256, 64}};
+    for (const auto &sh : shapes)
+        if (sh[0] == block && sh[1] == stack) return true;
+    return false;
+}
+
 cudaError_t launch_trace(cudaStream_t s, const TraceArgs &a, int any_hit) {
     if (a.n == 0) return cudaSuccess;
-    const bool count = a.counts != nullptr, multi = a.scenes != nullptr, pool = a.work != nullptr;
-    unsigned blocks = (unsigned)((a.n + TRACE_BLOCK - 1) / TRACE_BLOCK);
-    if (pool) {
-        // persistent grid: every block resident at once (the residency is
-        // queried once per device; all pool variants share the launch bounds)
-        // (kernels with the same launch bounds share an entry)
-        static std::atomic<int> resident[64][2];
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int roomy = (a.layout == 2 || multi) ? 1 : 0;
-        int per_sm = (dev >= 0 && dev < 64) ? resident[dev][roomy].load() : 0;
-        if (per_sm <= 0) {
-            if (roomy)
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_pool<false, false, 1, true>,
-                                                              TRACE_BLOCK, 0);
-            else
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_pool<false, false, 1, false>,
-                                                              TRACE_BLOCK, 0);
-            if (dev >= 0 && dev < 64 && per_sm > 0) resident[dev][roomy].store(per_sm);
-        }
-        const unsigned cap = (unsigned)std::max(1, sms) * (unsigned)std::max(1, per_sm);
-        blocks = std::min(blocks, cap);
-        cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), s);
-        if (e != cudaSuccess) return e;
-    }
-#define HCC_TRACE_KERNEL(K, ANY, CNT)                                           \
-    do {                                                                        \
-        if (multi) {                                                            \
-            if (a.layout == 0)                                                  \
-                K<ANY, CNT, 0, true><<<blocks, TRACE_BLOCK, 0, s>>>(a);         \
-            else if (a.layout == 1)                                             \
-                K<ANY, CNT, 1, true><<<blocks, TRACE_BLOCK, 0, s>>>(a);         \
-            else                                                                \
-                K<ANY, CNT, 2, true><<<blocks, TRACE_BLOCK, 0, s>>>(a);         \
-        } else {                                                                \
-            if (a.layout == 0)                                                  \
-                K<ANY, CNT, 0, false><<<blocks, TRACE_BLOCK, 0, s>>>(a);        \
-            else if (a.layout == 1)                                             \
-                K<ANY, CNT, 1, false><<<blocks, TRACE_BLOCK, 0, s>>>(a);        \
-            else                                                                \
-                K<ANY, CNT, 2, false><<<blocks, TRACE_BLOCK, 0, s>>>(a);        \
-        }                                                                       \
-    } while (0)
-#define HCC_TRACE_LAUNCH(ANY, CNT)                 \
-    do {                                           \
-        if (pool)                                  \
-            HCC_TRACE_KERNEL(k_trace_pool, ANY, CNT); \
-        else                                       \
-            HCC_TRACE_KERNEL(k_trace, ANY, CNT);   \
-    } while (0)
-    if (any_hit && count)
-        HCC_TRACE_LAUNCH(true, true);
-    else if (any_hit)
-        HCC_TRACE_LAUNCH(true, false);
-    else if (count)
-        HCC_TRACE_LAUNCH(false, true);
-    else
-        HCC_TRACE_LAUNCH(false, false);
-#undef HCC_TRACE_LAUNCH
-#undef HCC_TRACE_KERNEL
-    return cudaGetLastError();
+    const bool count = a.counts != nullptr, pool = a.work != nullptr;
+    if (any_hit && count) return launch_multi<true, true>(s, a, pool);
+    if (any_hit) return launch_multi<true, false>(s, a, pool);
+    if (count) return launch_multi<false, true>(s, a, pool);
+    return launch_multi<false, false>(s, a, pool);
 }
 
 }  // namespace hcc

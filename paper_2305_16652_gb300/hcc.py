@@ -39,7 +39,8 @@ class HccError(RuntimeError):
 
 
 class _Rays(ctypes.Structure):
-    _fields_ = [("org_tmin", ctypes.c_void_p), ("dir_tmax", ctypes.c_void_p), ("n", ctypes.c_uint64)]
+    _fields_ = [("org_tmin", ctypes.c_void_p), ("dir_tmax", ctypes.c_void_p), ("n", ctypes.c_uint64),
+                ("stride", ctypes.c_uint64)]
 
 
 class _ServerConfig(ctypes.Structure):
@@ -80,6 +81,7 @@ def load(path: str = LIB_PATH):
         "hcc_set_trace_schedule": [P, i32],
         "hcc_set_twopoint_distance": [P, ctypes.c_float],
         "hcc_set_sort_wait_limit": [P, u32],
+        "hcc_set_trace_shape": [P, u32, u32],
         "hcc_test_sort_withhold_tile": [P, u32],
         "hcc_reserve": [P, u64, u32],
         "hcc_sync": [P],
@@ -147,11 +149,27 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _row_stride_bytes(t) -> int:
+    """Bytes between consecutive rays of an (n, 4) float32 view (torch or numpy)."""
+    if isinstance(t, np.ndarray):
+        if t.ndim != 2 or t.shape[1] != 4 or t.strides[1] != 4:
+            raise ValueError("rays must be (n, 4) float32 views with contiguous rows")
+        return int(t.strides[0])
+    if t.dim() != 2 or t.shape[1] != 4 or t.stride(1) != 1:
+        raise ValueError("rays must be (n, 4) float32 views with contiguous rows")
+    return int(t.stride(0)) * t.element_size()
+
+
 def _rays(org, dir_):
+    """Ray descriptor of two (n, 4) views: two packed arrays, or the halves of
+    an (n, 8) tensor of 32-byte records (rec[:, :4], rec[:, 4:])."""
     n = int(org.shape[0])
     if dir_.shape[0] != n:
         raise ValueError("org_tmin and dir_tmax differ in length")
-    return _Rays(_ptr(org), _ptr(dir_), n)
+    so, sd = (_row_stride_bytes(org), _row_stride_bytes(dir_)) if n > 1 else (16, 16)
+    if so != sd:
+        raise ValueError("org_tmin and dir_tmax must have the same row stride")
+    return _Rays(_ptr(org), _ptr(dir_), n, so)
 
 
 def _stream_handle(stream):
@@ -240,6 +258,15 @@ def hcc_set_trace_schedule(ctx, schedule="auto"):
 def hcc_set_twopoint_distance(ctx, fraction: float = 0.25):
     """TwoPoint ray-length estimate as a fraction of the largest scene extent."""
     _check(load().hcc_set_twopoint_distance(ctx, fraction), ctx)
+
+
+HCC_TRACE_STACK = 64  # default traversal-stack entries per ray (include/hcc.h)
+TRACE_SHAPES = [(b, st) for b in (64, 128, 256) for st in (32, 48, 64)]
+
+
+def hcc_set_trace_shape(ctx, block_threads: int = 0, stack_entries: int = 0):
+    """Threads per block and stack entries per ray of the closest-hit persistent trace ((0, 0) = default)."""
+    _check(load().hcc_set_trace_shape(ctx, block_threads, stack_entries), ctx)
 
 
 def hcc_set_sort_wait_limit(ctx, status_reads: int = 0):

@@ -94,7 +94,10 @@ def test_batch_rejects_bad_arguments(env):
     hcc.hcc_sync(ctx)
 
 
-def test_spawn_matches_oracle_and_second_bounce(env):
+@pytest.mark.parametrize("records", [False, True])
+def test_spawn_matches_oracle_and_second_bounce(env, records):
+    """Both bounces of the batch, on packed arrays or on 32-byte ray records
+    (origin and direction adjacent) for the input and the spawned rays."""
     ctx = env["ctx"]
     bvhs, cuts = env["layouts"]["exact"]
     batch = hcc.hcc_batch_create(ctx, bvhs, cuts, env["offsets"])
@@ -102,7 +105,13 @@ def test_spawn_matches_oracle_and_second_bounce(env):
     o = torch.from_numpy(env["org"]).to(DEV)
     d = torch.from_numpy(env["dir"]).to(DEV)
     hits = torch.zeros((n, 4), dtype=torch.int32, device=DEV)
-    o2, d2 = torch.zeros_like(o), torch.zeros_like(d)
+    if records:
+        rec1 = torch.cat([o, d], 1)
+        rec2 = torch.zeros_like(rec1)
+        o, d = rec1[:, :4], rec1[:, 4:]
+        o2, d2 = rec2[:, :4], rec2[:, 4:]
+    else:
+        o2, d2 = torch.zeros_like(o), torch.zeros_like(d)
     hits2 = torch.zeros_like(hits)
     try:
         hcc.hcc_batch_run(ctx, batch, "hcc", o, d, 32, hits)
@@ -121,8 +130,8 @@ def test_spawn_matches_oracle_and_second_bounce(env):
         ref_o.append(ro)
         ref_d.append(rd)
         ref_h2.append(oracle.trace_bvh(w.bvh, ro, rd))
-    assert o2.cpu().numpy().tobytes() == np.concatenate(ref_o).tobytes()
-    assert d2.cpu().numpy().tobytes() == np.concatenate(ref_d).tobytes()
+    assert o2.contiguous().cpu().numpy().tobytes() == np.concatenate(ref_o).tobytes()
+    assert d2.contiguous().cpu().numpy().tobytes() == np.concatenate(ref_d).tobytes()
     g2 = hcc.hits_to_numpy(hits2)
     compare_hits(g2, np.concatenate(ref_h2))
     assert (g2["prim"] >= 0).mean() > 0.05
@@ -152,6 +161,42 @@ def test_graph_capture_replays_a_bounce(env):
         hcc.hcc_destroy(ctx)
 
 
+@pytest.mark.parametrize("layout", ["exact", "quantised", "wide"])
+def test_every_trace_shape_returns_the_oracle_hits(env, layout):
+    """Each block size and stack depth the autotuner may pick (deep enough for
+    the BVHs) gives the oracle's hits, on single wavefronts through the sorted
+    ids and on the whole batch; a stack too shallow is reported, never silent."""
+    from paper_2305_16652_gb300 import tune
+    ctx = env["ctx"]
+    bvhs, cuts = env["layouts"][layout]
+    cands = tune.shape_candidates(bvhs, layout)
+    assert cands and all(st >= tune.stack_bound(b, layout) for b in bvhs for _, st in cands)
+    off = env["offsets"].astype(np.int64)
+    o = torch.from_numpy(env["org"]).to(DEV)
+    d = torch.from_numpy(env["dir"]).to(DEV)
+    batch = hcc.hcc_batch_create(ctx, bvhs, cuts, env["offsets"])
+    try:
+        for shape in cands:
+            hcc.hcc_set_trace_shape(ctx, *shape)
+            hits = torch.zeros((o.shape[0], 4), dtype=torch.int32, device=DEV)
+            hcc.hcc_batch_run(ctx, batch, "hcc", o, d, 32, hits)
+            hcc.hcc_sync(ctx)
+            compare_hits(hcc.hits_to_numpy(hits), env["ref"])
+            s = 0
+            n = int(off[1] - off[0])
+            h1 = torch.zeros((n, 4), dtype=torch.int32, device=DEV)
+            hcc.hcc_run(ctx, "hcc", bvhs[s], cuts[s], o[:n], d[:n], 32, h1)
+            hcc.hcc_sync(ctx)
+            compare_hits(hcc.hits_to_numpy(h1), env["ref"][:n])
+    finally:
+        hcc.hcc_set_trace_shape(ctx, 0, 0)
+        hcc.hcc_batch_destroy(batch)
+    with pytest.raises(hcc.HccError):
+        hcc.hcc_set_trace_shape(ctx, 96, 64)
+    with pytest.raises(hcc.HccError):
+        hcc.hcc_set_trace_shape(ctx, 128, 40)
+
+
 def test_autotuner_choices_are_valid_and_keep_the_results(env):
     from paper_2305_16652_gb300 import tune
     stream = torch.cuda.Stream()
@@ -168,6 +213,7 @@ def test_autotuner_choices_are_valid_and_keep_the_results(env):
         assert t["key_bits"] in (16, 32) and t["schedule"] in ("refill", "per_ray")
         assert len(t["cut_sizes"]) == len(bvhs) and set(t["cut_sizes"]) <= {8, 32}
         assert set(t["lambdas"]) <= {0.0625, 0.125}
+        assert tuple(t["shape"]) in tune.shape_candidates(bvhs, "exact")
         cuts = [hcc.hcc_select_cut(ctx, b, C, lam) for b, C, lam in zip(bvhs, t["cut_sizes"], t["lambdas"])]
         batch = hcc.hcc_batch_create(ctx, bvhs, cuts, env["offsets"])
         hits = torch.zeros((o.shape[0], 4), dtype=torch.int32, device=DEV)

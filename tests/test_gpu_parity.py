@@ -322,6 +322,86 @@ def test_gather_bit_exact(ctx, n):
     assert po.cpu().numpy().tobytes() == oo.tobytes() and pd.cpu().numpy().tobytes() == od.tobytes()
 
 
+# ------------------------------------------------------------- ray layouts
+
+def _record_views(org, dir_, width=8, at=4):
+    """The rays as rows of `width` floats: origin at 0..3, direction at at..at+3."""
+    n = org.shape[0]
+    rec = torch.full((n, width), float("nan"), dtype=torch.float32, device=DEV)
+    rec[:, :4] = org
+    rec[:, at:at + 4] = dir_
+    return rec, rec[:, :4], rec[:, at:at + 4]
+
+
+@pytest.mark.parametrize("width,at", [(8, 4), (12, 8)])
+def test_strided_ray_layouts_give_the_same_keys_and_hits(ctx, room, width, at):
+    """32-byte records (origin, direction) and a wider stride give bit for bit
+    the keys, the gathered rays and the hit records of two packed arrays."""
+    rec, o, d = _record_views(room.org, room.dir, width, at)
+    cut = hcc.hcc_select_cut(ctx, room.bvh, 32, 0.125)
+    try:
+        for method, k in (("hcc", 32), ("twopoint", 30), ("origin", 30), ("origin_dir", 48)):
+            c = cut if method == "hcc" else None
+            assert np.array_equal(gpu_encode(ctx, room, method, k, cut=c, org=o, dir_=d),
+                                  gpu_encode(ctx, room, method, k, cut=c)), method
+        for kind in ("ppc", "mlhcc"):
+            a, b = _keys_tensor(room.n, 32), _keys_tensor(room.n, 32)
+            h = room.bvh_exact if kind == "ppc" else room.bvh
+            c = hcc.hcc_select_cut_ml(ctx, room.bvh, 8, 8, 0.125) if kind == "mlhcc" else None
+            try:
+                hcc.hcc_encode(ctx, kind, h, c, o, d, 32, a)
+                hcc.hcc_encode(ctx, kind, h, c, room.org, room.dir, 32, b)
+                hcc.hcc_sync(ctx)
+            finally:
+                if c is not None:
+                    hcc.hcc_cut_destroy(c)
+            assert torch.equal(a, b), kind
+        keys = _keys_tensor(room.n, 32)
+        hcc.hcc_encode(ctx, "hcc", room.bvh, cut, o, d, 32, keys)
+        perm = torch.empty(room.n, dtype=torch.int32, device=DEV)
+        hcc.hcc_sort(ctx, keys, 32, room.n, perm)
+    finally:
+        hcc.hcc_cut_destroy(cut)
+    ref = oracle.trace_bvh(room.w.bvh, room.w.rays.org, room.w.rays.dir)
+    for layout in ("quantised", "exact", "wide"):
+        compare_hits(gpu_trace(ctx, room, o, d, layout=layout), ref)
+        bvh = {"quantised": room.bvh, "exact": room.bvh_exact, "wide": room.bvh_wide}[layout]
+        hits = torch.zeros((room.n, 4), dtype=torch.int32, device=DEV)
+        hcc.hcc_trace_sorted(ctx, bvh, o, d, perm, hits)
+        hcc.hcc_sync(ctx)
+        compare_hits(hcc.hits_to_numpy(hits), ref)
+    # gathers between every pair of layouts: the oracle's gathered records, bit for bit
+    p = perm.cpu().numpy().view(np.uint32)
+    oo, od = oracle.gather(room.w.rays.org, room.w.rays.dir, p)
+    packed_out = (torch.zeros_like(room.org), torch.zeros_like(room.dir))
+    _, ro, rd = _record_views(torch.zeros_like(room.org), torch.zeros_like(room.dir), width, at)
+    for src in ((room.org, room.dir), (o, d)):
+        for dst in (packed_out, (ro, rd)):
+            dst[0].zero_()
+            dst[1].zero_()
+            hcc.hcc_gather(ctx, src[0], src[1], perm, dst[0], dst[1])
+            hcc.hcc_sync(ctx)
+            assert dst[0].cpu().numpy().tobytes() == oo.tobytes()
+            assert dst[1].cpu().numpy().tobytes() == od.tobytes()
+    # the whole pipeline on records
+    hits = torch.zeros((room.n, 4), dtype=torch.int32, device=DEV)
+    cut = hcc.hcc_select_cut(ctx, room.bvh, 32, 0.125)
+    try:
+        hcc.hcc_run(ctx, "hcc", room.bvh, cut, o, d, 32, hits)
+        hcc.hcc_sync(ctx)
+    finally:
+        hcc.hcc_cut_destroy(cut)
+    compare_hits(hcc.hits_to_numpy(hits), ref)
+
+
+def test_ray_stride_must_be_a_multiple_of_16(ctx, room):
+    bad = torch.zeros((room.n, 6), dtype=torch.float32, device=DEV)  # 24-byte rows
+    keys = _keys_tensor(room.n, 32)
+    with pytest.raises(hcc.HccError) as ei:
+        hcc.hcc_encode(ctx, "twopoint", room.bvh, None, bad[:, :4], bad[:, 2:6], 32, keys)
+    assert ei.value.status == 1
+
+
 # ------------------------------------------------------------------- trace
 
 @pytest.mark.parametrize("layout", ["quantised", "exact", "wide"])
@@ -510,6 +590,34 @@ def test_stack_overflow_is_reported_and_context_survives(ctx, tiny, layout):
     # the context keeps working
     g = gpu_trace(ctx, tiny, tiny.org, tiny.dir)
     compare_hits(g, oracle.trace_bvh(tiny.w.bvh, tiny.w.rays.org, tiny.w.rays.dir))
+
+
+@pytest.mark.parametrize("layout", ["quantised", "exact"])
+def test_trace_shape_stack_depth_is_honoured(ctx, tiny, layout):
+    """A 40-level chain fits 48 or 64 stack entries but not 32: the shallow
+    shape reports the overflow (and a miss), the deeper ones find the hit."""
+    deep = _chain_bvh(40)
+    h = hcc.hcc_bvh_upload(ctx, deep, layout=layout)
+    c = deep.tris.reshape(-1, 3).mean(0)
+    org = torch.tensor([[c[0], c[1], c[2] - 5.0, 0.0]], dtype=torch.float32, device=DEV)
+    dir_ = torch.tensor([[0.0, 0.0, 1.0, float("inf")]], dtype=torch.float32, device=DEV)
+    ref = oracle.trace_bvh(deep, org.cpu().numpy(), dir_.cpu().numpy())
+    try:
+        for block in (64, 128, 256):
+            for stack in (32, 48, 64):
+                hcc.hcc_set_trace_shape(ctx, block, stack)
+                hits = torch.zeros((1, 4), dtype=torch.int32, device=DEV)
+                hcc.hcc_trace(ctx, h, org, dir_, hits)
+                if stack == 32:
+                    with pytest.raises(hcc.HccError) as ei:
+                        hcc.hcc_sync(ctx)
+                    assert ei.value.status == 5 and int(hits[0, 0]) == -1
+                else:
+                    hcc.hcc_sync(ctx)
+                    compare_hits(hcc.hits_to_numpy(hits), ref)
+    finally:
+        hcc.hcc_set_trace_shape(ctx, 0, 0)
+        hcc.hcc_bvh_destroy(h)
 
 
 @pytest.mark.parametrize("which", ["tiny", "room"])
