@@ -1087,13 +1087,17 @@ def profile_case(name: str):
     """Small, fixed workloads for ncu captures (not a benchmark: nothing is timed).
 
     trace-small: 480x270x8spp room, 200k triangles, exact nodes: HCC encode,
-                 sort, trace through the sorted ids, then the NoSort trace.
+                 sort, trace through the sorted ids, the NoSort trace, then the
+                 trace through the sorted ids of the rays as 32-byte records.
     sort-16m:    two sorts of 16,588,800 seeded uniform 32-bit keys.
     sort-hcc:    two sorts of the 16,588,800 HCC keys (cut 32, 32-bit keys) of
                  the 1920x1080x8spp room wavefront.
+    gather:      the split gather of that wavefront through its HCC permutation,
+                 from and to two float4 arrays, then from and to 32-byte records.
     trace-orders: the 1920x1080x8spp room (16,588,800 rays), exact nodes: the
                  closest-hit trace in NoSort, TwoPoint and HCC order (32-bit
-                 keys, cut 32), one launch each, in that order.
+                 keys, cut 32), one launch each, in that order, then in HCC
+                 order on the rays as 32-byte records.
     """
     import torch
     from paper_2305_16652_gb300 import build, hcc
@@ -1118,6 +1122,24 @@ def profile_case(name: str):
         hcc.hcc_encode(ctx, "hcc", bvh, cut, org, dir_, 32, keys)
         for _ in range(2):
             hcc.hcc_sort(ctx, keys, 32, n, perm)
+    elif name == "gather":
+        w = make_workload(1, False)
+        n = w.rays.n
+        bvh = hcc.hcc_bvh_upload(ctx, w.bvh, layout="exact")
+        cut = hcc.hcc_select_cut(ctx, bvh, 32, 0.125)
+        org, dir_ = torch.from_numpy(w.rays.org).cuda(), torch.from_numpy(w.rays.dir).cuda()
+        keys = torch.empty(n, dtype=torch.int32, device="cuda")
+        perm = torch.empty(n, dtype=torch.int32, device="cuda")
+        hcc.hcc_reserve(ctx, n, 32)
+        hcc.hcc_encode(ctx, "hcc", bvh, cut, org, dir_, 32, keys)
+        hcc.hcc_sort(ctx, keys, 32, n, perm)
+        so, sd = torch.empty_like(org), torch.empty_like(dir_)
+        hcc.hcc_gather(ctx, org, dir_, perm, so, sd)
+        del so, sd
+        rec = torch.cat([org, dir_], 1)
+        del org, dir_
+        out = torch.empty_like(rec)
+        hcc.hcc_gather(ctx, rec[:, :4], rec[:, 4:], perm, out[:, :4], out[:, 4:])
     elif name == "trace-small":
         w = make_workload(1, True)
         n = w.rays.n
@@ -1131,6 +1153,8 @@ def profile_case(name: str):
         hcc.hcc_sort(ctx, keys, 32, n, perm)
         hcc.hcc_trace_sorted(ctx, bvh, org, dir_, perm, hits)
         hcc.hcc_trace(ctx, bvh, org, dir_, hits)
+        rec = torch.cat([org, dir_], 1)  # the same rays as 32-byte records, traced in HCC order
+        hcc.hcc_trace_sorted(ctx, bvh, rec[:, :4], rec[:, 4:], perm, hits)
     elif name == "trace-orders":
         w = make_workload(1, False)
         n = w.rays.n
@@ -1146,6 +1170,8 @@ def profile_case(name: str):
             hcc.hcc_encode(ctx, method, bvh, cut if method == "hcc" else None, org, dir_, 32, keys)
             hcc.hcc_sort(ctx, keys, 32, n, perm)
             hcc.hcc_trace_sorted(ctx, bvh, org, dir_, perm, hits)
+        rec = torch.cat([org, dir_], 1)  # HCC order again, the rays as 32-byte records
+        hcc.hcc_trace_sorted(ctx, bvh, rec[:, :4], rec[:, 4:], perm, hits)
     else:
         raise SystemExit(f"unknown case {name}")
     hcc.hcc_sync(ctx)
@@ -1166,7 +1192,7 @@ def main(argv=None):
     ap.add_argument("--cpu-sample", type=int, default=1_500_000)
     ap.add_argument("--ref-sample", type=int, default=300_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["trace-small", "sort-16m", "sort-hcc", "trace-orders"], help="run a profiling case and exit")
+    ap.add_argument("--case", choices=["trace-small", "sort-16m", "sort-hcc", "gather", "trace-orders"], help="run a profiling case and exit")
     ap.add_argument("--sweep", choices=["keylen", "batch", "serve", "methods", "hyper"],
                     help="run a study instead of the headline benchmark")
     ap.add_argument("--slots", type=int, default=4, help="serving: requests on the GPU at once")

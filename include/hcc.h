@@ -189,7 +189,7 @@ hcc_status hcc_set_twopoint_distance(hcc_ctx *ctx, float fraction);
 hcc_status hcc_set_sort_wait_limit(hcc_ctx *ctx, uint32_t status_reads);
 
 /* Test hook for the bounded wait above (no counterpart in the paper): while
- * set, tile number `tile` (4096 keys each) of every digit pass of this
+ * set, tile number `tile` (3584 keys each) of every digit pass of this
  * context's sorts never publishes its counts, so the tile after it waits
  * until its limit and the sort reports HCC_ERR_TIMEOUT.  0xFFFFFFFF (the
  * default) withholds nothing.  Never needed outside tests. */

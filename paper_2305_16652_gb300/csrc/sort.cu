@@ -10,7 +10,7 @@
 //            ping-pong buffers are chosen so that the first active pass reads
 //            the caller's keys and synthesises ids, and the last one writes
 //            only the permutation
-//   k_pass   one block per 4096-key tile: warp-level stable ranking
+//   k_pass   one block per tile of keys: warp-level stable ranking
 //            (match.any, or a ballot split when a warp's digits are spread),
 //            per-digit tile counts published to a decoupled look-back chain
 //            (bounded waits), keys reordered in shared memory and written out
@@ -30,7 +30,15 @@ constexpr int RADIX = 256;
 constexpr int MAX_PASSES = 8;
 constexpr int SORT_BLOCK = 256;  // one thread per digit in the scan / look-back
 constexpr int SORT_WARPS = SORT_BLOCK / 32;
-constexpr int SORT_ITEMS = 16;
+// 14 keys per thread (3584-key tiles) and four resident blocks per SM
+// measured fastest among 8-16 keys and 3-6 blocks on 16.6M ray keys
+#ifndef SORT_ITEMS_PER_THREAD
+#define SORT_ITEMS_PER_THREAD 14
+#endif
+#ifndef SORT_MIN_BLOCKS
+#define SORT_MIN_BLOCKS 4
+#endif
+constexpr int SORT_ITEMS = SORT_ITEMS_PER_THREAD;
 constexpr int SORT_TILE = SORT_BLOCK * SORT_ITEMS;
 constexpr uint32_t ST_AGG = 1u << 30;  // tile count of this digit available
 constexpr uint32_t ST_INC = 2u << 30;  // inclusive prefix of this digit available
@@ -296,7 +304,7 @@ __device__ __forceinline__ void rank_items(const K (&kreg)[SORT_ITEMS], uint32_t
     }
 }
 
-// One digit pass, one block per tile of 4096 keys.  A block takes its tile
+// One digit pass, one block per tile of SORT_TILE keys.  A block takes its tile
 // from an atomic counter when it starts, so tiles are worked on in the order
 // blocks start and a tile's predecessors are already running when it looks
 // back.  Per tile: each thread loads its 16 items (a warp reads 32
@@ -308,7 +316,7 @@ __device__ __forceinline__ void rank_items(const K (&kreg)[SORT_ITEMS], uint32_t
 // element moves with one 8-byte access; 64-bit keys as separate key and id
 // arrays.
 template <typename K>
-__global__ void __launch_bounds__(SORT_BLOCK, sizeof(K) == 4 ? 3 : 2) k_pass(PassArgs<K> a, int pass) {
+__global__ void __launch_bounds__(SORT_BLOCK, sizeof(K) == 4 ? SORT_MIN_BLOCKS : 2) k_pass(PassArgs<K> a, int pass) {
     constexpr bool PAIRS = sizeof(K) == 4;
     const PassPlan pl = a.h->plan[pass];
     if (!pl.active) {

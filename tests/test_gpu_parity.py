@@ -250,7 +250,7 @@ def _keys(kind, n, k, rng):
     raise ValueError(kind)
 
 
-@pytest.mark.parametrize("n", [0, 1, 2, 31, 32, 33, 4095, 4096, 4097, 8193, 12288, 65537, 300_001])
+@pytest.mark.parametrize("n", [0, 1, 2, 31, 32, 33, 3583, 3584, 3585, 4096, 7169, 10752, 65537, 300_001])
 def test_sort_sizes(ctx, n):
     rng = np.random.default_rng(n)
     for k in (32, 17):
@@ -292,7 +292,7 @@ def test_sort_bounded_wait_runs_out_and_the_context_recovers(ctx, tile, k):
     tile returns (the sort ends), and the next sort on the same context is
     the oracle's stable sort again."""
     rng = np.random.default_rng(77 + tile + k)
-    n = 300_001  # 74 tiles of 4096 keys
+    n = 300_001  # 84 tiles of 3584 keys
     keys = _keys("uniform", n, k, rng)
     try:
         hcc.hcc_set_sort_wait_limit(ctx, 256)
