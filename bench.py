@@ -836,8 +836,8 @@ def run_batch_sweep(args):
                                   f"{n} rays per bounce", "bvh_layout": args.layout,
                       "scenes": [{"tris": int(w.tris.shape[0]), "rays": int(w.rays.n)} for w in ws]},
            "autotune": {"key_bits": tuned["key_bits"], "cut_sizes": tuned["cut_sizes"], "lambdas": tuned["lambdas"],
-                        "schedule": tuned["schedule"], "totals_ms": tuned["totals_ms"],
-                        "seconds": round(tune_s, 1)},
+                        "schedule": tuned["schedule"], "shape": list(tuned["shape"]), "shape_ms": tuned["shape_ms"],
+                        "totals_ms": tuned["totals_ms"], "seconds": round(tune_s, 1)},
            "generation_s": round(gen_s, 1), "methods": results}
     for c in cuts:
         hcc.hcc_cut_destroy(c)

@@ -29,6 +29,23 @@ struct DevBuf {
 // pipelined hcc_run_host.
 constexpr uint64_t HOST_CHUNK = 1ull << 22;
 constexpr uint32_t HOST_LANES = 2;
+#ifndef HCC_HOST_FIRST_CHUNK
+#define HCC_HOST_FIRST_CHUNK (1ull << 21)
+#endif
+#ifndef HCC_HOST_LAST_CHUNK
+#define HCC_HOST_LAST_CHUNK 0ull
+#endif
+// The first chunk is smaller, so the first kernels start sooner; with a
+// last-chunk size set, the rays left after the full chunks end with a chunk
+// that small, so less of the final copy back follows the last kernel.
+constexpr uint64_t HOST_FIRST = HCC_HOST_FIRST_CHUNK, HOST_LAST = HCC_HOST_LAST_CHUNK;
+
+static uint64_t host_chunk_rays(uint64_t c, uint64_t rem) {
+    if (c == 0) return std::min(HOST_FIRST, rem);
+    if (HOST_LAST == 0 || rem <= HOST_LAST) return std::min(HOST_CHUNK, rem);
+    if (rem <= HOST_CHUNK + HOST_LAST) return rem - HOST_LAST;
+    return HOST_CHUNK;
+}
 
 struct hcc_ctx {
     int device = 0;
@@ -1555,8 +1572,7 @@ hcc_status hcc_run_host(hcc_ctx *ctx, hcc_method method, const hcc_bvh *bvh, con
         hcc_ctx *L = ctx->lane[c % HOST_LANES];
         L->schedule = ctx->schedule;
         L->twopoint_fraction = ctx->twopoint_fraction;
-        // the first chunk is half as large, so the first kernels start sooner
-        m = std::min<uint64_t>(c == 0 ? HOST_CHUNK / 2 : HOST_CHUNK, n - c0);
+        m = host_chunk_rays(c, n - c0);
         if ((st = ensure(L, L->in_org, HOST_CHUNK * 16, "input rays")) != HCC_OK ||
             (st = ensure(L, L->in_dir, HOST_CHUNK * 16, "input rays")) != HCC_OK ||
             (st = ensure(L, L->hits, HOST_CHUNK * sizeof(hcc_hit), "hits")) != HCC_OK) {

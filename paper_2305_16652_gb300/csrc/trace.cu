@@ -244,11 +244,19 @@ __device__ __forceinline__ void ray_init(RayState &s, const float4 o4, const flo
 
 __device__ __forceinline__ bool ray_done(const RayState &s) { return s.node == REF_NONE && s.leaf == REF_NONE; }
 
+// Pending subtrees are (node reference, entry distance) entries of a
+// STACKN-entry array in local memory, one 8-byte access each.
+template <int STACKN>
+__device__ __forceinline__ bool ray_push(RayState &s, uint2 *stack, uint2 e) {  // false: no room
+    if (s.sp >= STACKN) return false;
+    stack[s.sp++] = e;
+    return true;
+}
+
 // Next pending subtree that can still hold a closer hit, or REF_NONE.
 __device__ __forceinline__ uint32_t ray_pop(RayState &s, const uint2 *stack) {
     while (s.sp > 0) {
-        --s.sp;
-        const uint2 e = stack[s.sp];  // (node reference, entry distance): one 8-byte access
+        const uint2 e = stack[--s.sp];
         if (__uint_as_float(e.y) <= s.tcap) return e.x;
     }
     return REF_NONE;
@@ -299,9 +307,9 @@ __device__ __forceinline__ void ray_round(RayState &s, uint2 *stack, const uint4
                 s.node = s.leaf = REF_NONE;
                 break;
             }
-            if (met > 3) stack[s.sp++] = make_uint2(r3, __float_as_uint(t3));
-            if (met > 2) stack[s.sp++] = make_uint2(r2, __float_as_uint(t2));
-            if (met > 1) stack[s.sp++] = make_uint2(r1, __float_as_uint(t1));
+            if (met > 3) ray_push<STACKN>(s, stack, make_uint2(r3, __float_as_uint(t3)));
+            if (met > 2) ray_push<STACKN>(s, stack, make_uint2(r2, __float_as_uint(t2)));
+            if (met > 1) ray_push<STACKN>(s, stack, make_uint2(r1, __float_as_uint(t1)));
             s.node = r0;
         }
         if (s.node != REF_NONE && (s.node & REF_LEAF) && s.leaf == REF_NONE) {
@@ -327,13 +335,11 @@ __device__ __forceinline__ void ray_round(RayState &s, uint2 *stack, const uint4
         const bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
         if (h0 && h1) {
             const bool first0 = tn0 <= tn1;
-            if (s.sp == STACKN) {
+            if (!ray_push<STACKN>(s, stack, make_uint2(first0 ? c.ref1 : c.ref0, __float_as_uint(first0 ? tn1 : tn0)))) {
                 s.overflow = true;
                 s.node = s.leaf = REF_NONE;
                 break;
             }
-            stack[s.sp] = make_uint2(first0 ? c.ref1 : c.ref0, __float_as_uint(first0 ? tn1 : tn0));
-            ++s.sp;
             s.node = first0 ? c.ref0 : c.ref1;
         } else if (h0) {
             s.node = c.ref0;
