@@ -29,23 +29,8 @@ struct DevBuf {
 // pipelined hcc_run_host.
 constexpr uint64_t HOST_CHUNK = 1ull << 22;
 constexpr uint32_t HOST_LANES = 2;
-#ifndef HCC_HOST_FIRST_CHUNK
-#define HCC_HOST_FIRST_CHUNK (1ull << 21)
-#endif
-#ifndef HCC_HOST_LAST_CHUNK
-#define HCC_HOST_LAST_CHUNK 0ull
-#endif
-// The first chunk is smaller, so the first kernels start sooner; with a
-// last-chunk size set, the rays left after the full chunks end with a chunk
-// that small, so less of the final copy back follows the last kernel.
-constexpr uint64_t HOST_FIRST = HCC_HOST_FIRST_CHUNK, HOST_LAST = HCC_HOST_LAST_CHUNK;
-
-static uint64_t host_chunk_rays(uint64_t c, uint64_t rem) {
-    if (c == 0) return std::min(HOST_FIRST, rem);
-    if (HOST_LAST == 0 || rem <= HOST_LAST) return std::min(HOST_CHUNK, rem);
-    if (rem <= HOST_CHUNK + HOST_LAST) return rem - HOST_LAST;
-    return HOST_CHUNK;
-}
+// The first chunk is half as large, so the first kernels start sooner.
+static uint64_t host_chunk_rays(uint64_t c, uint64_t rem) { return std::min(c == 0 ? HOST_CHUNK / 2 : HOST_CHUNK, rem); }
 
 struct hcc_ctx {
     int device = 0;
