@@ -269,6 +269,53 @@ struct PassArgs {
     int last_launch;         // the last pass launch writes the identity permutation if no pass is active
 };
 
+// Decoupled look-back for digit d of tile `tile`: the sum of the digit's
+// counts in all earlier tiles, read from their status words newest first
+// (LOOKBACK per round) until an inclusive prefix is found.  Each wait is
+// bounded: after wait_limit status reads without progress (or once another
+// tile has given up) it records a timeout and returns.
+template <typename K>
+__device__ __forceinline__ uint32_t look_back(const PassArgs<K> &a, int pass, uint32_t tile, uint32_t d,
+                                              bool &timed_out) {
+    uint32_t excl = 0;
+    int64_t j = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    bool done = false;
+    const uint32_t wait_rounds = a.wait_limit / LOOKBACK;
+    const uint32_t *col = a.status + (size_t)pass * a.num_tiles * RADIX + d;
+    while (!done) {
+        uint32_t sv[LOOKBACK];
+#pragma unroll
+        for (int w = 0; w < LOOKBACK; ++w) sv[w] = (j - w >= 0) ? ld_relaxed(col + (size_t)(j - w) * RADIX) : ST_INC;
+        int used = 0;
+        bool stalled = false;
+#pragma unroll
+        for (int w = 0; w < LOOKBACK; ++w) {
+            if (done || stalled) continue;
+            const uint32_t flag = sv[w] & ~ST_VALUE;
+            if (flag == 0) {
+                stalled = true;
+                continue;
+            }
+            if (j - w >= 0) excl += sv[w] & ST_VALUE;
+            ++used;
+            if (flag == ST_INC) done = true;
+        }
+        j -= used;
+        if (done) break;
+        if (stalled) {
+            if (++spins > wait_rounds || ((spins & 63u) == 0 && ld_relaxed(&a.h->abort))) {
+                timed_out = true;
+                atomicOr(a.err, ERR_TIMEOUT);
+                atomicExch(&a.h->abort, 1u);
+                break;
+            }
+            __nanosleep(spins < 8 ? 32u * spins : 256u);
+        }
+    }
+    return excl;
+}
+
 // Stable rank of this thread's items within their digit in the warp's
 // running count: lanes with equal digits found by match.any (or by the
 // ballot split when the warp's first item shows many distinct digits), the
@@ -434,46 +481,9 @@ __global__ void __launch_bounds__(SORT_BLOCK, sizeof(K) == 4 ? SORT_MIN_BLOCKS :
     if (tile == 0) {
         excl = a.h->start[pass][tid];
     } else {
-        excl = 0;
-        int64_t j = (int64_t)tile - 1;
-        uint32_t spins = 0;
-        bool timed_out = false, done = false;
-        const uint32_t wait_rounds = a.wait_limit / LOOKBACK;
-        const uint32_t *col = a.status + (size_t)pass * a.num_tiles * RADIX + tid;
-        while (!done) {
-            uint32_t sv[LOOKBACK];
-#pragma unroll
-            for (int w = 0; w < LOOKBACK; ++w)
-                sv[w] = (j - w >= 0) ? ld_relaxed(col + (size_t)(j - w) * RADIX) : ST_INC;
-            int used = 0;
-            bool stalled = false;
-#pragma unroll
-            for (int w = 0; w < LOOKBACK; ++w) {
-                if (done || stalled) continue;
-                const uint32_t flag = sv[w] & ~ST_VALUE;
-                if (flag == 0) {
-                    stalled = true;
-                    continue;
-                }
-                if (j - w >= 0) excl += sv[w] & ST_VALUE;
-                ++used;
-                if (flag == ST_INC) done = true;
-            }
-            j -= used;
-            if (done) break;
-            if (stalled) {
-                if (++spins > wait_rounds || ((spins & 63u) == 0 && ld_relaxed(&a.h->abort))) {
-                    timed_out = true;
-                    break;
-                }
-                __nanosleep(spins < 8 ? 32u * spins : 256u);
-            }
-        }
-        if (timed_out) {
-            atomicOr(a.err, ERR_TIMEOUT);
-            atomicExch(&a.h->abort, 1u);
-            s_abort = 1;
-        }
+        bool timed_out = false;
+        excl = look_back(a, pass, tile, tid, timed_out);
+        if (timed_out) s_abort = 1;
         if (publish) st_relaxed(st + tid, ST_INC | ((excl + total) & ST_VALUE));
     }
     s_gofs[tid] = excl - local;
