@@ -181,8 +181,9 @@ def peaks():
         return FALLBACK_HBM_GBS, 2070.0, "fallback"
 
 
-def recorded_traffic():
-    """DRAM bytes per trace launch from the committed ncu summary, if trace.cu is unchanged."""
+def recorded_trace_counters():
+    """DRAM bytes and instruction counts of one HCC-order trace launch from the
+    committed ncu summary, if trace.cu is unchanged (else an empty dict)."""
     try:
         rec = {}
         for line in open(TRAFFIC_FILE):
@@ -192,10 +193,10 @@ def recorded_traffic():
             rec[k.strip()] = v.strip()
         src = open(os.path.join(ROOT, "paper_2305_16652_gb300", "csrc", "trace.cu"), "rb").read()
         if rec.get("trace_cu_sha256") != hashlib.sha256(src).hexdigest():
-            return None
-        return int(rec["dram_bytes_per_launch"])
+            return {}
+        return {k: int(rec[k]) for k in ("dram_bytes_per_launch", "warp_instructions", "lane_instructions") if k in rec}
     except Exception:
-        return None
+        return {}
 
 
 # ------------------------------------------------------------- our path
@@ -219,14 +220,20 @@ def run_ours(args, rank, world, local_rank):
     keys = torch.empty(n, dtype=torch.int32, device=dev)
     perm = torch.empty(n, dtype=torch.int32, device=dev)
     sorg, sdir = torch.empty_like(org), torch.empty_like(dir_)
+    # the same rays as 32-byte records (origin then direction) for the record legs
+    rec = torch.cat([org, dir_], 1)
+    srec = torch.empty_like(rec)
     hits = torch.empty((n, 4), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
     shapes = {"nosort": (128, hcc.HCC_TRACE_STACK), "sorted": (128, hcc.HCC_TRACE_STACK)}
 
-    def step(method, ev=None, fused=True, bvh_h=None, schedule="auto"):
-        """One wavefront through the C ABI; ev = 5 events around encode/sort/gather/trace."""
+    def step(method, ev=None, fused=True, bvh_h=None, schedule="auto", records=False):
+        """One wavefront through the C ABI; ev = 5 events around encode/sort/gather/trace.
+        records: the rays as 32-byte records instead of two float4 arrays."""
         b = bvh_h or bvh
+        o, d = (rec[:, :4], rec[:, 4:]) if records else (org, dir_)
+        so, sd = (srec[:, :4], srec[:, 4:]) if records else (sorg, sdir)
         hcc.hcc_set_trace_schedule(ctx, schedule)
         hcc.hcc_set_trace_shape(ctx, *shapes["nosort" if method == "nosort" else "sorted"])
         if ev:
@@ -235,11 +242,11 @@ def run_ours(args, rank, world, local_rank):
             if ev:
                 for e in ev[1:4]:
                     e.record(stream)
-            hcc.hcc_trace(ctx, b, org, dir_, hits)
+            hcc.hcc_trace(ctx, b, o, d, hits)
             if ev:
                 ev[4].record(stream)
             return
-        hcc.hcc_encode(ctx, method, b, cut if method == "hcc" else None, org, dir_, K, keys)
+        hcc.hcc_encode(ctx, method, b, cut if method == "hcc" else None, o, d, K, keys)
         if ev:
             ev[1].record(stream)
         hcc.hcc_sort(ctx, keys, K, n, perm)
@@ -248,12 +255,12 @@ def run_ours(args, rank, world, local_rank):
         if fused:  # the trace fetches each ray through the sorted ids (Sec. 5)
             if ev:
                 ev[3].record(stream)
-            hcc.hcc_trace_sorted(ctx, b, org, dir_, perm, hits)
+            hcc.hcc_trace_sorted(ctx, b, o, d, perm, hits)
         else:
-            hcc.hcc_gather(ctx, org, dir_, perm, sorg, sdir)
+            hcc.hcc_gather(ctx, o, d, perm, so, sd)
             if ev:
                 ev[3].record(stream)
-            hcc.hcc_trace(ctx, b, sorg, sdir, hits, scatter=perm)
+            hcc.hcc_trace(ctx, b, so, sd, hits, scatter=perm)
         if ev:
             ev[4].record(stream)
 
@@ -287,6 +294,8 @@ def run_ours(args, rank, world, local_rank):
     others = {}
     variants = [("nosort", "nosort", {}), ("twopoint", "twopoint", {}),
                 ("hcc_split_gather", "hcc", {"fused": False}),
+                ("hcc_records", "hcc", {"records": True}),
+                ("hcc_split_gather_records", "hcc", {"fused": False, "records": True}),
                 ("nosort_quantised", "nosort", {"bvh_h": bvh_q}), ("hcc_quantised", "hcc", {"bvh_h": bvh_q}),
                 ("nosort_per_ray", "nosort", {"schedule": "per_ray"}), ("hcc_per_ray", "hcc", {"schedule": "per_ray"}),
                 ("twopoint_per_ray", "twopoint", {"schedule": "per_ray"})]
@@ -312,6 +321,7 @@ def run_ours(args, rank, world, local_rank):
     p99 = per[min(len(per) - 1, int(round(0.99 * (len(per) - 1))))]
     st = [statistics.mean(x) for x in r["stages"]]
     g_split = others["hcc_split_gather"]["stages_ms"]["gather"]
+    g_split_rec = others["hcc_split_gather_records"]["stages_ms"]["gather"]
 
     # e2e through the public host-buffer call: H2D rays, pipeline, D2H hits
     h_org = torch.empty((n, 4), dtype=torch.float32, pin_memory=True)
@@ -355,6 +365,14 @@ def run_ours(args, rank, world, local_rank):
     trace_ms = st[3]
     work = counts["node_visits"] * OPS_PER_NODE[args.layout] + counts["tri_tests"] * OPS_PER_TRI
     achieved = work / (trace_ms * 1e-3) / 1e12
+    tc = recorded_trace_counters() if args.layout == "exact" and C == 32 and K == 32 else {}
+    measured = None
+    if "lane_instructions" in tc:  # counters of the same launch (ncu), over this run's trace time
+        measured = {"lane_instructions_per_ray": round(tc["lane_instructions"] / n, 1),
+                    "active_lanes": round(tc["lane_instructions"] / tc["warp_instructions"], 2),
+                    "issue_frac": round(tc["warp_instructions"] / (trace_ms * 1e-3) / (SMS * 4 * clk_mhz * 1e6), 3),
+                    "lane_frac": round(tc["lane_instructions"] / (trace_ms * 1e-3) / 1e12 / alu_peak, 3),
+                    "source": "ncu counters of one launch (profiles/trace_room_1080p_dram.txt)"}
     sort_passes = active_digit_passes(keys, K)
     sb = sort_bytes_per_key(sort_passes)
     enc_ops = (ENCODE_OPS_PER_NODE * min(C, K) + ENCODE_OPS_PER_RAY) * n
@@ -368,13 +386,17 @@ def run_ours(args, rank, world, local_rank):
                      achieved_gbs=round(sb * n / (st[1] * 1e6), 1), frac=round(sb * n / (st[1] * 1e6) / hbm, 3)),
         "gather": dict(ms=0.0, fused_into_trace=True, split_kernel_ms=round(g_split, 4), bound="hbm",
                        split_achieved_gbs=round(BYTES_GATHER * n / (g_split * 1e6), 1),
-                       split_frac=round(BYTES_GATHER * n / (g_split * 1e6) / hbm, 3)),
+                       split_frac=round(BYTES_GATHER * n / (g_split * 1e6) / hbm, 3),
+                       split_kernel_ms_records=round(g_split_rec, 4),
+                       split_achieved_gbs_records=round(BYTES_GATHER * n / (g_split_rec * 1e6), 1),
+                       split_frac_records=round(BYTES_GATHER * n / (g_split_rec * 1e6) / hbm, 3)),
         "trace": dict(ms=round(st[3], 4), bound="alu", achieved_tops=round(achieved, 3),
                       frac=round(achieved / alu_peak, 3),
                       node_visits_per_ray=round(counts["node_visits"] / n, 2),
                       tri_tests_per_ray=round(counts["tri_tests"] / n, 2),
                       warp_efficiency=round(counts["node_visits"] / (32.0 * max(1, counts["warp_node_steps"])), 4),
-                      warp_efficiency_nosort=round(counts0["node_visits"] / (32.0 * max(1, counts0["warp_node_steps"])), 4)),
+                      warp_efficiency_nosort=round(counts0["node_visits"] / (32.0 * max(1, counts0["warp_node_steps"])), 4),
+                      measured=measured),
     }
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -399,9 +421,9 @@ def run_ours(args, rank, world, local_rank):
         "hits_identical_hcc_vs_nosort": identical,
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(n * 32),
                 "d2h_bytes_per_step": int(n * 16), "call": "hcc_run_host"},
-        "gpu_launches": 9 * args.steps,
+        "gpu_launches": 7 * args.steps,  # per step: encode, sort histogram + 4 digit passes, trace
         "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 2), "unit": "Tops/s",
-                     "frac": round(achieved / alu_peak, 3), "traffic": recorded_traffic(),
+                     "frac": round(achieved / alu_peak, 3), "traffic": tc.get("dram_bytes_per_launch"),
                      "kernel": f"k_trace_pool (closest hit, HCC order, {args.layout} nodes, ray replacement)",
                      "peak_source": f"{SMS} SMs x {LANES_PER_SM} lanes x {clk_mhz:.0f} MHz"},
         "stages": stages,

@@ -3,8 +3,9 @@
 //
 // Design (one pass per 8-bit digit, "onesweep" structure):
 //   k_hist   one read of every key builds the digit histograms of all passes
-//            (warp-private counters, equal digits of a warp merged with
-//            match.any); the last block to finish scans them and plans the
+//            (each warp counts its most common digit in a register, the rest
+//            with shared-memory atomics); the last block to finish scans them
+//            and plans the
 //            passes: a pass whose digit is the same for every key is marked
 //            inactive (skipping it cannot change a stable result), and the
 //            ping-pong buffers are chosen so that the first active pass reads
