@@ -21,6 +21,7 @@
 // only ever waits for tiles that are already running.
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 #include "hcc_internal.cuh"
 
@@ -181,10 +182,25 @@ __device__ void plan_passes(SortHeader *h, int passes, uint64_t n) {
 // batches are heavily skewed (one digit value often holds most keys), so
 // each warp first picks the most common digit of its first 32 keys for each
 // pass and counts that value in a register; every other digit goes to a
-// shared-memory atomic, where collisions are then rare.  The block's counts
-// then go to the global histograms, and the last block to finish plans the
-// passes.
+// shared-memory atomic.  Threads read 16 bytes of keys at a time (VEC keys)
+// where the keys are 16-byte aligned, whole chunks without bounds checks
+// and the ragged tail one key at a time.  The block's counts then go to the
+// global histograms, and the last block to finish plans the passes.
 template <typename K>
+__device__ __forceinline__ void hist_key(K k, int passes, const uint32_t (&dom)[sizeof(K)],
+                                         uint32_t (&cnt)[sizeof(K)], uint32_t *sh) {
+#pragma unroll
+    for (int p = 0; p < (int)sizeof(K); ++p) {
+        if (p < passes) {
+            const uint32_t d = digit_of(k, (uint32_t)p);
+            const bool is_dom = d == dom[p];
+            cnt[p] += is_dom ? 1u : 0u;
+            if (!is_dom) atomicAdd(&sh[p * RADIX + d], 1u);
+        }
+    }
+}
+
+template <typename K, int VEC>
 __global__ void __launch_bounds__(HIST_BLOCK) k_hist(const K *__restrict__ keys, uint64_t n, uint32_t key_bits,
                                                      int passes, SortHeader *h) {
     __shared__ uint32_t sh[MAX_PASSES * RADIX];
@@ -197,9 +213,9 @@ __global__ void __launch_bounds__(HIST_BLOCK) k_hist(const K *__restrict__ keys,
     const uint64_t first = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     // dominant digit per pass among the warp's first keys
     const K k0 = first < n ? (keys[first] & mask) : (K)0;
-    uint32_t dom[MAX_PASSES], cnt[MAX_PASSES];
+    uint32_t dom[sizeof(K)], cnt[sizeof(K)];  // one per possible pass
 #pragma unroll
-    for (int p = 0; p < MAX_PASSES; ++p) {
+    for (int p = 0; p < (int)sizeof(K); ++p) {
         cnt[p] = 0;
         dom[p] = 0;
         if (p < passes) {
@@ -210,31 +226,35 @@ __global__ void __launch_bounds__(HIST_BLOCK) k_hist(const K *__restrict__ keys,
             dom[p] = best & 511u;
         }
     }
-    constexpr int UNROLL = 8;  // independent loads in flight per thread
-    for (uint64_t base = first; base < n; base += UNROLL * stride) {
-        K kk[UNROLL];
+    constexpr int UNROLL = 4;  // independent 16-byte loads in flight per thread
+    using V = typename std::conditional<VEC == 1, K, uint4>::type;
+    const V *kv = reinterpret_cast<const V *>(keys);
+    const uint64_t nv = n / VEC;                 // whole vectors
+    const uint64_t chunk = UNROLL * stride;      // vectors per grid-wide step
+    const uint64_t full = nv / chunk * chunk;    // vectors in whole steps
+    for (uint64_t base = first; base < full; base += chunk) {
+        V x[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) x[u] = __ldcs(kv + base + (uint64_t)u * stride);
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) {
-            const uint64_t i = base + (uint64_t)u * stride;
-            kk[u] = i < n ? (keys[i] & mask) : (K)0;
-        }
-#pragma unroll
-        for (int u = 0; u < UNROLL; ++u) {
-            if (base + (uint64_t)u * stride >= n) break;
-#pragma unroll
-            for (int p = 0; p < MAX_PASSES; ++p) {
-                if (p < passes) {
-                    const uint32_t d = digit_of(kk[u], (uint32_t)p);
-                    if (d == dom[p])
-                        ++cnt[p];
-                    else
-                        atomicAdd(&sh[p * RADIX + d], 1u);
-                }
+            if constexpr (VEC == 1) {
+                hist_key<K>(x[u] & mask, passes, dom, cnt, sh);
+            } else if constexpr (sizeof(K) == 4) {
+                hist_key<K>((K)x[u].x & mask, passes, dom, cnt, sh);
+                hist_key<K>((K)x[u].y & mask, passes, dom, cnt, sh);
+                hist_key<K>((K)x[u].z & mask, passes, dom, cnt, sh);
+                hist_key<K>((K)x[u].w & mask, passes, dom, cnt, sh);
+            } else {
+                hist_key<K>((((K)x[u].y << 32) | x[u].x) & mask, passes, dom, cnt, sh);
+                hist_key<K>((((K)x[u].w << 32) | x[u].z) & mask, passes, dom, cnt, sh);
             }
         }
     }
+    // the ragged tail: keys after the whole steps, one at a time
+    for (uint64_t i = full * VEC + first; i < n; i += stride) hist_key<K>(keys[i] & mask, passes, dom, cnt, sh);
 #pragma unroll
-    for (int p = 0; p < MAX_PASSES; ++p) {
+    for (int p = 0; p < (int)sizeof(K); ++p) {
         if (p < passes) {
             const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, cnt[p]);
             if (lane == 0 && c && dom[p] < 256u) atomicAdd(&sh[p * RADIX + dom[p]], c);
@@ -544,7 +564,10 @@ cudaError_t run_sort(cudaStream_t s, const K *keys, uint32_t key_bits, uint64_t 
         if (e != cudaSuccess) return e;
         opted.fetch_or(1ull << dev);
     }
-    k_hist<K><<<(unsigned)hblocks, HIST_BLOCK, 0, s>>>(keys, n, key_bits, passes, h);
+    if ((reinterpret_cast<uintptr_t>(keys) & 15u) == 0)
+        k_hist<K, 16 / sizeof(K)><<<(unsigned)hblocks, HIST_BLOCK, 0, s>>>(keys, n, key_bits, passes, h);
+    else
+        k_hist<K, 1><<<(unsigned)hblocks, HIST_BLOCK, 0, s>>>(keys, n, key_bits, passes, h);
     PassArgs<K> a;
     a.user_keys = keys;
     a.buf_a = scratch + L.ka;

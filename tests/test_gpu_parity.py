@@ -267,6 +267,27 @@ def test_sort_key_widths(ctx, k, kind):
     assert np.array_equal(gpu_sort(ctx, keys, k), oracle.stable_sort(keys))
 
 
+@pytest.mark.parametrize("k", [32, 64])
+@pytest.mark.parametrize("n", [5, 622_591, 622_593, 2_490_369])
+def test_sort_keys_not_16_byte_aligned(ctx, k, n):
+    """Keys that start one element past a 16-byte boundary (the histogram
+    then reads them one at a time) and sizes around the histogram's whole
+    vector steps (608 blocks x 256 threads x 4 loads of 16 bytes)."""
+    rng = np.random.default_rng(n + k)
+    keys = _keys("uniform", n, k, rng)
+    keys[::5] = keys[0]
+    dt = np.int32 if k <= 32 else np.int64
+    raw = np.zeros(n + 1, dtype=np.uint32 if k <= 32 else np.uint64)
+    raw[1:] = keys.astype(raw.dtype)
+    base = torch.from_numpy(raw.view(dt)).to(DEV)
+    for kt in (base[1:], base[:n]):
+        perm = torch.full((n,), -7, dtype=torch.int32, device=DEV)
+        hcc.hcc_sort(ctx, kt, k, n, perm)
+        hcc.hcc_sync(ctx)
+        ref = kt.cpu().numpy().view(np.uint32 if k <= 32 else np.uint64).astype(np.uint64)
+        assert np.array_equal(perm.cpu().numpy().view(np.uint32), oracle.stable_sort(ref))
+
+
 def test_sort_ignores_bits_above_key_bits(ctx):
     rng = np.random.default_rng(5)
     keys = rng.integers(0, 2 ** 32 - 1, 50_000, dtype=np.uint64)
