@@ -182,30 +182,31 @@ __device__ void plan_passes(SortHeader *h, int passes, uint64_t n) {
 // batches are heavily skewed (one digit value often holds most keys), so
 // each warp first picks the most common digit of its first 32 keys for each
 // pass and counts that value in a register; every other digit goes to a
-// shared-memory atomic.  Threads read 16 bytes of keys at a time (VEC keys)
-// where the keys are 16-byte aligned, whole chunks without bounds checks
-// and the ragged tail one key at a time.  The block's counts then go to the
+// shared-memory add (predicated, not branched around).  Threads read 16
+// bytes of keys at a time (VEC keys) where the keys are 16-byte aligned; the
+// last n % VEC keys are read one at a time.  The block's counts then go to the
 // global histograms, and the last block to finish plans the passes.
-template <typename K>
-__device__ __forceinline__ void hist_key(K k, int passes, const uint32_t (&dom)[sizeof(K)],
-                                         uint32_t (&cnt)[sizeof(K)], uint32_t *sh) {
+template <typename K, int P>
+__device__ __forceinline__ void hist_key(K k, const uint32_t (&dom)[P], uint32_t (&cnt)[P], uint32_t sh) {
 #pragma unroll
-    for (int p = 0; p < (int)sizeof(K); ++p) {
-        if (p < passes) {
-            const uint32_t d = digit_of(k, (uint32_t)p);
-            const bool is_dom = d == dom[p];
-            cnt[p] += is_dom ? 1u : 0u;
-            if (!is_dom) atomicAdd(&sh[p * RADIX + d], 1u);
-        }
+    for (int p = 0; p < P; ++p) {
+        const uint32_t d = digit_of(k, (uint32_t)p);
+        cnt[p] += d == dom[p] ? 1u : 0u;
+        // a predicated shared-memory add for the other digits, no branch
+        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, %1;\n\t@q red.shared.add.u32 [%2], 1;\n\t}" ::"r"(d),
+                     "r"(dom[p]), "r"(sh + (uint32_t)(p * RADIX + d) * 4u)
+                     : "memory");
     }
 }
 
-template <typename K, int VEC>
+// P: the number of digit passes (a template argument, so that the per-key
+// loop has no pass test).
+template <typename K, int VEC, int P>
 __global__ void __launch_bounds__(HIST_BLOCK) k_hist(const K *__restrict__ keys, uint64_t n, uint32_t key_bits,
-                                                     int passes, SortHeader *h) {
+                                                     SortHeader *h) {
     __shared__ uint32_t sh[MAX_PASSES * RADIX];
     __shared__ bool s_last;
-    for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) sh[i] = 0;
+    for (int i = threadIdx.x; i < P * RADIX; i += blockDim.x) sh[i] = 0;
     __syncthreads();
     const K mask = key_mask<K>(key_bits);
     const uint32_t lane = threadIdx.x & 31;
@@ -213,55 +214,52 @@ __global__ void __launch_bounds__(HIST_BLOCK) k_hist(const K *__restrict__ keys,
     const uint64_t first = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     // dominant digit per pass among the warp's first keys
     const K k0 = first < n ? (keys[first] & mask) : (K)0;
-    uint32_t dom[sizeof(K)], cnt[sizeof(K)];  // one per possible pass
+    uint32_t dom[P], cnt[P];
 #pragma unroll
-    for (int p = 0; p < (int)sizeof(K); ++p) {
+    for (int p = 0; p < P; ++p) {
         cnt[p] = 0;
-        dom[p] = 0;
-        if (p < passes) {
-            const uint32_t d = digit_of(k0, (uint32_t)p);
-            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, first < n ? d : 256u + lane);
-            uint32_t best = ((uint32_t)__popc(peers) << 9) | d;
-            best = __reduce_max_sync(0xFFFFFFFFu, best);
-            dom[p] = best & 511u;
-        }
+        const uint32_t d = digit_of(k0, (uint32_t)p);
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, first < n ? d : 256u + lane);
+        uint32_t best = ((uint32_t)__popc(peers) << 9) | d;
+        best = __reduce_max_sync(0xFFFFFFFFu, best);
+        dom[p] = best & 511u;
     }
     constexpr int UNROLL = 4;  // independent 16-byte loads in flight per thread
     using V = typename std::conditional<VEC == 1, K, uint4>::type;
     const V *kv = reinterpret_cast<const V *>(keys);
-    const uint64_t nv = n / VEC;                 // whole vectors
-    const uint64_t chunk = UNROLL * stride;      // vectors per grid-wide step
-    const uint64_t full = nv / chunk * chunk;    // vectors in whole steps
-    for (uint64_t base = first; base < full; base += chunk) {
+    const uint32_t shb = (uint32_t)__cvta_generic_to_shared(sh);
+    const uint64_t nv = n / VEC;  // whole vectors; the last n % VEC keys follow one at a time
+    for (uint64_t base = first; base < nv; base += UNROLL * stride) {
         V x[UNROLL];
 #pragma unroll
-        for (int u = 0; u < UNROLL; ++u) x[u] = __ldcs(kv + base + (uint64_t)u * stride);
+        for (int u = 0; u < UNROLL; ++u) {
+            const uint64_t v = base + (uint64_t)u * stride;
+            x[u] = v < nv ? kv[v] : V{};
+        }
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) {
+            if (base + (uint64_t)u * stride >= nv) break;
             if constexpr (VEC == 1) {
-                hist_key<K>(x[u] & mask, passes, dom, cnt, sh);
+                hist_key<K, P>(x[u] & mask, dom, cnt, shb);
             } else if constexpr (sizeof(K) == 4) {
-                hist_key<K>((K)x[u].x & mask, passes, dom, cnt, sh);
-                hist_key<K>((K)x[u].y & mask, passes, dom, cnt, sh);
-                hist_key<K>((K)x[u].z & mask, passes, dom, cnt, sh);
-                hist_key<K>((K)x[u].w & mask, passes, dom, cnt, sh);
+                hist_key<K, P>((K)x[u].x & mask, dom, cnt, shb);
+                hist_key<K, P>((K)x[u].y & mask, dom, cnt, shb);
+                hist_key<K, P>((K)x[u].z & mask, dom, cnt, shb);
+                hist_key<K, P>((K)x[u].w & mask, dom, cnt, shb);
             } else {
-                hist_key<K>((((K)x[u].y << 32) | x[u].x) & mask, passes, dom, cnt, sh);
-                hist_key<K>((((K)x[u].w << 32) | x[u].z) & mask, passes, dom, cnt, sh);
+                hist_key<K, P>((((K)x[u].y << 32) | x[u].x) & mask, dom, cnt, shb);
+                hist_key<K, P>((((K)x[u].w << 32) | x[u].z) & mask, dom, cnt, shb);
             }
         }
     }
-    // the ragged tail: keys after the whole steps, one at a time
-    for (uint64_t i = full * VEC + first; i < n; i += stride) hist_key<K>(keys[i] & mask, passes, dom, cnt, sh);
+    for (uint64_t i = nv * VEC + first; i < n; i += stride) hist_key<K, P>(keys[i] & mask, dom, cnt, shb);
 #pragma unroll
-    for (int p = 0; p < (int)sizeof(K); ++p) {
-        if (p < passes) {
-            const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, cnt[p]);
-            if (lane == 0 && c && dom[p] < 256u) atomicAdd(&sh[p * RADIX + dom[p]], c);
-        }
+    for (int p = 0; p < P; ++p) {
+        const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, cnt[p]);
+        if (lane == 0 && c && dom[p] < 256u) atomicAdd(&sh[p * RADIX + dom[p]], c);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x)
+    for (int i = threadIdx.x; i < P * RADIX; i += blockDim.x)
         if (sh[i]) atomicAdd(&h->hist[0][0] + i, sh[i]);
     // the last block to finish plans the passes
     __threadfence();
@@ -270,7 +268,21 @@ __global__ void __launch_bounds__(HIST_BLOCK) k_hist(const K *__restrict__ keys,
     __syncthreads();
     if (s_last) {
         __threadfence();
-        plan_passes(h, passes, n);
+        plan_passes(h, P, n);
+    }
+}
+
+// The histogram kernel for `passes` digit passes (1-4 for 32-bit keys, 5-8
+// for 64-bit keys) and the keys' alignment.
+template <typename K, int VEC>
+void launch_hist(cudaStream_t s, unsigned blocks, const K *keys, uint64_t n, uint32_t key_bits, int passes,
+                 SortHeader *h) {
+    constexpr int LO = sizeof(K) == 4 ? 1 : 5;
+    switch (passes - LO) {
+        case 0: k_hist<K, VEC, LO><<<blocks, HIST_BLOCK, 0, s>>>(keys, n, key_bits, h); break;
+        case 1: k_hist<K, VEC, LO + 1><<<blocks, HIST_BLOCK, 0, s>>>(keys, n, key_bits, h); break;
+        case 2: k_hist<K, VEC, LO + 2><<<blocks, HIST_BLOCK, 0, s>>>(keys, n, key_bits, h); break;
+        default: k_hist<K, VEC, LO + 3><<<blocks, HIST_BLOCK, 0, s>>>(keys, n, key_bits, h); break;
     }
 }
 
@@ -565,9 +577,9 @@ cudaError_t run_sort(cudaStream_t s, const K *keys, uint32_t key_bits, uint64_t 
         opted.fetch_or(1ull << dev);
     }
     if ((reinterpret_cast<uintptr_t>(keys) & 15u) == 0)
-        k_hist<K, 16 / sizeof(K)><<<(unsigned)hblocks, HIST_BLOCK, 0, s>>>(keys, n, key_bits, passes, h);
+        launch_hist<K, 16 / sizeof(K)>(s, (unsigned)hblocks, keys, n, key_bits, passes, h);
     else
-        k_hist<K, 1><<<(unsigned)hblocks, HIST_BLOCK, 0, s>>>(keys, n, key_bits, passes, h);
+        launch_hist<K, 1>(s, (unsigned)hblocks, keys, n, key_bits, passes, h);
     PassArgs<K> a;
     a.user_keys = keys;
     a.buf_a = scratch + L.ka;
