@@ -29,8 +29,12 @@ struct DevBuf {
 // pipelined hcc_run_host.
 constexpr uint64_t HOST_CHUNK = 1ull << 22;
 constexpr uint32_t HOST_LANES = 2;
-// The first chunk is half as large, so the first kernels start sooner.
-static uint64_t host_chunk_rays(uint64_t c, uint64_t rem) { return std::min(c == 0 ? HOST_CHUNK / 2 : HOST_CHUNK, rem); }
+// The first chunks are a quarter and a half as large, so the first kernels
+// start sooner while the next copies catch up (1M, 2M, then 4M rays: 5.81 ms
+// for the room's 16.6M rays against 5.88 with 2M then 4M, 5.98 with 1M then 4M).
+static uint64_t host_chunk_rays(uint64_t c, uint64_t rem) {
+    return std::min(c == 0 ? HOST_CHUNK / 4 : c == 1 ? HOST_CHUNK / 2 : HOST_CHUNK, rem);
+}
 
 struct hcc_ctx {
     int device = 0;

@@ -685,9 +685,10 @@ def chunk_room():
     return w
 
 
-# the whole wavefront (a 2^21 chunk, then 2^22 and the rest), one ray more
-# than a single pass (2^21 + 2^21 + 1), and three chunks with a 5-ray tail
-@pytest.mark.parametrize("n_rays", [None, (1 << 22) + 1, (1 << 21) + (1 << 22) + 5])
+# the whole wavefront (chunks of 2^20, 2^21, then 2^22 and the rest), one ray
+# more than a single pass (2^20 + 2^21 + 2^20 + 1), and four chunks with a
+# 5-ray tail
+@pytest.mark.parametrize("n_rays", [None, (1 << 22) + 1, (1 << 20) + (1 << 21) + (1 << 22) + 5])
 def test_run_host_pipeline_over_chunks(ctx, chunk_room, n_rays):
     """Rays above 2^22 go through the two-stream chunked host pipeline: every
     hit equals the device pipeline's, and a sample equals the oracle's."""
