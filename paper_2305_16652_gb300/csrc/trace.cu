@@ -464,7 +464,7 @@ template <bool ANY, bool COUNT, int LAYOUT, bool MULTI>
 __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
     uint64_t i = (uint64_t)blockIdx.x * TRACE_BLOCK + threadIdx.x;
     if (i >= a.n) return;
-    if (a.gather) i = a.n - 1 - i;  // sorted order from its end (blocks start in index order)
+    if (a.gather || a.scatter) i = a.n - 1 - i;  // sorted order from its end (blocks start in index order)
     float4 o4, d4;
     const uint4 *nodes;
     const float4 *tris;
@@ -488,11 +488,14 @@ __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(TraceArgs a) {
 // equal keys.  Every ray's record is the same as in k_trace: a ray's own
 // traversal does not depend on which rays share its warp, except for which
 // of several hits an any-hit query returns first.  A trace in sorted order
-// (rays fetched through a permutation) hands out its slots from the end of
-// the order, largest keys first: for HCC keys those are the rays that cross
-// the most cut boxes, the longest traversals, and starting them first leaves
-// short rays for the end of the launch, where warps run out of work (the
-// room's 16.6M-ray HCC trace: 4.08 ms against 4.19 in ascending order).
+// (rays fetched through a permutation, or already gathered and their hits
+// written back through one) hands out its slots from the end of
+// the order, largest keys first: in HCC order those are the rays whose keys
+// set the most cut nodes and the longest traversals (the room's 16.6M rays:
+// 54.8 node visits per ray in the last tenth of the order, 15.8 in the
+// first), and starting them first leaves short rays for the end of the
+// launch, where warps run out of work (its HCC trace: 4.08 ms against 4.19
+// in ascending order).
 // BLOCK threads per block and STACKN stack entries per ray are a shape the
 // autotuner may pick.
 template <bool ANY, bool COUNT, int LAYOUT, bool MULTI, int BLOCK, int STACKN>
@@ -521,7 +524,7 @@ __global__ void __launch_bounds__(BLOCK, ((LAYOUT == 2 || MULTI) ? POOL_THREADS_
             base = __shfl_sync(FULL, base, leader);
             if (want) {
                 slot = base + __popc(need & lt);
-                if (a.gather && slot < a.n) slot = a.n - 1 - slot;  // sorted order from its end
+                if ((a.gather || a.scatter) && slot < a.n) slot = a.n - 1 - slot;  // sorted order from its end
                 if (slot < a.n) {
                     float4 o4, d4;
                     uint32_t root;
