@@ -262,10 +262,23 @@ __device__ __forceinline__ uint32_t ray_pop(RayState &s, const uint2 *stack) {
     return REF_NONE;
 }
 
+// The node loop of a round ends once all but LEAF_SLACK of the warp's lanes
+// still descending hold a parked leaf.  Waiting for every lane (the plain
+// postponed-leaf rule) kept the others idle behind the last few descents:
+// on the room's 16.6M rays a slack of 3 or 4 traced 4.6 % (unsorted) and
+// 2 % (HCC order) faster than 0, 6 and 8 slower than 3.
+constexpr int LEAF_SLACK = 3;
+__device__ __forceinline__ bool leaves_ready(const RayState &s) {
+    const uint32_t active = __activemask();
+    const uint32_t parked = __ballot_sync(active, s.leaf != REF_NONE);
+    return __popc(parked) + LEAF_SLACK >= __popc(active);
+}
+
 // One round of the traversal loop ("while-while" with postponed leaves,
-// Aila & Laine 2009): descend internal nodes until every lane of the warp
-// holds a leaf (a lane that reaches a leaf parks it and keeps descending),
-// then test the parked leaf and any leaf that is next on the stack.  The
+// Aila & Laine 2009): descend internal nodes until (nearly) every lane of
+// the warp holds a leaf (a lane that reaches a leaf parks it and keeps
+// descending), then test the parked leaf and any leaf that is next on the
+// stack; a lane without a leaf yet resumes its descent in the next round.  The
 // nearer child is visited first and the farther one is pushed with its
 // entry distance, which lets a pop skip subtrees beyond the best hit.
 template <bool ANY, bool COUNT, int LAYOUT, int STACKN>
@@ -316,9 +329,9 @@ __device__ __forceinline__ void ray_round(RayState &s, uint2 *stack, const uint4
             s.leaf = s.node;
             s.node = ray_pop(s, stack);
         }
-        if (__all_sync(__activemask(), s.leaf != REF_NONE)) break;
+        if (leaves_ready(s)) break;
     }
-    // internal nodes: descend until every lane has a leaf parked
+    // internal nodes: descend until (nearly) every lane has a leaf parked
     while (LAYOUT != 2 && s.node != REF_NONE && !(s.node & REF_LEAF)) {
         ChildBoxes c;
         if (LAYOUT == 0)
@@ -352,7 +365,7 @@ __device__ __forceinline__ void ray_round(RayState &s, uint2 *stack, const uint4
             s.leaf = s.node;
             s.node = ray_pop(s, stack);
         }
-        if (__all_sync(__activemask(), s.leaf != REF_NONE)) break;
+        if (leaves_ready(s)) break;
     }
     // leaves: the parked one, then any leaf that is next on the stack
     while (s.leaf != REF_NONE) {
