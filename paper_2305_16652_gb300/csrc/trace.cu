@@ -262,17 +262,21 @@ __device__ __forceinline__ uint32_t ray_pop(RayState &s, const uint2 *stack) {
     return REF_NONE;
 }
 
-// The node loop of a round ends once all but LEAF_SLACK of the warp's lanes
-// still descending hold a parked leaf.  Waiting for every lane (the plain
-// postponed-leaf rule) kept the others idle behind the last few descents:
-// on the room's 16.6M rays a slack of 3 or 4 traced 4.6 % (unsorted) and
-// 2 % (HCC order) faster than 0, 6 and 8 slower than 3.
+// The node loop of a closest-hit round ends once all but LEAF_SLACK of the
+// warp's lanes still descending hold a parked leaf.  Waiting for every lane
+// (the plain postponed-leaf rule) kept the others idle behind the last few
+// descents: on the room's 16.6M rays a slack of 3 or 4 traced 4.6 %
+// (unsorted) and 2 % (HCC order) faster than 0, 6 and 8 slower than 3.
+// The leaf loop of a closest-hit round goes on to the next leaf on the stack
+// while at least LEAF_MIN lanes have one (4 measured best of 0, 4, 8 and 12:
+// 0.6 % faster than chaining leaves while any lane has one).  Any-hit traces
+// keep the plain rules (every lane; chain while any lane has a leaf), which
+// measured 1-2 % faster for them.
 constexpr int LEAF_SLACK = 3;
-// The leaf loop of a round goes on to the next leaf on the stack while at
-// least LEAF_MIN lanes have one (4 measured best of 0, 4, 8 and 12: 0.6 %
-// faster than chaining leaves while any lane has one).
 constexpr int LEAF_MIN = 4;
+template <bool ANY>
 __device__ __forceinline__ bool leaves_ready(const RayState &s) {
+    if (ANY) return __all_sync(__activemask(), s.leaf != REF_NONE);
     const uint32_t active = __activemask();
     const uint32_t parked = __ballot_sync(active, s.leaf != REF_NONE);
     return __popc(parked) + LEAF_SLACK >= __popc(active);
@@ -333,7 +337,7 @@ __device__ __forceinline__ void ray_round(RayState &s, uint2 *stack, const uint4
             s.leaf = s.node;
             s.node = ray_pop(s, stack);
         }
-        if (leaves_ready(s)) break;
+        if (leaves_ready<ANY>(s)) break;
     }
     // internal nodes: descend until (nearly) every lane has a leaf parked
     while (LAYOUT != 2 && s.node != REF_NONE && !(s.node & REF_LEAF)) {
@@ -369,7 +373,7 @@ __device__ __forceinline__ void ray_round(RayState &s, uint2 *stack, const uint4
             s.leaf = s.node;
             s.node = ray_pop(s, stack);
         }
-        if (leaves_ready(s)) break;
+        if (leaves_ready<ANY>(s)) break;
     }
     // leaves: the parked one, then any leaf that is next on the stack
     while (s.leaf != REF_NONE) {
@@ -404,8 +408,7 @@ __device__ __forceinline__ void ray_round(RayState &s, uint2 *stack, const uint4
         }
         // fewer than LEAF_MIN lanes with a next leaf: keep it parked for
         // the next round rather than hold the warp here for them
-        const uint32_t active = __activemask();
-        if (__popc(__ballot_sync(active, s.leaf != REF_NONE)) < LEAF_MIN) break;
+        if (!ANY && __popc(__ballot_sync(__activemask(), s.leaf != REF_NONE)) < LEAF_MIN) break;
     }
 }
 
